@@ -1,0 +1,258 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmark and the oracle.
+
+This module holds no arithmetic of the method: only a counter-based random
+generator, the problem description and the recipes of the synthetic
+workloads (sizes, frequencies, parameter draws).  Both the CUDA binding and
+the oracle read a ``Problem``; neither is imported here.
+
+Random numbers: SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), evaluated as a counter-based
+generator: value i of stream s is mix64(s + (i + 1) * 0x9E3779B97F4A7C15).
+Uniforms take the top 53 bits; normals use the Box-Muller transform.  The
+stream is the same on every machine and numpy version.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+MODEL_TOY, MODEL_WMAP, MODEL_JF12 = 0, 1, 2
+N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16}
+
+#: Parameter names of each model, in theta order.
+THETA_NAMES = {
+    MODEL_TOY: ["Bx", "By", "Bz", "ne", "N0", "p", "R0"],
+    MODEL_WMAP: ["b0", "psi0", "psi1", "chi0B", "Bux", "N0_obs", "p", "ne0"],
+    MODEL_JF12: [f"b{k + 1}" for k in range(8)]
+    + ["B_h", "z_h", "B_X", "theta_X", "N0_obs", "p", "h1", "h2"],
+}
+
+#: Index of the CR spectral index p in each model's theta.
+P_INDEX = {MODEL_TOY: 5, MODEL_WMAP: 6, MODEL_JF12: 13}
+
+OBS_PAPER_KPC = (-8.3, 0.0, 0.006)      # Sec. 2.1
+OBS_CONFIG_KPC = (-8.5, 0.0, 0.015)     # synthetic workloads
+BOX_PAPER_KPC = (40.0, 40.0, 10.0)      # Sec. 2.4
+N0_EARTH = 4.0e-5                       # cm^-3, Sec. 3.1
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = z.copy()
+    z ^= z >> np.uint64(30)
+    z *= _M1
+    z ^= z >> np.uint64(27)
+    z *= _M2
+    z ^= z >> np.uint64(31)
+    return z
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n consecutive SplitMix64 outputs of stream `seed`, starting at index `offset`."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        state = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + idx * _GOLDEN
+        return _mix64(state)
+
+
+def substream(seed: int, tag: int) -> int:
+    """A seed for an independent sub-stream (one mix of seed and tag)."""
+    with np.errstate(over="ignore"):
+        v = np.array([(seed * 0x100000001B3 + tag) & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
+        return int(_mix64(v)[0])
+
+
+def uniform(seed: int, n: int, lo: float = 0.0, hi: float = 1.0, offset: int = 0) -> np.ndarray:
+    u = (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+def normal(seed: int, n: int) -> np.ndarray:
+    """n standard normals by Box-Muller over pairs of uniforms."""
+    m = (n + 1) // 2
+    raw = splitmix64(seed, 2 * m)
+    u1 = ((raw[0::2] >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)  # (0, 1]
+    u2 = (raw[1::2] >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    rad = np.sqrt(-2.0 * np.log(u1))
+    out = np.empty(2 * m, dtype=np.float64)
+    out[0::2] = rad * np.cos(2.0 * math.pi * u2)
+    out[1::2] = rad * np.sin(2.0 * math.pi * u2)
+    return out[:n]
+
+
+@dataclasses.dataclass
+class Problem:
+    """One map to march (the paper's problem statement, Sec. 2.3).
+
+    nside, n_steps: HEALPix resolution and N_int.  freq_hz: 1..16
+    frequencies.  model_id / theta: field model and its parameters (see
+    THETA_NAMES).  r_max_kpc: ray length, unless box_clip, in which case each
+    ray ends at the boundary of the box box_kpc centred on the Galactic centre.
+    obs_kpc: observer position.  f64: march in double precision and return
+    double maps.  pix_begin / pix_count: a contiguous RING pixel range
+    (pix_count 0 = to the end of the map).  rm_rule: how much of a cell's
+    own n_e B_LOS dr enters the RM at its midpoint: 0 half (default), 1 none,
+    2 all of it (a plain cumulative sum).
+    """
+
+    nside: int
+    n_steps: int
+    freq_hz: tuple
+    model_id: int
+    theta: np.ndarray
+    r_max_kpc: float = 20.0
+    obs_kpc: tuple = OBS_CONFIG_KPC
+    box_clip: bool = False
+    box_kpc: tuple = BOX_PAPER_KPC
+    f64: bool = False
+    pix_begin: int = 0
+    pix_count: int = 0
+    rm_rule: int = 0
+
+    def __post_init__(self):
+        self.theta = np.asarray(self.theta, dtype=np.float64).copy()
+        self.freq_hz = tuple(float(f) for f in self.freq_hz)
+
+    @property
+    def npix(self) -> int:
+        return 12 * self.nside * self.nside
+
+    @property
+    def n_pix_out(self) -> int:
+        return self.pix_count if self.pix_count else self.npix - self.pix_begin
+
+    @property
+    def n_freq(self) -> int:
+        return len(self.freq_hz)
+
+    @property
+    def samples(self) -> int:
+        """LOS integration points of one map (Sec. 4.2: 12 NSIDE^2 N_int)."""
+        return self.n_pix_out * self.n_steps
+
+    def replace(self, **kw) -> "Problem":
+        return dataclasses.replace(self, **kw)
+
+    def with_theta(self, theta) -> "Problem":
+        return dataclasses.replace(self, theta=np.asarray(theta, dtype=np.float64).copy())
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes
+# ---------------------------------------------------------------------------
+FREQS_C1 = (408e6, 1.4e9)
+FREQS_C2 = (408e6, 1.4e9, 2.3e9, 23e9)
+
+
+def toy_theta(Bx=6.0, By=0.0, Bz=0.0, ne=0.01, N0=4.01e-5, p=3.0, R0=4.0) -> np.ndarray:
+    """Sec. 2.4 toy: uniform B = (6 uG, 0, 0), n_e = 0.01, N0 = 4.01e-5 cm^-3
+    inside a 4 kpc sphere around the observer."""
+    return np.array([Bx, By, Bz, ne, N0, p, R0], dtype=np.float64)
+
+
+def toy_problem(nside=64, n_steps=1024, freq_hz=(2.4e9,), box_clip=True, **kw) -> Problem:
+    """The paper's accuracy test (Sec. 2.4): NSIDE 64, N_int 1024, 2.4 GHz,
+    box (40, 40, 10) kpc, observer at (-8.3, 0, 0.006) kpc."""
+    return Problem(nside=nside, n_steps=n_steps, freq_hz=freq_hz, model_id=MODEL_TOY,
+                   theta=kw.pop("theta", toy_theta()), obs_kpc=kw.pop("obs_kpc", OBS_PAPER_KPC),
+                   box_clip=box_clip, **kw)
+
+
+def wmap_theta() -> np.ndarray:
+    """Plain-forward workload at Nside 16: b0 = 6 uG, pitch psi0 = 11.5 deg,
+    psi1 = chi0B = 0, uniform 1 uG x field, N0(obs) = 4e-5 cm^-3, p = 3,
+    n_e0 = 0.03 cm^-3."""
+    return np.array([6.0, math.radians(11.5), 0.0, 0.0, 1.0, N0_EARTH, 3.0, 0.03])
+
+
+def config1() -> Problem:
+    """Nside 16, 128 steps to 20 kpc, WMAP-type field, 408 MHz and 1.4 GHz, FP64."""
+    return Problem(nside=16, n_steps=128, freq_hz=FREQS_C1, model_id=MODEL_WMAP,
+                   theta=wmap_theta(), f64=True)
+
+
+def jf12_fiducial(seed: int = 2) -> np.ndarray:
+    """JF12-type parameters: arm strengths U[-3, 3] uG and p U[2.8, 3.2] drawn
+    from `seed`; halo B_h = 1.4 uG, z_h = 5.3 kpc; X field B_X = 4.6 uG,
+    theta_X = 49 deg; N0(obs) = 4e-5 cm^-3; n_e scale heights 1.0 and 0.15 kpc."""
+    arms = uniform(substream(seed, 1), 8, -3.0, 3.0)
+    p = float(uniform(substream(seed, 2), 1, 2.8, 3.2)[0])
+    return np.concatenate([arms, [1.4, 5.3, 4.6, math.radians(49.0), N0_EARTH, p, 1.0, 0.15]])
+
+
+#: Scale of each JF12 parameter for relative steps: |theta_i|, 3 uG for arms.
+def jf12_scales(theta) -> np.ndarray:
+    s = np.abs(np.asarray(theta, dtype=np.float64)).copy()
+    s[:8] = 3.0
+    return s
+
+
+def config2(seed: int = 2) -> Problem:
+    """Nside 64, 512 steps to 20 kpc, JF12-type field, four frequencies, FP32."""
+    return Problem(nside=64, n_steps=512, freq_hz=FREQS_C2, model_id=MODEL_JF12,
+                   theta=jf12_fiducial(seed))
+
+
+def perturbed_theta(theta, seed: int = 3, frac: float = 0.05) -> np.ndarray:
+    """theta + N(0, (frac * scale_i)^2), scale = |theta_i| (3 uG for arms)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    return theta + frac * jf12_scales(theta) * normal(substream(seed, 1), theta.size)
+
+
+def target_noise(shape, seed: int = 3, sigma: float = 0.5) -> np.ndarray:
+    """Gaussian map noise N(0, sigma^2) in K, for the chi^2 target."""
+    n = int(np.prod(shape))
+    return (sigma * normal(substream(seed, 2), n)).reshape(shape)
+
+
+def config3(seed: int = 3) -> tuple[Problem, np.ndarray, float]:
+    """Adjoint workload: the Nside-64 JF12-type model, its 16 parameters free.
+    Returns (problem at the fiducial theta, the perturbed theta that generates
+    the target map, sigma = 0.5 K).  The caller renders the target map with a
+    forward model of its choice and adds target_noise()."""
+    prob = config2()
+    return prob, perturbed_theta(prob.theta, seed), 0.5
+
+
+NSIDE_CHOICES = (16, 32, 64, 128)
+STEP_CHOICES = (128, 256, 512, 1024)
+
+
+def config4(n_sets: int = 256, seed: int = 4) -> list[Problem]:
+    """Batched ensemble: theta ~ N(theta_fid, (0.05 |theta_fid|)^2) (arms 0.15 uG),
+    p clipped to [2.8, 3.2]; Nside and steps drawn uniformly per set."""
+    fid = jf12_fiducial(2)
+    scale = jf12_scales(fid)
+    sets = []
+    g = normal(substream(seed, 1), n_sets * fid.size).reshape(n_sets, fid.size)
+    u_ns = splitmix64(substream(seed, 2), n_sets)
+    u_st = splitmix64(substream(seed, 3), n_sets)
+    for k in range(n_sets):
+        th = fid + 0.05 * scale * g[k]
+        th[13] = min(max(th[13], 2.8), 3.2)
+        nside = NSIDE_CHOICES[int(u_ns[k] % np.uint64(4))]
+        steps = STEP_CHOICES[int(u_st[k] % np.uint64(4))]
+        sets.append(Problem(nside=nside, n_steps=steps, freq_hz=FREQS_C2,
+                            model_id=MODEL_JF12, theta=th))
+    return sets
+
+
+def config5_thetas(n: int = 50000, seed: int = 50, frac: float = 0.2) -> np.ndarray:
+    """Surrogate training draws: theta ~ U[theta_fid -/+ frac * scale_i]."""
+    fid = jf12_fiducial(2)
+    scale = jf12_scales(fid)
+    u = uniform(substream(seed, 1), n * fid.size, -1.0, 1.0).reshape(n, fid.size)
+    th = fid[None, :] + frac * scale[None, :] * u
+    return th
+
+
+def sample_pixels(npix: int, count: int, seed: int = 11) -> np.ndarray:
+    """`count` distinct pixel indices in [0, npix), sorted, from a seeded stream."""
+    count = min(count, npix)
+    keys = splitmix64(substream(seed, npix), npix)
+    return np.sort(np.argsort(keys, kind="stable")[:count]).astype(np.int64)
