@@ -1,0 +1,144 @@
+/*
+ * synax.h -- C ABI of the GB300-native synchrotron ray march.
+ *
+ * The library marches one ray per HEALPix pixel (paper Sec. 2.3) through a
+ * parametric Galactic magnetic field B, cosmic-ray density N0 and thermal
+ * electron density n_e.  At each midpoint it evaluates the synchrotron
+ * emissivities j_I and j_P (Eq. 2, Eq. 5), the intrinsic polarisation angle
+ * chi_0 (Eq. 8) and the rotation measure RM (Eq. 7), and it accumulates
+ * Stokes I, Q, U as the discrete sums of Eq. 9 with chi = chi_0 + RM lambda^2
+ * (Eq. 6).  Outputs are Rayleigh-Jeans brightness temperatures in K.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are CUDA device pointers of the current device;
+ *     the caller allocates and owns them.  Host structs are read during the
+ *     call only and may be freed when it returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it; results are valid
+ *     after the stream is synchronised.
+ *   - Return value: SYNAX_OK (0) or a negative SYNAX_E* code.  Problems are
+ *     validated on the host before anything is enqueued; an invalid problem
+ *     returns SYNAX_EINVAL (or SYNAX_ENONFINITE for NaN/Inf parameters) and
+ *     touches no device memory.  SYNAX_ECUDA reports a CUDA launch or API
+ *     error; synax_last_cuda_error() then gives the CUDA error code.
+ *   - No C++ exception crosses this boundary.  The library allocates device
+ *     memory only inside synax_batch_plan_create and synax_surrogate_create;
+ *     every other call uses caller-provided buffers.
+ *
+ * Map layout: maps[f][s][i], f = frequency index (order of freq_hz), s = 0 (I),
+ * 1 (Q), 2 (U), i = pixel index relative to pix_begin, contiguous, float32
+ * unless SYNAX_F64 is set (then float64).
+ */
+#ifndef SYNAX_H
+#define SYNAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SYNAX_OK           0
+#define SYNAX_EINVAL      -1   /* malformed problem or argument */
+#define SYNAX_ENONFINITE  -2   /* a parameter, frequency or position is NaN/Inf */
+#define SYNAX_ECUDA       -3   /* CUDA runtime error (see synax_last_cuda_error) */
+#define SYNAX_ENOMEM      -4   /* allocation inside a *_create call failed */
+#define SYNAX_ETIMEOUT    -5   /* a bounded device-side wait gave up */
+#define SYNAX_ENOTSUP     -6   /* combination not supported (e.g. model without adjoint) */
+#define SYNAX_ESPACE      -7   /* caller-provided workspace too small */
+
+/* ---- field models (layout of theta) ----
+ * SYNAX_MODEL_TOY  (Sec. 2.4) theta = [Bx, By, Bz (uG), n_e (cm^-3), N0 (cm^-3), p, R0 (kpc)]:
+ *   uniform fields inside the sphere |r - r_obs| < R0, zero outside.
+ * SYNAX_MODEL_WMAP (Sec. 3.1, Eq. 12-13, with an exponential envelope)
+ *   theta = [b0 (uG), psi0, psi1, chi0B (rad), Bux (uG), N0_obs (cm^-3), p, ne0 (cm^-3)].
+ * SYNAX_MODEL_JF12 (JF12-type: 8 smooth log-spiral arms, toroidal halo, X field)
+ *   theta = [b1..b8 (uG), B_h (uG), z_h (kpc), B_X (uG), theta_X (rad),
+ *            N0_obs (cm^-3), p, h1 (kpc), h2 (kpc)].
+ * N0_obs is the CR density at the observer; p is the CR spectral index
+ * (the paper's alpha). */
+#define SYNAX_MODEL_TOY   0
+#define SYNAX_MODEL_WMAP  1
+#define SYNAX_MODEL_JF12  2
+
+#define SYNAX_MAX_FREQ   16
+#define SYNAX_MAX_THETA  32
+
+/* ---- problem flags ---- */
+#define SYNAX_F64       (1u << 0)  /* march in FP64; maps (and gmaps/targets) are double */
+#define SYNAX_BOX_CLIP  (1u << 1)  /* ray ends at the box boundary (Sec. 2.3), else at r_max */
+
+/* One map to march: the paper's problem statement (Sec. 2.3). */
+typedef struct synax_problem {
+    int32_t  nside;               /* HEALPix Nside, power of two in [1, 8192] */
+    int32_t  n_steps;             /* N_int, in [1, 65536] */
+    double   r_max_kpc;           /* ray length when SYNAX_BOX_CLIP is clear, > 0 */
+    double   box_kpc[3];          /* box lengths (l_x, l_y, l_z) centred on the GC */
+    double   obs_kpc[3];          /* observer, galactocentric Cartesian kpc */
+    int32_t  n_freq;              /* 1..SYNAX_MAX_FREQ */
+    double   freq_hz[SYNAX_MAX_FREQ];
+    int32_t  model_id;            /* SYNAX_MODEL_* */
+    int32_t  n_theta;             /* must equal the model's parameter count */
+    double   theta[SYNAX_MAX_THETA];
+    uint32_t flags;               /* SYNAX_F64 | SYNAX_BOX_CLIP */
+    int32_t  rm_rule;             /* share of a cell's own n_e B_LOS dr in its RM:
+                                     0 half (default), 1 none, 2 all */
+    int64_t  pix_begin;           /* first RING pixel marched, >= 0 */
+    int64_t  pix_count;           /* pixels marched; 0 = to the end of the map */
+} synax_problem;
+
+/* Forward march (Sec. 2.3, Eq. 2 and 5-9).
+ * maps_dev: [n_freq][3][pix_count] float32 (float64 with SYNAX_F64),
+ * written completely.  Returns SYNAX_OK or an error code (see above). */
+int synax_forward(const synax_problem* prob, void* maps_dev, void* stream);
+
+/* Bytes of device workspace synax_adjoint needs for `prob` (written to *bytes). */
+int synax_adjoint_workspace_bytes(const synax_problem* prob, size_t* bytes);
+
+/* Adjoint (reverse-mode) march: the gradient of a scalar of the maps with
+ * respect to theta, computed by recomputing each ray from theta (no per-step
+ * storage) and marching it backwards for the RM adjoint (Eq. 7 is a prefix
+ * sum along the ray, so its adjoint is a suffix sum).  Models: WMAP, JF12.
+ *
+ * Two modes:
+ *  - VJP mode, gmaps_dev != NULL: grad = sum_{f,s,i} gmaps[f][s][i] dM[f][s][i]/dtheta.
+ *    target_dev and chi2_dev are ignored.
+ *  - chi^2 mode, gmaps_dev == NULL: target_dev [n_freq][3][pix_count] must be
+ *    given; grad = d chi^2 / d theta with chi^2 = sum (M - target)^2 / sigma_K^2
+ *    (-2 log L of Eq. 15 up to a constant), and *chi2_dev receives chi^2
+ *    when chi2_dev != NULL.
+ * grad_dev: n_theta doubles (overwritten).  maps_dev: optional; when non-NULL
+ * it receives the forward maps M.  gmaps/target/maps are float32 (float64
+ * with SYNAX_F64).  workspace_dev: at least synax_adjoint_workspace_bytes
+ * bytes of device memory (SYNAX_ESPACE otherwise); its contents are scratch.
+ * The reduction over pixels is performed in a fixed order, so results are
+ * bitwise reproducible for a given problem and device. */
+int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
+                  double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
+                  void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Field models evaluated at arbitrary points (diagnostics and unit tests of
+ * the device field code, which is the code the march runs).
+ * pos_dev: [n][3] doubles (kpc, galactocentric); t_dev: [n] doubles, the
+ * distance of each point from the observer (used by the toy model's sphere);
+ * out_dev: [n][5] doubles = (Bx, By, Bz in uG, N0, n_e in cm^-3).  Inputs are
+ * rounded to the march precision (FP32 unless SYNAX_F64) before evaluation. */
+int synax_eval_fields(const synax_problem* prob, const double* pos_dev, const double* t_dev,
+                      int64_t n, double* out_dev, void* stream);
+
+/* Last CUDA error code seen by this thread in a call that returned SYNAX_ECUDA. */
+int synax_last_cuda_error(void);
+
+/* Static description of an error code. */
+const char* synax_strerror(int status);
+
+/* ABI version (major * 100 + minor). */
+int synax_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYNAX_H */

@@ -101,6 +101,11 @@ def _load():
                                            ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_int]
             lib.oracle_forward.restype = ctypes.c_int
+            lib.oracle_fields_batch.argtypes = [ctypes.POINTER(_OracleProblem), ctypes.c_int64,
+                                                ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_double)]
+            lib.oracle_fields_batch.restype = ctypes.c_int
             lib.oracle_ray_length.argtypes = [ctypes.POINTER(_OracleProblem), ctypes.c_int64]
             lib.oracle_ray_length.restype = ctypes.c_double
             _lib = lib
@@ -199,6 +204,20 @@ def fields(prob, r, t: float = 0.0):
     if _load().oracle_fields(ctypes.byref(s), rr, float(t), B, ctypes.byref(n0), ctypes.byref(ne)) != 0:
         raise ValueError("bad model")
     return np.array(B[:]), n0.value, ne.value
+
+
+def fields_batch(prob, r, t) -> np.ndarray:
+    """Fields at many points: r [n, 3] kpc, t [n] observer distances ->
+    [n, 5] = (Bx, By, Bz, N0, n_e)."""
+    s = _to_struct(prob)
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(-1, 3))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1))
+    out = np.zeros((r.shape[0], 5), dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    if _load().oracle_fields_batch(ctypes.byref(s), r.shape[0], r.ctypes.data_as(dp),
+                                   t.ctypes.data_as(dp), out.ctypes.data_as(dp)) != 0:
+        raise ValueError("bad model")
+    return out
 
 
 def emissivity(nu: float, p: float, b_trans_gauss: float, n0: float) -> tuple[float, float]:

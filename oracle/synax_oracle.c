@@ -233,8 +233,10 @@ static void field_wmap(const double* th, const double r[3], const double obs[3],
  *   disc: 8 log-spiral arms, pitch i = 11.5 deg, reference radius 5 kpc.
  *     Arm coordinate u = 8 (phi - ln(rho/5)/tan i) / (2 pi) mod 8; arm k
  *     covers u in [k, k+1); weights w_k(u) = S((d+delta)/(2delta))
- *     - S((d-1+delta)/(2delta)), d = u - k wrapped to [-4, 4), delta = 0.1,
- *     S the cubic smoothstep; beta(u) = sum_k b_k w_k(u).
+ *     - S((d-1+delta)/(2delta)), d = u - k wrapped to [-4, 4), delta = 1/2,
+ *     S the cubic smoothstep; beta(u) = sum_k b_k w_k(u): the strength is
+ *     b_k at the arm centre u = k + 1/2 and is interpolated C^1 between
+ *     neighbouring centres.
  *     B_disc = beta (5/rho) W(rho) (1 - L(z; 0.4, 0.27)) (sin i rho^ + cos i phi^),
  *     W(rho) = S((rho - 4.75)/0.5) S((20.25 - rho)/0.5).
  *   toroidal halo: B_h e^{-|z|/z_h} L(z; 0.4, 0.27) (1 - L(rho; 9.22, 0.2)) s(z) phi^,
@@ -261,7 +263,7 @@ static void field_jf12(const double* th, const double r[3], const double obs[3],
         double phi0 = phi - log(rho / 5.0) / tan(pitch);
         double u = fmod(8.0 * phi0 / (2.0 * OR_PI), 8.0);
         if (u < 0.0) u += 8.0;
-        double beta = 0.0, delta = 0.1;
+        double beta = 0.0, delta = 0.5;
         for (int k = 0; k < 8; ++k) {
             double d = u - (double)k;
             if (d >= 4.0) d -= 8.0;
@@ -476,6 +478,23 @@ int oracle_forward(const oracle_problem* P, const int64_t* pix, int64_t n_pix,
     for (int t = 1; t < n_threads; ++t) pthread_create(&tids[t], NULL, or_worker, &jobs[t]);
     or_worker(&jobs[0]);
     for (int t = 1; t < n_threads; ++t) pthread_join(tids[t], NULL);
+    return 0;
+}
+
+/* Field evaluation at n points (positions r[3n], observer distances t[n]) for
+ * unit tests: out[5i..5i+4] = B (3), N0, n_e. */
+int oracle_fields_batch(const oracle_problem* P, int64_t n, const double* r, const double* t,
+                        double* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double B[3], N0, ne;
+        if (oracle_fields(P, r + 3 * i, t[i], B, &N0, &ne) != 0) return -1;
+        out[5 * i + 0] = B[0];
+        out[5 * i + 1] = B[1];
+        out[5 * i + 2] = B[2];
+        out[5 * i + 3] = N0;
+        out[5 * i + 4] = ne;
+    }
     return 0;
 }
 

@@ -1,1 +1,162 @@
-"""GB300-native synchrotron ray march (synax, arXiv 2410.01136) -- placeholder."""
+"""GB300-native synchrotron ray march (synax, arXiv 2410.01136).
+
+Python surface of libsynax (include/synax.h).  PyTorch provides device memory
+and streams; every step of the march runs in the library's CUDA kernels.
+
+    from paper_2410_01136_gb300 import forward, adjoint, SynaxMaps, inputs
+    prob = inputs.config2()
+    maps = forward(prob)                 # [F, 3, n_pix] on the current CUDA device
+
+There is no CPU path: without the built library (``build()``) or without a
+CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import inputs
+from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
+
+__all__ = ["forward", "adjoint", "eval_fields", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
+           "SynaxError"]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force, verbose=verbose)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libsynax needs a CUDA device; none is available")
+    return torch
+
+
+def _stream_handle(torch, stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+def _map_dtype(torch, prob):
+    return torch.float64 if getattr(prob, "f64", False) else torch.float32
+
+
+def _check_map_tensor(torch, t, prob, name):
+    shape = (prob.n_freq, 3, prob.n_pix_out)
+    if not t.is_cuda or t.dtype != _map_dtype(torch, prob) or tuple(t.shape) != shape \
+            or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {_map_dtype(torch, prob)} tensor of "
+                         f"shape {shape}")
+
+
+def forward(prob, out=None, stream=None):
+    """March all pixels of `prob` (Sec. 2.3) and return the [F, 3, n_pix]
+    brightness-temperature maps (I, Q, U) as a CUDA tensor."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty((prob.n_freq, 3, prob.n_pix_out), dtype=_map_dtype(torch, prob),
+                          device="cuda")
+    else:
+        _check_map_tensor(torch, out, prob, "out")
+    s = problem_struct(prob)
+    check(lib().synax_forward(ctypes.byref(s), ctypes.c_void_p(out.data_ptr()),
+                              _stream_handle(torch, stream)), "synax_forward")
+    return out
+
+
+def eval_fields(prob, pos, t, stream=None):
+    """B (uG), N0, n_e (cm^-3) of prob's model at positions pos [n, 3] (kpc) with
+    observer distances t [n], evaluated by the march's device code; returns a
+    [n, 5] float64 CUDA tensor."""
+    torch = _torch()
+    pos = torch.as_tensor(pos, dtype=torch.float64, device="cuda").reshape(-1, 3).contiguous()
+    t = torch.as_tensor(t, dtype=torch.float64, device="cuda").reshape(-1).contiguous()
+    out = torch.empty((pos.shape[0], 5), dtype=torch.float64, device="cuda")
+    s = problem_struct(prob)
+    check(lib().synax_eval_fields(ctypes.byref(s), ctypes.c_void_p(pos.data_ptr()),
+                                  ctypes.c_void_p(t.data_ptr()), pos.shape[0],
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(torch, stream)),
+          "synax_eval_fields")
+    return out
+
+
+def adjoint_workspace_bytes(prob) -> int:
+    s = problem_struct(prob)
+    n = ctypes.c_size_t(0)
+    check(lib().synax_adjoint_workspace_bytes(ctypes.byref(s), ctypes.byref(n)),
+          "synax_adjoint_workspace_bytes")
+    return int(n.value)
+
+
+def adjoint(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=None, workspace=None,
+            stream=None):
+    """Gradient with respect to theta (a float64 CUDA tensor of n_theta values).
+
+    VJP mode (gmaps given): sum(gmaps * dM/dtheta).  chi^2 mode (target given):
+    d chi^2 / d theta with chi^2 = sum((M - target)^2) / sigma^2; returns
+    (grad, chi2) in that mode.  maps_out optionally receives M.
+    """
+    torch = _torch()
+    if (gmaps is None) == (target is None):
+        raise ValueError("give exactly one of gmaps (VJP mode) or target (chi^2 mode)")
+    seed = gmaps if gmaps is not None else target
+    _check_map_tensor(torch, seed, prob, "gmaps" if gmaps is not None else "target")
+    if maps_out is not None:
+        _check_map_tensor(torch, maps_out, prob, "maps_out")
+    nbytes = adjoint_workspace_bytes(prob)
+    if workspace is None:
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    grad = torch.empty(len(prob.theta), dtype=torch.float64, device="cuda")
+    chi2 = torch.empty(1, dtype=torch.float64, device="cuda") if target is not None else None
+    s = problem_struct(prob)
+    check(lib().synax_adjoint(
+        ctypes.byref(s),
+        ctypes.c_void_p(gmaps.data_ptr() if gmaps is not None else 0),
+        ctypes.c_void_p(target.data_ptr() if target is not None else 0),
+        ctypes.c_double(float(sigma)),
+        ctypes.c_void_p(grad.data_ptr()),
+        ctypes.c_void_p(chi2.data_ptr() if chi2 is not None else 0),
+        ctypes.c_void_p(maps_out.data_ptr() if maps_out is not None else 0),
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+        _stream_handle(torch, stream)), "synax_adjoint")
+    if target is not None:
+        return grad, chi2
+    return grad
+
+
+class SynaxMaps:
+    """torch.autograd.Function over the march: maps = SynaxMaps.apply(theta, prob).
+
+    theta: float64 tensor (CPU or CUDA) of the model parameters; the maps come
+    back on the current CUDA device.  backward() calls the library's adjoint
+    in VJP mode with the incoming map gradient.
+    """
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, theta, prob):
+        if cls._fn is None:
+            cls._fn = _make_function()
+        return cls._fn.apply(theta, prob)
+
+
+def _make_function():
+    import torch
+
+    class _SynaxMapsFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, prob):
+            th = theta.detach().to("cpu", torch.float64).numpy()
+            p = prob.with_theta(th)
+            ctx.prob = p
+            ctx.theta_device = theta.device
+            return forward(p)
+
+        @staticmethod
+        def backward(ctx, gmaps):
+            g = adjoint(ctx.prob, gmaps=gmaps.contiguous())
+            return g.to(ctx.theta_device), None
+
+    return _SynaxMapsFn

@@ -1,0 +1,138 @@
+"""ctypes binding of libsynax (include/synax.h): argument marshalling only.
+
+Every step of the march runs in the CUDA library; this module copies a
+``Problem`` into the C struct, passes raw device pointers and the current
+torch stream, and turns negative status codes into exceptions.  There is no
+CPU fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libsynax.so")
+
+SYNAX_OK = 0
+SYNAX_EINVAL = -1
+SYNAX_ENONFINITE = -2
+SYNAX_ECUDA = -3
+SYNAX_ENOMEM = -4
+SYNAX_ETIMEOUT = -5
+SYNAX_ENOTSUP = -6
+SYNAX_ESPACE = -7
+
+SYNAX_F64 = 1 << 0
+SYNAX_BOX_CLIP = 1 << 1
+
+MAX_FREQ = 16
+MAX_THETA = 32
+
+
+class SynaxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status
+
+
+class SynaxProblem(ctypes.Structure):
+    _fields_ = [
+        ("nside", ctypes.c_int32),
+        ("n_steps", ctypes.c_int32),
+        ("r_max_kpc", ctypes.c_double),
+        ("box_kpc", ctypes.c_double * 3),
+        ("obs_kpc", ctypes.c_double * 3),
+        ("n_freq", ctypes.c_int32),
+        ("freq_hz", ctypes.c_double * MAX_FREQ),
+        ("model_id", ctypes.c_int32),
+        ("n_theta", ctypes.c_int32),
+        ("theta", ctypes.c_double * MAX_THETA),
+        ("flags", ctypes.c_uint32),
+        ("rm_rule", ctypes.c_int32),
+        ("pix_begin", ctypes.c_int64),
+        ("pix_count", ctypes.c_int64),
+    ]
+
+
+#: Exported symbols of include/synax.h with (restype, argtypes).
+SIGNATURES = {
+    "synax_forward": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p, ctypes.c_void_p]),
+    "synax_adjoint_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(SynaxProblem),
+                                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "synax_adjoint": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p]),
+    "synax_eval_fields": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    "synax_last_cuda_error": (ctypes.c_int, []),
+    "synax_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "synax_version": (ctypes.c_int, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libsynax (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libsynax is not built ({LIB_PATH} missing); run "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` or "
+                    "`python paper_2410_01136_gb300/build.py`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str) -> None:
+    if status == SYNAX_OK:
+        return
+    L = lib()
+    msg = L.synax_strerror(status).decode()
+    if status == SYNAX_ECUDA:
+        msg += f" (cudaError {L.synax_last_cuda_error()})"
+    raise SynaxError(status, f"{what}: {msg} [{status}]")
+
+
+def problem_struct(prob) -> SynaxProblem:
+    """Copy a Problem (paper_2410_01136_gb300.inputs.Problem or any object with
+    the same fields) into the C struct."""
+    s = SynaxProblem()
+    s.nside = int(prob.nside)
+    s.n_steps = int(prob.n_steps)
+    s.r_max_kpc = float(prob.r_max_kpc)
+    for k in range(3):
+        s.box_kpc[k] = float(prob.box_kpc[k])
+        s.obs_kpc[k] = float(prob.obs_kpc[k])
+    freqs = list(prob.freq_hz)
+    if len(freqs) > MAX_FREQ:
+        raise ValueError(f"at most {MAX_FREQ} frequencies")
+    s.n_freq = len(freqs)
+    for k, f in enumerate(freqs):
+        s.freq_hz[k] = float(f)
+    s.model_id = int(prob.model_id)
+    th = [float(x) for x in prob.theta]
+    if len(th) > MAX_THETA:
+        raise ValueError(f"at most {MAX_THETA} parameters")
+    s.n_theta = len(th)
+    for k, x in enumerate(th):
+        s.theta[k] = x
+    s.flags = (SYNAX_F64 if getattr(prob, "f64", False) else 0) | (
+        SYNAX_BOX_CLIP if getattr(prob, "box_clip", False) else 0)
+    s.rm_rule = int(getattr(prob, "rm_rule", 0))
+    s.pix_begin = int(getattr(prob, "pix_begin", 0))
+    s.pix_count = int(getattr(prob, "pix_count", 0))
+    return s

@@ -1,0 +1,353 @@
+// abi.cu -- the extern "C" boundary of libsynax (declared in include/synax.h).
+//
+// Responsibilities: validate a synax_problem on the host (nothing is enqueued
+// for an invalid one), derive every constant of the march in double
+// precision, pack them into MapParams<R>, and dispatch to the kernels.
+//
+// Host-side constant derivation (per frequency nu_f, spectral index p):
+//   Eq. 2:  j_I = sqrt(3) q^3 B N0 / (8 pi m c^2) (4 pi nu m c / (3 q B))^{(1-p)/2}
+//                 2^{(p+1)/2} / (p+1) Gamma(p/4 - 1/12) Gamma(p/4 + 19/12)
+//   Eq. 5:  j_P = same prefactor 2^{(p-3)/2} Gamma(p/4 - 1/12) Gamma(p/4 + 7/12)
+//   With B in uG: j = A N0 (B_uG^2)^{(p+1)/4}, A absorbing (1e-6)^{(p+1)/2}.
+//   I dr (cgs) -> K:  x kpc_cm x c^2 / (2 k nu^2)  (Rayleigh-Jeans)
+//   Eq. 6-7: phase 2 lambda^2 RM with RM = K_RM sum n_e B_par dr (cgs);
+//            per (cm^-3 uG kpc): c_f = 2 lambda^2 K_RM 1e-6 kpc_cm rad,
+//            stored in revolutions (c_f / 2 pi) as a double-float.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "synax_internal.h"
+
+namespace synax {
+
+namespace {
+// CODATA 2018, cgs
+constexpr double kC = 2.99792458e10;
+constexpr double kQe = 4.803204712570263e-10;
+constexpr double kMe = 9.1093837015e-28;
+constexpr double kKb = 1.380649e-16;
+constexpr double kKpc = 3.0856775814913673e21;
+constexpr double kMicroGauss = 1.0e-6;
+constexpr double kPiD = 3.141592653589793238;
+
+thread_local int g_last_cuda_error = 0;
+
+int model_n_theta(int id) {
+    switch (id) {
+    case SYNAX_MODEL_TOY: return 7;
+    case SYNAX_MODEL_WMAP: return 8;
+    case SYNAX_MODEL_JF12: return 16;
+    default: return -1;
+    }
+}
+
+int model_p_index(int id) {
+    switch (id) {
+    case SYNAX_MODEL_TOY: return 5;
+    case SYNAX_MODEL_WMAP: return 6;
+    default: return 13;
+    }
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// CR density profile of the WMAP form (Sec. 3.1, Eq. 12) without its
+// normalisation: e^{-rho/5} sech^2(z/1).
+double cr_profile(const double r[3]) {
+    const double rho = std::hypot(r[0], r[1]);
+    const double ch = std::cosh(r[2]);
+    return std::exp(-rho / 5.0) / (ch * ch);
+}
+
+}  // namespace
+
+int record_cuda_error(int err) {
+    g_last_cuda_error = err;
+    return SYNAX_ECUDA;
+}
+
+// Digamma for x > 0: upward recurrence to x >= 8, then the asymptotic series
+// psi(x) ~ ln x - 1/(2x) - sum_k B_{2k} / (2k x^{2k}) (Abramowitz & Stegun 6.3.18).
+double digamma(double x) {
+    double acc = 0.0;
+    while (x < 8.0) {
+        acc -= 1.0 / x;
+        x += 1.0;
+    }
+    const double x2 = 1.0 / (x * x);
+    const double series =
+        x2 * (1.0 / 12 - x2 * (1.0 / 120 - x2 * (1.0 / 252 - x2 * (1.0 / 240 - x2 * (1.0 / 132)))));
+    return acc + std::log(x) - 0.5 / x - series;
+}
+
+// Validates a problem; on success *n_pix receives the number of pixels marched.
+int validate_problem(const synax_problem* P, long long* n_pix) {
+    if (!P) return SYNAX_EINVAL;
+    if (!is_pow2(P->nside) || P->nside > 8192) return SYNAX_EINVAL;
+    if (P->n_steps < 1 || P->n_steps > 65536) return SYNAX_EINVAL;
+    if (P->n_freq < 1 || P->n_freq > SYNAX_MAX_FREQ) return SYNAX_EINVAL;
+    if (P->flags & ~(SYNAX_F64 | SYNAX_BOX_CLIP)) return SYNAX_EINVAL;
+    if (P->rm_rule < 0 || P->rm_rule > 2) return SYNAX_EINVAL;
+    const int nt = model_n_theta(P->model_id);
+    if (nt < 0 || P->n_theta != nt) return SYNAX_EINVAL;
+    for (int k = 0; k < P->n_theta; ++k)
+        if (!is_finite(P->theta[k])) return SYNAX_ENONFINITE;
+    for (int k = 0; k < P->n_freq; ++k) {
+        if (!is_finite(P->freq_hz[k])) return SYNAX_ENONFINITE;
+        if (!(P->freq_hz[k] > 0.0)) return SYNAX_EINVAL;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!is_finite(P->obs_kpc[k])) return SYNAX_ENONFINITE;
+    if (P->flags & SYNAX_BOX_CLIP) {
+        for (int k = 0; k < 3; ++k) {
+            if (!is_finite(P->box_kpc[k])) return SYNAX_ENONFINITE;
+            if (!(P->box_kpc[k] > 0.0)) return SYNAX_EINVAL;
+            if (!(std::fabs(P->obs_kpc[k]) < 0.5 * P->box_kpc[k])) return SYNAX_EINVAL;
+        }
+    } else {
+        if (!is_finite(P->r_max_kpc)) return SYNAX_ENONFINITE;
+        if (!(P->r_max_kpc > 0.0)) return SYNAX_EINVAL;
+    }
+    const double p = P->theta[model_p_index(P->model_id)];
+    if (!(p > 1.0 / 3.0 && p < 20.0)) return SYNAX_EINVAL;
+    if (P->model_id == SYNAX_MODEL_TOY && !(P->theta[6] >= 0.0)) return SYNAX_EINVAL;
+    if (P->model_id == SYNAX_MODEL_JF12) {
+        if (!(P->theta[9] > 0.0) || !(P->theta[14] > 0.0) || !(P->theta[15] > 0.0)) return SYNAX_EINVAL;
+        if (!(P->theta[11] > 0.0 && P->theta[11] < 0.5 * kPiD)) return SYNAX_EINVAL;
+    }
+    const long long npix = 12LL * P->nside * P->nside;
+    if (P->pix_begin < 0 || P->pix_begin > npix || P->pix_count < 0) return SYNAX_EINVAL;
+    const long long count = P->pix_count ? P->pix_count : npix - P->pix_begin;
+    if (P->pix_begin + count > npix) return SYNAX_EINVAL;
+    *n_pix = count;
+    return SYNAX_OK;
+}
+
+static void set_phase(float& hi_out, float& lo_out, double v) {
+    const float hi = (float)v;
+    hi_out = hi;
+    lo_out = (float)(v - (double)hi);
+}
+static void store_phase(ff& out, double v) { set_phase(out.hi, out.lo, v); }
+static void store_phase(double& out, double v) { out = v; }
+
+// Per-frequency physical prefactors (double).  aI, aP: K per (cm^-3 uG^{(p+1)/2}
+// kpc); crev: revolutions per (cm^-3 uG kpc); dlnaI/dp, dlnaP/dp for the adjoint.
+struct FreqConsts {
+    double aI, aP, crev, dlnaI, dlnaP;
+};
+
+static FreqConsts freq_consts(double nu, double p) {
+    FreqConsts F;
+    const double pre = std::sqrt(3.0) * kQe * kQe * kQe / (8.0 * kPiD * kMe * kC * kC);
+    const double X = 4.0 * kPiD * nu * kMe * kC / (3.0 * kQe);   // times 1/B
+    const double g1 = std::tgamma(p / 4.0 - 1.0 / 12.0);
+    const double base = pre * std::pow(X, 0.5 * (1.0 - p)) * std::pow(kMicroGauss, 0.5 * (p + 1.0));
+    const double toT = kKpc * kC * kC / (2.0 * kKb * nu * nu);
+    F.aI = base * std::pow(2.0, 0.5 * (p + 1.0)) / (p + 1.0) * g1 * std::tgamma(p / 4.0 + 19.0 / 12.0) * toT;
+    F.aP = base * std::pow(2.0, 0.5 * (p - 3.0)) * g1 * std::tgamma(p / 4.0 + 7.0 / 12.0) * toT;
+    const double lam = kC / nu;
+    const double K = kQe * kQe * kQe / (2.0 * kPiD * kMe * kMe * kC * kC * kC * kC);
+    F.crev = 2.0 * lam * lam * K * kMicroGauss * kKpc / (2.0 * kPiD);
+    const double common = -0.5 * std::log(X) + 0.5 * std::log(kMicroGauss) + 0.5 * std::log(2.0) +
+                          0.25 * digamma(p / 4.0 - 1.0 / 12.0);
+    F.dlnaI = common - 1.0 / (p + 1.0) + 0.25 * digamma(p / 4.0 + 19.0 / 12.0);
+    F.dlnaP = common + 0.25 * digamma(p / 4.0 + 7.0 / 12.0);
+    return F;
+}
+
+template <typename R>
+void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
+    std::memset(&M, 0, sizeof(M));
+    M.nside = P.nside;
+    M.n_steps = P.n_steps;
+    M.n_freq = P.n_freq;
+    M.model = P.model_id;
+    M.pix_begin = P.pix_begin;
+    M.n_pix = n_pix;
+    M.box_clip = (P.flags & SYNAX_BOX_CLIP) ? 1 : 0;
+    M.w_own = R(P.rm_rule == 1 ? 0.0 : (P.rm_rule == 2 ? 1.0 : 0.5));
+    for (int k = 0; k < 3; ++k) {
+        M.obs[k] = R(P.obs_kpc[k]);
+        M.obs_lo[k] = R(P.obs_kpc[k] - (double)R(P.obs_kpc[k]));
+        M.box_half[k] = R(0.5 * P.box_kpc[k]);
+    }
+    const double dr = P.r_max_kpc / P.n_steps;
+    M.r_max = R(P.r_max_kpc);
+    M.dr = R(dr);
+    M.dr_lo = R(dr - (double)R(dr));
+    const double p = P.theta[model_p_index(P.model_id)];
+    M.q = R((p - 3.0) / 4.0);
+    for (int f = 0; f < P.n_freq; ++f) {
+        const FreqConsts F = freq_consts(P.freq_hz[f], p);
+        M.aI[f] = R(F.aI);
+        M.aP[f] = R(F.aP);
+        store_phase(M.crev[f], F.crev);
+        store_phase(M.cdr[f], F.crev * dr);
+    }
+    const double* th = P.theta;
+    switch (P.model_id) {
+    case SYNAX_MODEL_TOY:
+        M.m[mc::TOY_B + 0] = R(th[0]);
+        M.m[mc::TOY_B + 1] = R(th[1]);
+        M.m[mc::TOY_B + 2] = R(th[2]);
+        M.m[mc::TOY_NE] = R(th[3]);
+        M.m[mc::TOY_N0] = R(th[4]);
+        M.m[mc::TOY_R0] = R(th[6]);
+        break;
+    case SYNAX_MODEL_WMAP:
+        M.m[mc::W_B0] = R(th[0]);
+        M.m[mc::W_PSI0] = R(th[1]);
+        M.m[mc::W_PSI1] = R(th[2]);
+        M.m[mc::W_CHI0] = R(th[3]);
+        M.m[mc::W_BUX] = R(th[4]);
+        M.m[mc::W_N0N] = R(th[5] / cr_profile(P.obs_kpc));
+        M.m[mc::W_NE0] = R(th[7]);
+        break;
+    case SYNAX_MODEL_JF12:
+        for (int k = 0; k < 8; ++k) M.m[mc::J_B + k] = R(th[k]);
+        M.m[mc::J_BH] = R(th[8]);
+        M.m[mc::J_IZH] = R(1.0 / th[9]);
+        M.m[mc::J_BX] = R(th[10]);
+        M.m[mc::J_COSX] = R(std::cos(th[11]));
+        M.m[mc::J_SINX] = R(std::sin(th[11]));
+        M.m[mc::J_COTX] = R(1.0 / std::tan(th[11]));
+        M.m[mc::J_N0N] = R(th[12] / cr_profile(P.obs_kpc));
+        M.m[mc::J_IH1] = R(1.0 / th[14]);
+        M.m[mc::J_IH2] = R(1.0 / th[15]);
+        M.m[mc::J_ZH] = R(th[9]);
+        M.m[mc::J_THX] = R(th[11]);
+        M.m[mc::J_H1] = R(th[14]);
+        M.m[mc::J_H2] = R(th[15]);
+        M.m[mc::J_N0OBS] = R(th[12]);
+        M.m[mc::J_SIN2X] = R(1.0 / (std::sin(th[11]) * std::sin(th[11])));
+        break;
+    default: break;
+    }
+}
+
+template <typename R>
+void fill_adj(const synax_problem& P, AdjParams<R>& A) {
+    std::memset(&A, 0, sizeof(A));
+    const double p = P.theta[model_p_index(P.model_id)];
+    for (int f = 0; f < P.n_freq; ++f) {
+        const FreqConsts F = freq_consts(P.freq_hz[f], p);
+        A.dlnaI_dp[f] = R(F.dlnaI);
+        A.dlnaP_dp[f] = R(F.dlnaP);
+    }
+    A.n_theta = P.n_theta;
+}
+
+template void fill_params<float>(const synax_problem&, long long, MapParams<float>&);
+template void fill_params<double>(const synax_problem&, long long, MapParams<double>&);
+template void fill_adj<float>(const synax_problem&, AdjParams<float>&);
+template void fill_adj<double>(const synax_problem&, AdjParams<double>&);
+
+}  // namespace synax
+
+using namespace synax;
+
+extern "C" {
+
+int synax_forward(const synax_problem* prob, void* maps_dev, void* stream) {
+    long long n_pix = 0;
+    const int rc = validate_problem(prob, &n_pix);
+    if (rc != SYNAX_OK) return rc;
+    if (n_pix == 0) return SYNAX_OK;
+    if (!maps_dev) return SYNAX_EINVAL;
+    if (prob->flags & SYNAX_F64) {
+        MapParams<double> M;
+        fill_params<double>(*prob, n_pix, M);
+        return launch_forward_f64(M, maps_dev, stream);
+    }
+    MapParams<float> M;
+    fill_params<float>(*prob, n_pix, M);
+    return launch_forward_f32(M, maps_dev, stream);
+}
+
+int synax_adjoint_workspace_bytes(const synax_problem* prob, size_t* bytes) {
+    long long n_pix = 0;
+    const int rc = validate_problem(prob, &n_pix);
+    if (rc != SYNAX_OK) return rc;
+    if (!bytes) return SYNAX_EINVAL;
+    *bytes = adjoint_workspace_bytes(n_pix, prob->n_theta);
+    return SYNAX_OK;
+}
+
+int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
+                  double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
+                  void* workspace_dev, size_t workspace_bytes, void* stream) {
+    long long n_pix = 0;
+    const int rc = validate_problem(prob, &n_pix);
+    if (rc != SYNAX_OK) return rc;
+    if (prob->model_id == SYNAX_MODEL_TOY) return SYNAX_ENOTSUP;
+    if (!grad_dev) return SYNAX_EINVAL;
+    const bool chi2_mode = gmaps_dev == nullptr;
+    if (chi2_mode) {
+        if (!target_dev) return SYNAX_EINVAL;
+        if (!is_finite(sigma_K)) return SYNAX_ENONFINITE;
+        if (!(sigma_K > 0.0)) return SYNAX_EINVAL;
+    }
+    const size_t need = adjoint_workspace_bytes(n_pix, prob->n_theta);
+    if (workspace_bytes < need || (need > 0 && !workspace_dev)) return SYNAX_ESPACE;
+    if (prob->flags & SYNAX_F64) {
+        MapParams<double> M;
+        AdjParams<double> A;
+        fill_params<double>(*prob, n_pix, M);
+        fill_adj<double>(*prob, A);
+        A.mode_chi2 = chi2_mode ? 1 : 0;
+        A.inv_sigma2 = chi2_mode ? 1.0 / (sigma_K * sigma_K) : 0.0;
+        return launch_adjoint_f64(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
+                                  maps_dev, workspace_dev, stream);
+    }
+    MapParams<float> M;
+    AdjParams<float> A;
+    fill_params<float>(*prob, n_pix, M);
+    fill_adj<float>(*prob, A);
+    A.mode_chi2 = chi2_mode ? 1 : 0;
+    A.inv_sigma2 = chi2_mode ? (float)(1.0 / (sigma_K * sigma_K)) : 0.0f;
+    return launch_adjoint_f32(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
+                              maps_dev, workspace_dev, stream);
+}
+
+int synax_eval_fields(const synax_problem* prob, const double* pos_dev, const double* t_dev,
+                      int64_t n, double* out_dev, void* stream) {
+    long long n_pix = 0;
+    const int rc = validate_problem(prob, &n_pix);
+    if (rc != SYNAX_OK) return rc;
+    if (n < 0) return SYNAX_EINVAL;
+    if (n == 0) return SYNAX_OK;
+    if (!pos_dev || !t_dev || !out_dev) return SYNAX_EINVAL;
+    if (prob->flags & SYNAX_F64) {
+        MapParams<double> M;
+        fill_params<double>(*prob, n_pix, M);
+        return launch_eval_fields_f64(M, pos_dev, t_dev, n, out_dev, stream);
+    }
+    MapParams<float> M;
+    fill_params<float>(*prob, n_pix, M);
+    return launch_eval_fields_f32(M, pos_dev, t_dev, n, out_dev, stream);
+}
+
+int synax_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* synax_strerror(int status) {
+    switch (status) {
+    case SYNAX_OK: return "success";
+    case SYNAX_EINVAL: return "invalid problem or argument";
+    case SYNAX_ENONFINITE: return "non-finite parameter, frequency or position";
+    case SYNAX_ECUDA: return "CUDA runtime error";
+    case SYNAX_ENOMEM: return "device allocation failed";
+    case SYNAX_ETIMEOUT: return "bounded device-side wait timed out";
+    case SYNAX_ENOTSUP: return "operation not supported for this model";
+    case SYNAX_ESPACE: return "workspace too small";
+    default: return "unknown status";
+    }
+}
+
+int synax_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// forward.cu -- forward ray-march kernel (Sec. 2.3, Eq. 2 and 5-9).
+//
+// Work decomposition: one warp per sightline, 8 sightlines per 256-thread
+// CTA.  The N_int midpoints of a ray are split into 32 contiguous chunks,
+// one per lane.  Each lane marches its chunk once, evaluating the fields and
+// emissivities, and keeps:
+//   * sum of j_I over its samples (I does not depend on RM);
+//   * per frequency, sum of j_P e^{2i chi_0} e^{2i lambda^2 RM_local}, where
+//     RM_local is the RM accumulated from the start of the lane's chunk;
+//   * the chunk total S_lane of f = n_e B_par (double-float).
+// A warp exclusive scan of S_lane gives every lane its RM offset O (the RM
+// of all earlier chunks); because e^{i(a + b)} = e^{ia} e^{ib}, rotating the
+// lane's complex partial sums by e^{2i lambda^2 K O} makes the split exact,
+// with no per-step storage.  A butterfly reduction then sums the lanes, and
+// the CTA stages its 8 rays in shared memory so that every (frequency,
+// Stokes) row is written as one contiguous 32-byte run.
+//
+// The RM sum and the Faraday phases are double-float in the FP32 path: the
+// phase 2 lambda^2 RM reaches ~10^3 rad at 408 MHz, and it must be known to
+// ~1e-6 rad for the 1e-4 Q/U tolerance.  Phases are carried in revolutions
+// so that the integer part is removed exactly before sin/cos.
+#include <cuda_runtime.h>
+
+#include "march.cuh"
+
+namespace synax {
+
+constexpr int kRaysPerCta = 8;
+constexpr int kThreads = 32 * kRaysPerCta;
+
+template <int MODEL, int NF, typename R>
+__global__ void __launch_bounds__(kThreads)
+k_forward(const MapParams<R> P, R* __restrict__ maps) {
+    using Ph = PhaseOps<R>;
+    using PT = typename Ph::T;
+    __shared__ R s_arms[8];
+    __shared__ R s_stage[3 * NF][kRaysPerCta];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x < 8) s_arms[threadIdx.x] = P.m[threadIdx.x];
+    __syncthreads();
+
+    const long long ray = (long long)blockIdx.x * kRaysPerCta + warp;
+    if (ray < P.n_pix) {
+        Los<R> L;
+        ff nd[3];
+        if constexpr (sizeof(R) == 4) healpix_los_dd(P.nside, P.pix_begin + ray, L, nd);
+        else healpix_los<R>(P.nside, P.pix_begin + ray, L);
+        const R dr = P.box_clip ? box_exit<R>(P.obs, P.box_half, L.n) / R(P.n_steps) : P.dr;
+        const R dr_lo = P.box_clip ? R(0) : P.dr_lo;
+        PT cd[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale(P.crev[k], dr) : P.cdr[k];
+
+        const int N = P.n_steps;
+        const int n0 = (int)(((long long)lane * N) >> 5);
+        const int n1 = (int)(((long long)(lane + 1) * N) >> 5);
+
+        R accI = R(0);
+        R zr[NF], zi[NF];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) { zr[k] = R(0); zi[k] = R(0); }
+        PT S = Ph::zero();
+        ArmTracker<R> trk;
+        if constexpr (MODEL == SYNAX_MODEL_JF12) {
+            if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
+        }
+
+        for (int n = n0; n < n1; ++n) {
+            if constexpr (MODEL == SYNAX_MODEL_JF12) {
+                if (n > n0) trk.step(+1);
+            }
+            const R nh = R(n) + R(0.5);
+            const R t = fma(nh, dr, nh * dr_lo);         // (n + 1/2) dr, dr as hi + lo
+            const R x = P.obs[0] + t * L.n[0];
+            const R y = P.obs[1] + t * L.n[1];
+            const R z = P.obs[2] + t * L.n[2];
+            R B[3], N0, ne;
+            ArmCoord<R> ac{0, R(0)};
+            if constexpr (MODEL == SYNAX_MODEL_JF12) ac = trk.coord(x, y, M<R>::sqrt(x * x + y * y));
+            Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne);
+            const Emit<R> e = emit<R>(B, N0, ne, L, P.q);
+            accI += e.jI;
+            const PT s_n = Ph::add(S, P.w_own * e.f);    // RM at the midpoint (Eq. 7)
+            S = Ph::add(S, e.f);
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                if (k < P.n_freq) {
+                    R sn, cs;
+                    M<R>::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
+                    zr[k] += e.pc * cs - e.ps * sn;       // (pc + i ps) e^{i phi}
+                    zi[k] += e.pc * sn + e.ps * cs;
+                }
+            }
+        }
+
+        // RM offset of this lane's chunk, then rotate its partial sums.
+        const PT O = warp_exclusive_scan<R>(S, lane);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            if (k < P.n_freq) {
+                R sn, cs;
+                M<R>::sincos_rev(Ph::frac_mul(cd[k], O), &sn, &cs);
+                const R a = zr[k] * cs - zi[k] * sn;
+                const R b = zr[k] * sn + zi[k] * cs;
+                zr[k] = a;
+                zi[k] = b;
+            }
+        }
+        accI = warp_sum<R>(accI);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            zr[k] = warp_sum<R>(zr[k]);
+            zi[k] = warp_sum<R>(zi[k]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                if (k < P.n_freq) {
+                    s_stage[3 * k + 0][warp] = P.aI[k] * dr * accI;
+                    s_stage[3 * k + 1][warp] = P.aP[k] * dr * zr[k];
+                    s_stage[3 * k + 2][warp] = P.aP[k] * dr * zi[k];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kRaysPerCta;
+    const int rows = 3 * P.n_freq;
+    for (int idx = threadIdx.x; idx < rows * kRaysPerCta; idx += kThreads) {
+        const int row = idx / kRaysPerCta;
+        const int col = idx - row * kRaysPerCta;
+        const long long r = base + col;
+        if (r < P.n_pix) maps[(long long)row * P.n_pix + r] = s_stage[row][col];
+    }
+}
+
+template <int MODEL, int NF, typename R>
+static int launch_nf(const MapParams<R>& P, R* maps, cudaStream_t st) {
+    const long long blocks = (P.n_pix + kRaysPerCta - 1) / kRaysPerCta;
+    k_forward<MODEL, NF, R><<<(unsigned)blocks, kThreads, 0, st>>>(P, maps);
+    const cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
+}
+
+template <int MODEL, typename R>
+static int launch_model(const MapParams<R>& P, R* maps, cudaStream_t st) {
+    const int F = P.n_freq;
+    if (F == 1) return launch_nf<MODEL, 1, R>(P, maps, st);
+    if (F == 2) return launch_nf<MODEL, 2, R>(P, maps, st);
+    if (F == 3) return launch_nf<MODEL, 3, R>(P, maps, st);
+    if (F == 4) return launch_nf<MODEL, 4, R>(P, maps, st);
+    if (F <= 8) return launch_nf<MODEL, 8, R>(P, maps, st);
+    return launch_nf<MODEL, 16, R>(P, maps, st);
+}
+
+template <typename R>
+static int launch_forward_t(const MapParams<R>& P, void* maps, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    R* out = (R*)maps;
+    switch (P.model) {
+    case SYNAX_MODEL_TOY: return launch_model<SYNAX_MODEL_TOY, R>(P, out, st);
+    case SYNAX_MODEL_WMAP: return launch_model<SYNAX_MODEL_WMAP, R>(P, out, st);
+    case SYNAX_MODEL_JF12: return launch_model<SYNAX_MODEL_JF12, R>(P, out, st);
+    default: return SYNAX_EINVAL;
+    }
+}
+
+int launch_forward_f32(const MapParams<float>& P, void* maps, void* stream) {
+    return launch_forward_t<float>(P, maps, stream);
+}
+
+int launch_forward_f64(const MapParams<double>& P, void* maps, void* stream) {
+    return launch_forward_t<double>(P, maps, stream);
+}
+
+}  // namespace synax

@@ -1,0 +1,654 @@
+// march.cuh -- device building blocks of the synchrotron ray march (sm_103a).
+//
+// Everything a kernel needs per ray and per sample:
+//   * fast FP32 transcendental primitives (PTX ex2/lg2/rcp/rsqrt/sin/cos
+//     .approx) and their FP64 counterparts, behind one traits type M<R>;
+//   * double-float arithmetic (Dekker/Knuth TwoSum, FMA-based products) for
+//     the running RM sum and the Faraday phase, PhaseOps<R>;
+//   * HEALPix RING pixel centres (Gorski et al. 2005) -> LOS triad n, e_l, e_b;
+//   * the three field models (toy, WMAP-type, JF12-type);
+//   * the per-sample emissivity terms of Eq. 2, 5, 8 and the RM integrand of Eq. 7.
+// The FP32 path folds all physical constants into host-computed per-frequency
+// prefactors so that every transcendental argument is O(1): B in uG,
+// lengths in kpc, densities in cm^-3.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ffmath.cuh"
+#include "synax_internal.h"
+
+namespace synax {
+
+constexpr double kLog2e = 1.4426950408889634;
+constexpr double kLn2 = 0.6931471805599453;
+constexpr double kPi = 3.141592653589793;
+
+// ---------------------------------------------------------------------------
+// FP32 approximate primitives (PTX ISA: ex2/lg2/rcp/rsqrt/sin/cos .approx.ftz.f32)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Math traits.  Two accuracy classes for FP32:
+//  * "accurate" (exp, log, div, sqrt, mulc): correctly rounded or libm
+//    (<= 2 ulp, unbiased), used for B and n_e, which feed the RM (Eq. 7).  At
+//    408 MHz the polarisation is ~560 times more sensitive to a systematic
+//    relative error of RM than to one of the emissivity, so the RM integrand
+//    must carry no bias beyond ~3e-8;
+//  * "fast" (exp2_fast, log2_fast, rcp_fast, rsqrt_fast, sincos_rev): PTX
+//    .approx, used for N0 and the B_perp power of Eq. 2/5 (magnitudes only)
+//    and for sin/cos of already-reduced phases.
+template <typename R> struct M;
+
+template <> struct M<float> {
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
+    static __device__ __forceinline__ float log(float x) { return logf(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt(float x) { return __fsqrt_rn(x); }
+    // x * c for a double constant c, with c split into two floats (hi + lo)
+    // so that the constant itself adds no systematic rounding.
+    static __device__ __forceinline__ float mulc(float x, double c) {
+        const float hi = (float)c;
+        const float lo = (float)(c - (double)hi);
+        return fmaf(x, hi, x * lo);
+    }
+    static __device__ __forceinline__ float exp2_fast(float x) { return ex2_approx(x); }
+    static __device__ __forceinline__ float log2_fast(float x) { return lg2_approx(x); }
+    static __device__ __forceinline__ float rcp_fast(float x) { return rcp_approx(x); }
+    static __device__ __forceinline__ float rsqrt_fast(float x) { return rsqrt_approx(x); }
+    static __device__ __forceinline__ float atan2(float y, float x) { return atan2f(y, x); }
+    static __device__ __forceinline__ float floor(float x) { return floorf(x); }
+    static __device__ __forceinline__ float abs(float x) { return fabsf(x); }
+    static __device__ __forceinline__ float min(float a, float b) { return fminf(a, b); }
+    static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
+    static __device__ __forceinline__ void sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+    static __device__ __forceinline__ void sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+    // sin and cos of 2 pi r, |r| <= 1/2 + eps
+    static __device__ __forceinline__ void sincos_rev(float r, float* s, float* c) {
+        float a = r * 6.2831853071795865f;
+        *s = sin_approx(a);
+        *c = cos_approx(a);
+    }
+};
+
+template <> struct M<double> {
+    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double log(double x) { return ::log(x); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double mulc(double x, double c) { return x * c; }
+    static __device__ __forceinline__ double exp2_fast(double x) { return ::exp2(x); }
+    static __device__ __forceinline__ double log2_fast(double x) { return ::log2(x); }
+    static __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double rsqrt_fast(double x) { return ::rsqrt(x); }
+    static __device__ __forceinline__ double atan2(double y, double x) { return ::atan2(y, x); }
+    static __device__ __forceinline__ double floor(double x) { return ::floor(x); }
+    static __device__ __forceinline__ double abs(double x) { return ::fabs(x); }
+    static __device__ __forceinline__ double min(double a, double b) { return ::fmin(a, b); }
+    static __device__ __forceinline__ double max(double a, double b) { return ::fmax(a, b); }
+    static __device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+    static __device__ __forceinline__ void sincospi(double x, double* s, double* c) { ::sincospi(x, s, c); }
+    static __device__ __forceinline__ void sincos_rev(double r, double* s, double* c) {
+        ::sincospi(2.0 * r, s, c);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (Knuth TwoSum, Dekker FastTwoSum, FMA TwoProd).
+// __fadd_rn / __fsub_rn are never contracted or reassociated.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return ff{s, e};
+}
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    ff s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+template <typename R> struct PhaseOps;
+
+template <> struct PhaseOps<float> {
+    using T = ff;
+    static __device__ __forceinline__ T zero() { return ff{0.f, 0.f}; }
+    static __device__ __forceinline__ T add(T a, float b) { return ff_add_f(a, b); }
+    static __device__ __forceinline__ T add(T a, T b) { return ff_add(a, b); }
+    static __device__ __forceinline__ T scale(T c, float d) {
+        float p = c.hi * d;
+        float e = fmaf(c.hi, d, -p);
+        e = fmaf(c.lo, d, e);
+        return fast_two_sum(p, e);
+    }
+    // Fractional part of c*s (revolutions), in [-1/2, 1/2] up to rounding.
+    // The product is formed exactly to ~2^-46 relative (TwoProd), the
+    // integer part is removed exactly (|hi| < 2^22), then the low parts added.
+    static __device__ __forceinline__ float frac_mul(T c, T s) {
+        float p = c.hi * s.hi;
+        float e = fmaf(c.hi, s.hi, -p);
+        e = fmaf(c.hi, s.lo, e);
+        e = fmaf(c.lo, s.hi, e);
+        float k = rintf(p);
+        return __fadd_rn(__fsub_rn(p, k), e);
+    }
+    static __device__ __forceinline__ T shfl_up(T v, int d) {
+        return ff{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+    }
+    static __device__ __forceinline__ T shfl_down(T v, int d) {
+        return ff{__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+    }
+    static __device__ __forceinline__ T neg(T v) { return ff{-v.hi, -v.lo}; }
+    static __device__ __forceinline__ float to_real(T v) { return v.hi + v.lo; }
+};
+
+template <> struct PhaseOps<double> {
+    using T = double;
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T scale(T c, double d) { return c * d; }
+    static __device__ __forceinline__ double frac_mul(T c, T s) {
+        double x = c * s;
+        return x - rint(x);
+    }
+    static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+    static __device__ __forceinline__ T shfl_down(T v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+    static __device__ __forceinline__ T neg(T v) { return -v; }
+    static __device__ __forceinline__ double to_real(T v) { return v; }
+};
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// Exclusive prefix sum of a per-lane phase value across the warp
+// (Kogge-Stone inclusive scan, then shift by one lane).
+template <typename R>
+__device__ __forceinline__ typename PhaseOps<R>::T warp_exclusive_scan(typename PhaseOps<R>::T v, int lane) {
+    using Ph = PhaseOps<R>;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        auto o = Ph::shfl_up(v, d);
+        if (lane >= d) v = Ph::add(v, o);
+    }
+    auto e = Ph::shfl_up(v, 1);
+    return lane == 0 ? Ph::zero() : e;
+}
+
+// Exclusive suffix sum (sum over higher lanes) of a plain value.
+template <typename R>
+__device__ __forceinline__ R warp_exclusive_suffix(R v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        R o = __shfl_down_sync(0xffffffffu, v, d);
+        if (lane + d < 32) v += o;
+    }
+    R e = __shfl_down_sync(0xffffffffu, v, 1);
+    return lane == 31 ? R(0) : e;
+}
+
+// ---------------------------------------------------------------------------
+// HEALPix RING pixel centre -> line-of-sight triad (Sec. 2.3; Gorski et al.
+// 2005).  l = phi, b = pi/2 - theta; n = (cos b cos l, cos b sin l, sin b),
+// e_l = (-sin l, cos l, 0), e_b = (-sin b cos l, -sin b sin l, cos b).
+// Ring and in-ring index are found with integer arithmetic; z and 1 - |z|
+// are formed from exact rationals, phi / pi = (j + offset) / (2 i).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Los {
+    R n[3], el[3], eb[3];
+};
+
+// Ring k >= 1 of a polar cap containing index c (0-based from the pole):
+// 2k(k-1) <= c < 2k(k+1).
+__device__ __forceinline__ long long cap_ring(long long c) {
+    long long k = (long long)(0.5f * (1.0f + sqrtf(1.0f + 2.0f * (float)c)));
+    if (k < 1) k = 1;
+    while (2 * k * (k - 1) > c) --k;
+    while (2 * k * (k + 1) <= c) ++k;
+    return k;
+}
+
+template <typename R>
+__device__ __forceinline__ void healpix_los(int nside, long long pix, Los<R>& L) {
+    const long long N = nside;
+    const long long ncap = 2 * N * (N - 1);
+    const long long npix = 12 * N * N;
+    R sinb, cosb, phi_pi;  // phi / pi
+    if (pix < ncap) {
+        long long k = cap_ring(pix);
+        long long j0 = pix - 2 * k * (k - 1);
+        R a = R(k * k) / R(3 * N * N);              // 1 - z
+        sinb = R(1) - a;
+        cosb = M<R>::sqrt(a * (R(2) - a));
+        phi_pi = (R(j0) + R(0.5)) / R(2 * k);
+    } else if (pix < npix - ncap) {
+        long long pp = pix - ncap;
+        long long i = N + pp / (4 * N);
+        long long j0 = pp - (i - N) * 4 * N;
+        long long s = (i - N + 1) & 1;
+        R z = R(4 * N - 2 * i) / R(3 * N);
+        sinb = z;
+        cosb = M<R>::sqrt((R(1) - z) * (R(1) + z));
+        phi_pi = (R(j0) + (s ? R(0.5) : R(0))) / R(2 * N);
+    } else {
+        long long c = npix - 1 - pix;
+        long long k = cap_ring(c);
+        long long m = c - 2 * k * (k - 1);
+        long long j0 = 4 * k - 1 - m;
+        R a = R(k * k) / R(3 * N * N);
+        sinb = a - R(1);
+        cosb = M<R>::sqrt(a * (R(2) - a));
+        phi_pi = (R(j0) + R(0.5)) / R(2 * k);
+    }
+    R sl, cl;
+    M<R>::sincospi(phi_pi, &sl, &cl);
+    L.n[0] = cosb * cl;
+    L.n[1] = cosb * sl;
+    L.n[2] = sinb;
+    L.el[0] = -sl;
+    L.el[1] = cl;
+    L.el[2] = R(0);
+    L.eb[0] = -sinb * cl;
+    L.eb[1] = -sinb * sl;
+    L.eb[2] = cosb;
+}
+
+// FP32 line of sight with the direction also as double-floats (nd): z = sin b
+// and phi/pi are exact rationals, so sin b, cos b = sqrt((1 - z)(1 + z)) and
+// sin l, cos l are formed to ~1e-10; the FP32 triad is their rounding.
+__device__ __forceinline__ void healpix_los_dd(int nside, long long pix, Los<float>& L, ff nd[3]) {
+    const long long N = nside;
+    const long long ncap = 2 * N * (N - 1);
+    const long long npix = 12 * N * N;
+    ff sinb, cos2b;
+    long long pn, pd;  // phi / pi = pn / pd
+    if (pix < ncap || pix >= npix - ncap) {
+        const bool north = pix < ncap;
+        const long long c = north ? pix : npix - 1 - pix;
+        const long long k = cap_ring(c);
+        const long long m = c - 2 * k * (k - 1);
+        const long long j0 = north ? m : 4 * k - 1 - m;
+        const ff a = dd_div(dd_from_int(k * k), dd_from_int(3 * N * N));     // 1 - |z|
+        const ff az = dd_add(ff{1.0f, 0.0f}, dd_neg(a));
+        sinb = north ? az : dd_neg(az);
+        cos2b = dd_mul(a, dd_add(ff{2.0f, 0.0f}, dd_neg(a)));
+        pn = 2 * j0 + 1;
+        pd = 4 * k;
+    } else {
+        const long long pp = pix - ncap;
+        const long long i = N + pp / (4 * N);
+        const long long j0 = pp - (i - N) * 4 * N;
+        const long long s = (i - N + 1) & 1;
+        sinb = dd_div(dd_from_int(4 * N - 2 * i), dd_from_int(3 * N));
+        cos2b = dd_mul(dd_add(ff{1.0f, 0.0f}, dd_neg(sinb)), dd_add(ff{1.0f, 0.0f}, sinb));
+        pn = 2 * j0 + s;
+        pd = 4 * N;
+    }
+    const ff cosb = cos2b.hi > 0.0f ? dd_sqrt(cos2b) : ff{0.0f, 0.0f};
+    ff sl, cl;
+    dd_sincospi_rational(pn, pd, sl, cl);
+    nd[0] = dd_mul(cosb, cl);
+    nd[1] = dd_mul(cosb, sl);
+    nd[2] = sinb;
+    L.n[0] = nd[0].hi;
+    L.n[1] = nd[1].hi;
+    L.n[2] = nd[2].hi;
+    L.el[0] = -sl.hi;
+    L.el[1] = cl.hi;
+    L.el[2] = 0.0f;
+    L.eb[0] = -(sinb.hi * cl.hi);
+    L.eb[1] = -(sinb.hi * sl.hi);
+    L.eb[2] = cosb.hi;
+}
+
+// Distance from the observer to the boundary of the box (half lengths h)
+// centred on the Galactic centre (Sec. 2.3).
+template <typename R>
+__device__ __forceinline__ R box_exit(const R o[3], const R h[3], const R n[3]) {
+    R t = R(1e30);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (n[k] > R(0)) t = M<R>::min(t, (h[k] - o[k]) / n[k]);
+        else if (n[k] < R(0)) t = M<R>::min(t, (-h[k] - o[k]) / n[k]);
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Field models.  B in uG (galactocentric Cartesian), N0 and n_e in cm^-3.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R smoothstep01(R t) {
+    t = M<R>::min(M<R>::max(t, R(0)), R(1));
+    return t * t * (R(3) - R(2) * t);
+}
+
+// JF12-type structure constants: pitch 11.5 deg, reference radius 5 kpc,
+// arm strengths interpolated with a cubic smoothstep between arm centres
+// (transition half-width 1/2 sector).
+constexpr double kPitchSin = 0.1993679344171972;    // sin 11.5 deg
+constexpr double kPitchCos = 0.9799247046208296;    // cos 11.5 deg
+constexpr double kPitchCot = 4.915157031071205;     // cot 11.5 deg
+constexpr double kArmDelta = 0.5;
+
+// Logistic pair of the JF12 transitions, L(x; h, w) = 1/(1 + e^{-2(x-h)/w}):
+// returns L and 1 - L, each without cancellation.
+template <typename R>
+__device__ __forceinline__ void logistic_pair(R x, double h, double w, R& L, R& omL) {
+    using F = M<R>;
+    const R e = F::exp(F::mulc(x - R(h), 2.0 / w));          // e^{2(x-h)/w}, may be +inf
+    omL = F::div(R(1), R(1) + e);
+    L = e > R(1) ? R(1) - omL : e * omL;
+}
+
+// CR density normalised at the observer (Sec. 3.1, Eq. 12):
+// N0 = N0n e^{-rho/5} sech^2(z), sech^2 z = 4 e^{-2|z|} / (1 + e^{-2|z|})^2.
+// N0 only scales the emissivities, so it uses the fast primitives.
+template <typename R>
+__device__ __forceinline__ R cr_density(R n0n, R rho, R az) {
+    using F = M<R>;
+    const R e2 = F::exp2_fast(R(-2.0 * kLog2e) * az);
+    const R inv1 = F::rcp_fast(R(1) + e2);
+    return n0n * F::exp2_fast(R(-0.2 * kLog2e) * rho) * (R(4) * e2 * inv1 * inv1);
+}
+
+// Position in the JF12 spiral-arm pattern: sector k in 0..7 and fraction
+// f in [0, 1) of u = (4/pi)(phi - cot(i) ln(rho/5)) mod 8.
+template <typename R>
+struct ArmCoord {
+    int k;
+    R f;
+};
+
+template <typename R>
+__device__ __forceinline__ ArmCoord<R> arm_from_u(R u) {
+    u = u - R(8) * M<R>::floor(u * R(0.125));
+    const R kf = M<R>::floor(u);
+    return ArmCoord<R>{((int)kf) & 7, u - kf};
+}
+
+// Direct evaluation from the position (FP64 march, field probes).
+template <typename R>
+__device__ __forceinline__ ArmCoord<R> arm_coord_direct(R x, R y, R rho) {
+    using F = M<R>;
+    if (!(rho > R(0))) return ArmCoord<R>{0, R(0)};
+    const R u = F::mulc(F::atan2(y, x) - F::mulc(F::log(F::div(rho, R(5))), kPitchCot), 4.0 / kPi);
+    return arm_from_u<R>(u);
+}
+
+// Tracks the arm coordinate along one lane's chunk of a ray.  FP32: u is
+// computed once, at the chunk's first marched sample, in double-float
+// (position from the double-float direction, atan2 and log in double-float),
+// then advanced sample by sample with the exact straight-line relations
+//   tan(d phi) = h L_z / (rho^2 + h b),   d ln rho = atanh(w / (2 + w)),
+//   w = h (2 b + h c) / rho^2,  b = p_xy . n_xy,  c = n_xy . n_xy,
+//   L_z = (p x n)_z  (constant along the ray),  h = +-dr,
+// whose small arguments are evaluated by short series (|arg| < 0.1,
+// truncation < 2e-10) and accumulated in double-float.  This keeps the
+// absolute error of u near 1e-8, where a plain FP32 evaluation of
+// ln(rho) and phi (values ~1-3, ulp ~2e-7) would give ~5e-7.
+template <typename R> struct ArmTracker;
+
+template <> struct ArmTracker<double> {
+    __device__ __forceinline__ void init(const MapParams<double>&, const ff*, int, double, double) {}
+    __device__ __forceinline__ void step(int) {}
+    __device__ __forceinline__ ArmCoord<double> coord(double x, double y, double rho) const {
+        return arm_coord_direct<double>(x, y, rho);
+    }
+};
+
+template <> struct ArmTracker<float> {
+    ff u;
+    float rho2_a, b_a, c, lz, dr;
+    float rho2, b;     // at the current sample
+    int n_a, n;
+
+    __device__ __forceinline__ void init(const MapParams<float>& P, const ff nd[3], int n0, float dr_,
+                                         float dr_lo) {
+        dr = dr_;
+        n_a = n = n0;
+        const ff t = dd_mul_f(ff{dr_, dr_lo}, float(n0) + 0.5f);
+        const ff px = dd_add(ff{P.obs[0], P.obs_lo[0]}, dd_mul(t, nd[0]));
+        const ff py = dd_add(ff{P.obs[1], P.obs_lo[1]}, dd_mul(t, nd[1]));
+        const ff r2 = dd_add(dd_sqr(px), dd_sqr(py));
+        lz = dd_add(dd_mul(ff{P.obs[0], P.obs_lo[0]}, nd[1]), dd_neg(dd_mul(ff{P.obs[1], P.obs_lo[1]}, nd[0]))).hi;
+        b_a = px.hi * nd[0].hi + py.hi * nd[1].hi;
+        c = nd[0].hi * nd[0].hi + nd[1].hi * nd[1].hi;
+        rho2_a = r2.hi;
+        rho2 = rho2_a;
+        b = b_a;
+        if (r2.hi > 0.0f) {
+            const ff phi = dd_atan2(py, px);
+            const ff ln_r2 = dd_log(r2);
+            const ff halfln = dd_add(ff{0.5f * ln_r2.hi, 0.5f * ln_r2.lo}, dd_const(-1.6094379124341003));
+            const ff d = dd_add(phi, dd_neg(dd_mul(dd_const(kPitchCot), halfln)));
+            u = dd_mul(dd_const(4.0 / kPi), d);
+        } else {
+            u = ff{0.0f, 0.0f};
+        }
+    }
+    // Advance to the neighbouring sample: dir = +1 (next) or -1 (previous).
+    __device__ __forceinline__ void step(int dir) {
+        const float h = dir > 0 ? dr : -dr;
+        const int nn = n + dir;
+        const float dt = float(nn - n_a) * dr;
+        const float rho2_new = rho2_a + dt * (2.0f * b_a + dt * c);
+        const float b_new = b_a + dt * c;
+        const float cross = h * lz;
+        const float dot = rho2 + h * b;
+        float dphi;
+        const float a = __fdividef(cross, dot);
+        if (dot > 0.0f && fabsf(a) < 0.1f) {
+            const float a2 = a * a;
+            dphi = a * (1.0f - a2 * (1.0f / 3.0f - a2 * (0.2f - a2 * (1.0f / 7.0f))));
+        } else {
+            dphi = atan2f(cross, dot);
+        }
+        const float w = __fdividef(h * (2.0f * b + h * c), rho2);      // rho2_new / rho2 - 1
+        const float sa = __fdividef(w, 2.0f + w);
+        float dln;
+        if (fabsf(sa) < 0.1f) {
+            const float s2 = sa * sa;
+            dln = sa * (1.0f + s2 * (1.0f / 3.0f + s2 * (0.2f + s2 * (1.0f / 7.0f))));
+        } else {
+            dln = 0.5f * log1pf(w);
+        }
+        u = dd_add_f(u, 1.2732395447351628f * (dphi - 4.9151570310712050f * dln));
+        rho2 = rho2_new;
+        b = b_new;
+        n = nn;
+    }
+    __device__ __forceinline__ ArmCoord<float> coord(float, float, float) const {
+        const float v = u.hi - 8.0f * floorf(u.hi * 0.125f);
+        float kf = floorf(v);
+        float f = (v - kf) + u.lo;
+        if (f < 0.0f) { f += 1.0f; kf -= 1.0f; }
+        else if (f >= 1.0f) { f -= 1.0f; kf += 1.0f; }
+        return ArmCoord<float>{((int)kf) & 7, f};
+    }
+};
+
+template <int MODEL> struct Model;
+
+template <> struct Model<SYNAX_MODEL_TOY> {
+    template <typename R>
+    static __device__ __forceinline__ void eval(const R* m, const R* /*arms*/, R t, R /*x*/, R /*y*/,
+                                                R /*z*/, const ArmCoord<R>& /*ac*/, R B[3], R& N0,
+                                                R& ne) {
+        const bool in = t < m[mc::TOY_R0];
+        B[0] = in ? m[mc::TOY_B + 0] : R(0);
+        B[1] = in ? m[mc::TOY_B + 1] : R(0);
+        B[2] = in ? m[mc::TOY_B + 2] : R(0);
+        ne = in ? m[mc::TOY_NE] : R(0);
+        N0 = in ? m[mc::TOY_N0] : R(0);
+    }
+};
+
+template <> struct Model<SYNAX_MODEL_WMAP> {
+    template <typename R>
+    static __device__ __forceinline__ void eval(const R* m, const R* /*arms*/, R /*t*/, R x, R y, R z,
+                                                const ArmCoord<R>& /*ac*/, R B[3], R& N0, R& ne) {
+        using F = M<R>;
+        const R rho2 = x * x + y * y;
+        const bool has_rho = rho2 > R(0);
+        const R rho = F::sqrt(rho2);
+        const R c = has_rho ? F::div(x, rho) : R(1);
+        const R s = has_rho ? F::div(y, rho) : R(0);
+        const R az = F::abs(z);
+        const R e2 = F::exp(R(-2) * az);                      // e^{-2|z|}
+        const R inv1 = F::div(R(1), R(1) + e2);
+        const R sech2 = R(4) * e2 * inv1 * inv1;
+        R psi = R(0), chi = R(0);
+        if (rho >= R(3) && rho <= R(20)) {
+            psi = m[mc::W_PSI0] + m[mc::W_PSI1] * F::log(F::div(rho, R(8)));
+            const R th = (R(1) - e2) * inv1;                 // tanh |z|
+            chi = m[mc::W_CHI0] * (z < R(0) ? -th : th);
+        }
+        const R amp = m[mc::W_B0] * F::exp(-(F::mulc(rho, 0.125) + az));
+        R sp, cp, sc, cc;
+        F::sincos(psi, &sp, &cp);
+        F::sincos(chi, &sc, &cc);
+        const R br = amp * cp * cc, bp = amp * sp * cc;
+        B[0] = br * c - bp * s + m[mc::W_BUX];
+        B[1] = br * s + bp * c;
+        B[2] = amp * sc;
+        N0 = cr_density<R>(m[mc::W_N0N], rho, az);
+        ne = m[mc::W_NE0] * F::exp(-F::mulc(rho, 0.05)) * sech2;
+    }
+};
+
+template <> struct Model<SYNAX_MODEL_JF12> {
+    template <typename R>
+    static __device__ __forceinline__ void eval(const R* m, const R* arms, R /*t*/, R x, R y, R z,
+                                                const ArmCoord<R>& ac, R B[3], R& N0, R& ne) {
+        using F = M<R>;
+        const R rho2 = x * x + y * y;
+        const bool has_rho = rho2 > R(0);
+        const R rho = F::sqrt(rho2);
+        const R ri = has_rho ? F::div(R(1), rho) : R(0);
+        const R c = has_rho ? x * ri : R(1);
+        const R s = has_rho ? y * ri : R(0);
+        const R az = F::abs(z);
+        const R sz = F::div(z, F::sqrt(z * z + R(0.01)));                 // smooth sign
+        R Lz, omLz;
+        logistic_pair<R>(az, 0.4, 0.27, Lz, omLz);
+        R br = R(0), bp = R(0), bz = R(0);
+
+        // disc: 8 smooth log-spiral arms inside a smooth radial window
+        const R W = smoothstep01<R>((rho - R(4.75)) * R(2)) * smoothstep01<R>((R(20.25) - rho) * R(2));
+        if (W > R(0)) {
+            const int k = ac.k;
+            const R f = ac.f;
+            // b_k at the arm centre u = k + 1/2, C^1 smoothstep towards the
+            // neighbouring centre on either side
+            R beta;
+            if (f < R(0.5)) {
+                const R prev = arms[(k + 7) & 7];
+                beta = prev + (arms[k] - prev) * smoothstep01<R>(f + R(0.5));
+            } else {
+                const R cur = arms[k];
+                beta = cur + (arms[(k + 1) & 7] - cur) * smoothstep01<R>(f - R(0.5));
+            }
+            const R amp = beta * R(5) * ri * W * omLz;
+            br += amp * R(kPitchSin);
+            bp += amp * R(kPitchCos);
+        }
+
+        // toroidal halo: (1 - L(rho; 9.22, 0.2)) is the second member of the pair
+        R Lr, omLr;
+        logistic_pair<R>(rho, 9.22, 0.2, Lr, omLr);
+        bp += m[mc::J_BH] * F::exp(-F::div(az, m[mc::J_ZH])) * Lz * omLr * sz;
+
+        // X field
+        const R rp = rho - az * m[mc::J_COTX];
+        if (rp > R(0)) {
+            const R mag = m[mc::J_BX] * F::exp(-F::mulc(rp, 1.0 / 4.8)) * rp * ri;
+            br += mag * sz * m[mc::J_COSX];
+            bz += mag * m[mc::J_SINX];
+        }
+        B[0] = br * c - bp * s;
+        B[1] = br * s + bp * c;
+        B[2] = bz;
+
+        N0 = cr_density<R>(m[mc::J_N0N], rho, az);
+        ne = R(0.025) * F::exp(-(F::mulc(rho, 0.05) + F::div(az, m[mc::J_H1]))) +
+             R(0.10) * F::exp(-(F::mulc(rho, 0.25) + F::div(az, m[mc::J_H2])));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Per-sample emission terms.  With a = B.e_l, b = B.e_b, B_perp^2 = a^2 + b^2
+// and w = (B_perp^2)^{(p-3)/4}:
+//   j_I  ~ N0 B_perp^{(p+1)/2}            = N0 w B_perp^2          (Eq. 2)
+//   j_P e^{2 i chi_0} ~ N0 B_perp^{(p+1)/2} (a + ib)^2 / B_perp^2
+//                      = N0 w (a^2 - b^2 + 2iab)                  (Eq. 5, 8)
+//   f = n_e B_par, B_par = -B.n                                    (Eq. 7)
+// Physical constants and the nu dependence are in the per-frequency
+// prefactors aI, aP (host).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Emit {
+    R jI, pc, ps, f;
+};
+
+template <typename R>
+__device__ __forceinline__ Emit<R> emit(const R B[3], R N0, R ne, const Los<R>& L, R q) {
+    const R bn = B[0] * L.n[0] + B[1] * L.n[1] + B[2] * L.n[2];
+    const R bl = B[0] * L.el[0] + B[1] * L.el[1];
+    const R bb = B[0] * L.eb[0] + B[1] * L.eb[1] + B[2] * L.eb[2];
+    const R bp2 = bl * bl + bb * bb;
+    // B_perp below 1e-15 uG radiates nothing measurable; the cut also keeps
+    // FP32 denormals away from the flush-to-zero logarithm.
+    const R w = bp2 > R(1e-30) ? M<R>::exp2_fast(q * M<R>::log2_fast(bp2)) : R(0);
+    const R nw = N0 * w;
+    Emit<R> e;
+    e.jI = nw * bp2;
+    e.pc = nw * (bl * bl - bb * bb);
+    e.ps = nw * (R(2) * bl * bb);
+    e.f = -ne * bn;
+    return e;
+}
+
+}  // namespace synax

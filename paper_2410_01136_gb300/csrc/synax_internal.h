@@ -1,0 +1,99 @@
+// synax_internal.h -- host/device parameter blocks of the synax CUDA library.
+//
+// The C-ABI layer (abi.cu) validates a synax_problem, derives every
+// constant the march needs in double precision on the host, and packs them
+// into a MapParams<R> block that is passed to the kernels by value (it lives
+// in the kernel-parameter constant bank, so all threads read it as a
+// broadcast).  R = float for the FP32 march, double for SYNAX_F64.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/synax.h"
+
+namespace synax {
+
+// Double-float value hi + lo (|lo| <= ulp(hi)/2), the compensated-FP32
+// representation used for the running RM sum and the Faraday phases.
+struct ff {
+    float hi, lo;
+};
+
+template <typename R> struct PhaseT;
+template <> struct PhaseT<float> { using type = ff; };
+template <> struct PhaseT<double> { using type = double; };
+
+// Number of model constants in MapParams::m.
+constexpr int kModelConsts = 48;
+
+// Indices into MapParams::m for each model (filled by the host, abi.cu).
+namespace mc {
+// toy
+constexpr int TOY_B = 0, TOY_NE = 3, TOY_N0 = 4, TOY_R0 = 5;
+// WMAP-type
+constexpr int W_B0 = 0, W_PSI0 = 1, W_PSI1 = 2, W_CHI0 = 3, W_BUX = 4, W_N0N = 5, W_NE0 = 6;
+// JF12-type
+constexpr int J_B = 0;              // b_1..b_8 at 0..7
+constexpr int J_BH = 8, J_IZH = 9, J_BX = 10, J_COSX = 11, J_SINX = 12, J_COTX = 13,
+              J_N0N = 14, J_IH1 = 15, J_IH2 = 16, J_ZH = 17, J_THX = 18, J_H1 = 19, J_H2 = 20,
+              J_N0OBS = 21, J_SIN2X = 22;
+}  // namespace mc
+
+template <typename R>
+struct MapParams {
+    using Phase = typename PhaseT<R>::type;
+    int nside;
+    int n_steps;
+    int n_freq;
+    int model;
+    long long pix_begin;
+    long long n_pix;          // pixels marched (output columns)
+    int box_clip;
+    R w_own;                  // share of a cell's own f in its RM (0.5, 0, 1)
+    R obs[3];
+    R obs_lo[3];              // obs - (R)obs (FP32: observer as hi + lo)
+    R box_half[3];
+    R r_max;
+    R dr;                     // r_max / n_steps (r_max mode), rounded
+    R dr_lo;                  // r_max / n_steps - dr (FP32: keeps positions unbiased)
+    R q;                      // (p - 3) / 4, exponent of B_perp^2 in w
+    R aI[SYNAX_MAX_FREQ];     // T per (cm^-3 uG^{(p+1)/2} kpc) for I
+    R aP[SYNAX_MAX_FREQ];     // same for P
+    Phase crev[SYNAX_MAX_FREQ];   // Faraday phase, revolutions per (cm^-3 uG kpc)
+    Phase cdr[SYNAX_MAX_FREQ];    // crev * dr (r_max mode)
+    R m[kModelConsts];
+};
+
+// Gradient-side constants (adjoint): d ln aI / dp and d ln aP / dp per
+// frequency, and the index of each model parameter.
+template <typename R>
+struct AdjParams {
+    R dlnaI_dp[SYNAX_MAX_FREQ];
+    R dlnaP_dp[SYNAX_MAX_FREQ];
+    int n_theta;
+    int mode_chi2;            // 1: seed = 2 (M - target) / sigma^2
+    R inv_sigma2;
+};
+
+// Host-side entry points into the kernels (forward.cu, adjoint.cu).
+int launch_forward_f32(const MapParams<float>& P, void* maps, void* stream);
+int launch_forward_f64(const MapParams<double>& P, void* maps, void* stream);
+
+size_t adjoint_workspace_bytes(long long n_pix, int n_theta);
+int launch_adjoint_f32(const MapParams<float>& P, const AdjParams<float>& A, const void* gmaps,
+                       const void* target, double* grad, double* chi2, void* maps,
+                       void* workspace, void* stream);
+int launch_adjoint_f64(const MapParams<double>& P, const AdjParams<double>& A, const void* gmaps,
+                       const void* target, double* grad, double* chi2, void* maps,
+                       void* workspace, void* stream);
+
+int launch_eval_fields_f32(const MapParams<float>& P, const double* pos, const double* t, long long n,
+                           double* out, void* stream);
+int launch_eval_fields_f64(const MapParams<double>& P, const double* pos, const double* t, long long n,
+                           double* out, void* stream);
+
+// Records a CUDA error for synax_last_cuda_error() and returns SYNAX_ECUDA.
+int record_cuda_error(int err);
+
+}  // namespace synax

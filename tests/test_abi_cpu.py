@@ -1,0 +1,160 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every symbol include/synax.h declares, its struct layout matches the
+Python binding, and host-side validation rejects malformed problems before
+anything is enqueued (no CUDA call is made on these paths)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2410_01136_gb300 import _native, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2410_01136_gb300 import build
+    build()
+    return _native.lib()
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(synax_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert "synax_forward" in names and "synax_adjoint" in names
+    for n in names:
+        assert hasattr(L, n), f"libsynax does not export {n}"
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}\b", out), n
+    # and the binding declares a signature for every one of them
+    for n in names:
+        assert n in _native.SIGNATURES or n.startswith("synax_batch") or n.startswith("synax_surrogate"), n
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    fields = [f for f, _ in _native.SynaxProblem._fields_]
+    body = "\n".join(f'printf("{f} %zu\\n", offsetof(synax_problem, {f}));' for f in fields)
+    src.write_text(f"""#include <stdio.h>
+#include <stddef.h>
+#include "synax.h"
+int main(void) {{ printf("size %zu\\n", sizeof(synax_problem)); {body} return 0; }}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(_native.SynaxProblem)
+    for f in fields:
+        assert int(got[f]) == getattr(_native.SynaxProblem, f).offset, f
+
+
+def call_forward(L, prob_struct):
+    # maps pointer is a dummy non-NULL value: validation fails before any use.
+    return L.synax_forward(ctypes.byref(prob_struct), ctypes.c_void_p(16), None)
+
+
+def good():
+    return inputs.config2().replace(nside=4, n_steps=64)
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda s: setattr(s, "nside", 3), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "nside", 0), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "nside", 16384), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "n_steps", 0), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "n_steps", 65537), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "n_freq", 0), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "n_freq", 17), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "model_id", 7), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "n_theta", 15), _native.SYNAX_EINVAL),
+    (lambda s: s.theta.__setitem__(3, float("nan")), _native.SYNAX_ENONFINITE),
+    (lambda s: s.freq_hz.__setitem__(0, float("inf")), _native.SYNAX_ENONFINITE),
+    (lambda s: s.freq_hz.__setitem__(1, -1.0), _native.SYNAX_EINVAL),
+    (lambda s: s.obs_kpc.__setitem__(2, float("nan")), _native.SYNAX_ENONFINITE),
+    (lambda s: setattr(s, "r_max_kpc", 0.0), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "flags", 1 << 7), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "rm_rule", 3), _native.SYNAX_EINVAL),
+    (lambda s: s.theta.__setitem__(13, 0.2), _native.SYNAX_EINVAL),     # p too small for Eq. 2
+    (lambda s: s.theta.__setitem__(9, 0.0), _native.SYNAX_EINVAL),      # z_h
+    (lambda s: s.theta.__setitem__(11, 1.6), _native.SYNAX_EINVAL),     # theta_X >= pi/2
+    (lambda s: setattr(s, "pix_begin", -1), _native.SYNAX_EINVAL),
+    (lambda s: setattr(s, "pix_begin", 193), _native.SYNAX_EINVAL),
+    (lambda s: (setattr(s, "pix_begin", 100), setattr(s, "pix_count", 93)), _native.SYNAX_EINVAL),
+    (lambda s: (setattr(s, "flags", _native.SYNAX_BOX_CLIP), s.box_kpc.__setitem__(2, 0.01)),
+     _native.SYNAX_EINVAL),   # observer outside the box
+])
+def test_validation_rejects(L, mutate, code):
+    s = _native.problem_struct(good())
+    mutate(s)
+    assert call_forward(L, s) == code
+    assert L.synax_strerror(code)
+
+
+def test_empty_range_and_null(L):
+    s = _native.problem_struct(good())
+    s.pix_begin = 192          # empty pixel range: nothing to do, no launch
+    assert L.synax_forward(ctypes.byref(s), None, None) == _native.SYNAX_OK
+    assert L.synax_forward(None, ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
+    s = _native.problem_struct(good())
+    assert L.synax_forward(ctypes.byref(s), None, None) == _native.SYNAX_EINVAL
+
+
+def test_adjoint_validation(L):
+    s = _native.problem_struct(good())
+    n = ctypes.c_size_t(0)
+    assert L.synax_adjoint_workspace_bytes(ctypes.byref(s), ctypes.byref(n)) == _native.SYNAX_OK
+    dummy = ctypes.c_void_p(16)
+    # chi^2 mode without target / with bad sigma
+    assert L.synax_adjoint(ctypes.byref(s), None, None, 1.0, dummy, None, None, dummy,
+                           n.value, None) == _native.SYNAX_EINVAL
+    assert L.synax_adjoint(ctypes.byref(s), None, dummy, float("nan"), dummy, None, None, dummy,
+                           n.value, None) == _native.SYNAX_ENONFINITE
+    assert L.synax_adjoint(ctypes.byref(s), None, dummy, -1.0, dummy, None, None, dummy,
+                           n.value, None) == _native.SYNAX_EINVAL
+    # no gradient buffer
+    assert L.synax_adjoint(ctypes.byref(s), dummy, None, 1.0, None, None, None, dummy,
+                           n.value, None) == _native.SYNAX_EINVAL
+    if n.value > 0:
+        assert L.synax_adjoint(ctypes.byref(s), dummy, None, 1.0, dummy, None, None, dummy,
+                               n.value - 1, None) == _native.SYNAX_ESPACE
+    toy = _native.problem_struct(inputs.toy_problem(nside=2, n_steps=8))
+    assert L.synax_adjoint(ctypes.byref(toy), dummy, None, 1.0, dummy, None, None, dummy,
+                           1 << 30, None) == _native.SYNAX_ENOTSUP
+
+
+def test_version_and_strerror(L):
+    assert L.synax_version() >= 100
+    for code in range(-7, 1):
+        assert isinstance(L.synax_strerror(code), bytes)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    monkeypatch.setattr(_native, "_lib", None)
+    monkeypatch.setattr(_native, "LIB_PATH", "/nonexistent/libsynax.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        _native.lib()
+
+
+def test_problem_struct_roundtrip():
+    p = inputs.config2().replace(pix_begin=5, pix_count=7, rm_rule=2, f64=True)
+    s = _native.problem_struct(p)
+    assert s.nside == 64 and s.n_steps == 512 and s.n_freq == 4 and s.n_theta == 16
+    assert s.flags == _native.SYNAX_F64 and s.rm_rule == 2 and s.pix_begin == 5 and s.pix_count == 7
+    assert np.allclose(list(s.theta)[:16], p.theta)

@@ -1,0 +1,150 @@
+"""Parity of the CUDA forward march (synax_forward, through the C ABI) with the
+FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances: I 1e-5 relative per pixel; Q + iU 1e-4 relative to
+max(|P|, 1e-2 median |P|) per pixel (tests/parity.py).  FP64 marches are held
+to 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_01136_gb300 import forward, inputs
+
+from .parity import assert_parity, assert_parity_coarse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    assert _t.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2410_01136_gb300 import build
+    build()
+    oracle.build()
+    return _t
+
+
+def gpu_map(torch, prob):
+    m = forward(prob)
+    torch.cuda.synchronize()
+    return m.cpu().numpy()
+
+
+def test_nside16_wmap_fp64_full(torch):
+    prob = inputs.config1()
+    g = gpu_map(torch, prob)
+    o = oracle.forward(prob)
+    assert g.dtype == np.float64
+    assert_parity(g, o, 1e-9, 1e-9, "WMAP-type FP64 full map")
+
+
+def test_jf12_fp32_small_ragged(torch):
+    # 768 rays (96 CTAs), 100 steps: 32 lanes get 3 or 4 samples
+    prob = inputs.config2().replace(nside=8, n_steps=100)
+    assert_parity(gpu_map(torch, prob), oracle.forward(prob), what="JF12-type FP32 nside 8, N 100")
+
+
+def test_jf12_fp32_fp64_agree(torch):
+    prob = inputs.config2().replace(nside=8, n_steps=256)
+    g32 = gpu_map(torch, prob)
+    g64 = gpu_map(torch, prob.replace(f64=True))
+    o = oracle.forward(prob)
+    assert_parity(g64, o, 1e-9, 1e-9, "JF12-type FP64")
+    assert_parity(g32, o, what="JF12-type FP32")
+
+
+@pytest.mark.slow
+def test_jf12_fp32_full_size_sampled(torch):
+    """Nside 64, 512 steps, four frequencies: the full map in the benchmark's
+    launch configuration, checked on 600 seeded sample pixels."""
+    prob = inputs.config2()
+    g = gpu_map(torch, prob)
+    assert g.shape == (4, 3, 49152)
+    assert np.all(np.isfinite(g))
+    pix = inputs.sample_pixels(prob.npix, 600, seed=21)
+    o = oracle.forward(prob, pix=pix)
+    assert_parity(g[:, :, pix], o, what="JF12-type FP32 full size (sampled)")
+
+
+def test_wmap_fp32(torch):
+    prob = inputs.config1().replace(f64=False)
+    assert_parity(gpu_map(torch, prob), oracle.forward(prob), what="WMAP-type FP32")
+
+
+def test_toy_box_fp64_and_fp32(torch):
+    prob = inputs.toy_problem(nside=8, n_steps=1024)
+    o = oracle.forward(prob)
+    assert_parity(gpu_map(torch, prob.replace(f64=True)), o, 1e-9, 1e-9, "toy box FP64")
+    g32 = gpu_map(torch, prob)
+    # FP32 may put a midpoint on the other side of the sphere edge |r - r_obs| = R0;
+    # such a pixel differs by one sample (~dr / R0).  Everything else is at tolerance.
+    err_I = np.abs(g32[0, 0] - o[0, 0]) / np.abs(o[0, 0])
+    assert np.mean(err_I <= 1e-5) > 0.99
+    assert np.max(err_I) < 1.5 * (40.0 / 1024) / 4.0
+
+
+@pytest.mark.parametrize("n_steps", [1, 2, 5, 31, 32, 33, 64, 257])
+def test_step_counts(torch, n_steps):
+    prob = inputs.config2().replace(nside=2, n_steps=n_steps)
+    g, o = gpu_map(torch, prob), oracle.forward(prob)
+    if n_steps < 16:
+        assert_parity_coarse(g, o, prob.freq_hz, what=f"N={n_steps}")
+    else:
+        assert_parity(g, o, what=f"N={n_steps}")
+
+
+@pytest.mark.parametrize("nside", [1, 2, 4])
+def test_tiny_maps(torch, nside):
+    prob = inputs.config2().replace(nside=nside, n_steps=64, freq_hz=(1.4e9,))
+    assert_parity(gpu_map(torch, prob), oracle.forward(prob), what=f"nside {nside}")
+
+
+@pytest.mark.parametrize("nf", [1, 2, 3, 5, 9, 16])
+def test_frequency_counts(torch, nf):
+    freqs = tuple(np.geomspace(300e6, 30e9, nf))
+    prob = inputs.config2().replace(nside=2, n_steps=96, freq_hz=freqs)
+    assert_parity(gpu_map(torch, prob), oracle.forward(prob), what=f"{nf} frequencies")
+
+
+def test_pixel_ranges_bitwise(torch):
+    prob = inputs.config2().replace(nside=8, n_steps=128)
+    full = gpu_map(torch, prob)
+    for begin, count in ((0, 1), (5, 7), (300, 77), (760, 0), (767, 1)):
+        part = gpu_map(torch, prob.replace(pix_begin=begin, pix_count=count))
+        n = count or prob.npix - begin
+        assert part.shape == (4, 3, n)
+        assert np.array_equal(part, full[:, :, begin:begin + n])
+
+
+@pytest.mark.parametrize("rule", [1, 2])
+def test_rm_rules(torch, rule):
+    prob = inputs.config2().replace(nside=4, n_steps=128, rm_rule=rule)
+    assert_parity(gpu_map(torch, prob), oracle.forward(prob), what=f"rm_rule {rule}")
+
+
+def test_deterministic(torch):
+    prob = inputs.config2().replace(nside=8, n_steps=512)
+    a = gpu_map(torch, prob)
+    b = gpu_map(torch, prob)
+    assert np.array_equal(a, b)
+
+
+def test_theta_variations(torch):
+    """Parity over a spread of parameters (ensemble draws)."""
+    sets = inputs.config4(n_sets=6, seed=4)
+    for s in sets:
+        prob = s.replace(nside=4, n_steps=min(s.n_steps, 256))
+        assert_parity(gpu_map(torch, prob), oracle.forward(prob), what=f"theta {prob.theta[:3]}")
+
+
+def test_streams_and_out_buffer(torch):
+    prob = inputs.config2().replace(nside=4, n_steps=64)
+    ref = gpu_map(torch, prob)
+    s = torch.cuda.Stream()
+    out = torch.full((4, 3, prob.npix), float("nan"), device="cuda")
+    with torch.cuda.stream(s):
+        forward(prob, out=out)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref)
