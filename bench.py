@@ -1,0 +1,354 @@
+"""Benchmark of the synchrotron ray march on GB300: LOS samples/s and maps+grad/s.
+
+One step = one map + gradient evaluation of the JF12-type workload (Nside 64,
+512 steps to 20 kpc, 408 MHz / 1.4 / 2.3 / 23 GHz, 16 free parameters): the
+C-ABI call synax_adjoint in chi^2 mode, which marches every ray forward
+(maps, chi^2 against a seeded target) and backwards (d chi^2 / d theta).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU; every rank
+evaluates its own map + gradient (independent parameter sets, as in an HMC
+ensemble), no collective on the data path (weak scaling); rank 0 prints one
+JSON line.  --impl reference times the FP64 CPU oracle (central finite
+differences for the gradient) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LOS samples/s and maps+grad/s (Nside 64, 512 steps) at stated tolerance"
+WORKLOAD = "JF12-type map+gradient, Nside 64, 512 steps, 4 freq, 16 params, chi^2 vs seeded target"
+
+# Algorithmic operation model per LOS sample (the stated per-sample figure of
+# the hot path: field model, emissivity, RM and four Faraday phases), FP32 ops
+# counting FMA/ADD/MUL/compare as one, and MUFU (SFU) ops.  The adjoint step
+# marches every sample forward once and backwards once with derivatives:
+# three forward-equivalents.
+FWD_FP32_OPS = 200
+FWD_MUFU_OPS = 22
+ADJ_FACTOR = 3
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="synax", choices=["synax", "reference"])
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smmax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smmax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smmax) if smmax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): FD gradient on a pixel sample
+# ---------------------------------------------------------------------------
+def oracle_map_grad_rate(n_pix_sample: int, n_repeat: int = 1) -> tuple[float, float, int, str]:
+    """samples/s of map + gradient with the FP64 oracle: per map+grad, one
+    forward and 2 * 16 central-difference maps, on n_pix_sample pixels."""
+    import numpy as np
+
+    import oracle
+    from paper_2410_01136_gb300 import inputs
+    oracle.build()
+    prob, _, _ = inputs.config3()
+    pix = inputs.sample_pixels(prob.npix, n_pix_sample, seed=41)
+    threads = oracle.default_threads()
+    h = 1e-4 * inputs.jf12_scales(prob.theta)
+    t0 = time.perf_counter()
+    for _ in range(n_repeat):
+        oracle.forward(prob, pix=pix, threads=threads)
+        for i in range(prob.theta.size):
+            for sgn in (1.0, -1.0):
+                th = prob.theta.copy()
+                th[i] += sgn * h[i]
+                oracle.forward(prob.with_theta(th), pix=pix, threads=threads)
+    dt = time.perf_counter() - t0
+    samples = n_repeat * pix.size * prob.n_steps        # LOS samples of the map+grad evaluations
+    sample_desc = (f"{pix.size} of {prob.npix} pixels x {prob.n_steps} steps x 4 freq, "
+                   f"map + 32-map central-difference gradient, {n_repeat} evaluation(s)")
+    return samples / dt, dt, threads, sample_desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    per_step = []
+    rate = None
+    threads = 1
+    desc = ""
+    for k in range(args.warmup + args.steps):
+        r, dt, threads, desc = oracle_map_grad_rate(256)
+        if k >= args.warmup:
+            per_step.append(dt)
+            rate = r if rate is None else rate
+    rates = [256 * 512 / d for d in per_step]
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(per_step)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nside": 64, "n_steps": 512, "n_freq": 4,
+                   "sample": "256 pixels per step"},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_synax(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_2410_01136_gb300 as sx
+    from paper_2410_01136_gb300 import inputs
+    sx.build()
+
+    prob, th_target, sigma = inputs.config3(seed=3 + rank)
+    # target: forward map of the perturbed parameters plus N(0, sigma^2) noise
+    with torch.cuda.device(dev):
+        target_clean = sx.forward(prob.with_theta(th_target))
+        noise = torch.tensor(inputs.target_noise(tuple(target_clean.shape), seed=3 + rank, sigma=sigma),
+                             dtype=torch.float32, device=dev)
+        target = (target_clean + noise).contiguous()
+    shape = tuple(target.shape)
+    maps = torch.empty(shape, dtype=torch.float32, device=dev)
+    ws = torch.empty(max(sx.adjoint_workspace_bytes(prob), 1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return sx.adjoint(prob, target=target, sigma=sigma, maps_out=maps, workspace=ws)
+
+    def fwd():
+        return sx.forward(prob, out=maps)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+        fwd()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K map+grad steps, L2 flushed between steps ----
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    # forward-only march of the same maps (context figure, same flushing)
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        fev[k][0].record(stream)
+        fwd()
+        fev[k][1].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = [a.elapsed_time(b) for a, b in fev]
+    time.sleep(0.2)
+    clk = clocks.stop()
+
+    # ---- end to end through the public API with host buffers ----
+    h_target = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    h_target.copy_(target.cpu())
+    h_maps = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    h_grad = torch.empty(16, dtype=torch.float64, pin_memory=True)
+    h_chi2 = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    d_target = torch.empty(shape, dtype=torch.float32, device=dev)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e2e_ev[k][0].record(stream)
+        d_target.copy_(h_target, non_blocking=True)
+        g, c2 = sx.adjoint(prob, target=d_target, sigma=sigma, maps_out=maps, workspace=ws)
+        h_maps.copy_(maps, non_blocking=True)
+        h_grad.copy_(g, non_blocking=True)
+        h_chi2.copy_(c2, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    barrier()
+    e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+
+    ms = float(np.mean(step_ms))
+    ms_e2e = float(np.mean(e2e_ms))
+    ms_fwd = float(np.mean(fwd_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_e2e, ms_fwd], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e, ms_fwd = [float(x) for x in t.tolist()]
+    samples = prob.samples
+    value = world * samples / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the adjoint march): algorithmic FP32 and
+    # MUFU work per launch over the launch's measured duration
+    clk_mhz = clk["sm_mhz"] or 2070.0
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12          # T op/s
+    mufu_peak = SM_COUNT * MUFU_LANES_PER_SM * clk_mhz * 1e6 / 1e12
+    adj_fp32 = ADJ_FACTOR * FWD_FP32_OPS * samples
+    adj_mufu = ADJ_FACTOR * FWD_MUFU_OPS * samples
+    t_s = ms * 1e-3
+    fp32_ach = adj_fp32 / t_s / 1e12
+    mufu_ach = adj_mufu / t_s / 1e12
+    bound_is_fp32 = adj_fp32 / fp32_peak >= adj_mufu / mufu_peak
+    roof = {
+        "bound": "alu",
+        "achieved": fp32_ach if bound_is_fp32 else mufu_ach,
+        "peak": fp32_peak if bound_is_fp32 else mufu_peak,
+        "unit": "T FP32 op/s" if bound_is_fp32 else "T MUFU op/s",
+        "frac": (fp32_ach / fp32_peak) if bound_is_fp32 else (mufu_ach / mufu_peak),
+        "traffic": None,
+        "kernel": "k_adjoint (+ k_reduce_partials)",
+        "ops_per_sample": {"fp32": ADJ_FACTOR * FWD_FP32_OPS, "mufu": ADJ_FACTOR * FWD_MUFU_OPS},
+        "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x median SM clock "
+                      f"{clk_mhz:.0f} MHz (no measured FP32 peak in the peaks file)",
+    }
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nside": 64, "n_steps": 512, "n_freq": 4, "n_theta": 16,
+                   "samples_per_step": samples, "global_batch": world, "l2": "flushed between steps "
+                   "(256 MiB write), inputs 2.4 MB", "parallelism": f"replicas x{world}"},
+        "maps_grad_per_s": world / (ms * 1e-3),
+        "forward_samples_per_s": world * samples / (ms_fwd * 1e-3),
+        "forward_ms": ms_fwd,
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": world * samples / (ms_e2e * 1e-3), "unit": "samples/s",
+                "h2d_bytes_per_step": int(target.numel() * 4),
+                "d2h_bytes_per_step": int(maps.numel() * 4 + 16 * 8 + 8)},
+        "gpu_launches": 2 * args.steps,
+    }
+    if rank == 0:
+        try:
+            rate, dt, threads, desc = oracle_map_grad_rate(8192)
+            out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
+                                   "kind": "oracle", "sample": desc, "seconds": dt}
+        except Exception as exc:  # the oracle is a baseline; report why it is absent
+            out["cpu_baseline"] = {"value": None, "unit": "samples/s", "cores": os.cpu_count(),
+                                   "kind": "oracle", "sample": f"failed: {exc}"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_synax(args)
+
+
+if __name__ == "__main__":
+    main()

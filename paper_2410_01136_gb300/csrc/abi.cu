@@ -205,7 +205,8 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         M.m[mc::W_PSI1] = R(th[2]);
         M.m[mc::W_CHI0] = R(th[3]);
         M.m[mc::W_BUX] = R(th[4]);
-        M.m[mc::W_N0N] = R(th[5] / cr_profile(P.obs_kpc));
+        M.m[mc::W_N0U] = R(1.0 / cr_profile(P.obs_kpc));
+        M.m[mc::W_N0OBS] = R(th[5]);
         M.m[mc::W_NE0] = R(th[7]);
         break;
     case SYNAX_MODEL_JF12:
@@ -217,6 +218,7 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         M.m[mc::J_SINX] = R(std::sin(th[11]));
         M.m[mc::J_COTX] = R(1.0 / std::tan(th[11]));
         M.m[mc::J_N0N] = R(th[12] / cr_profile(P.obs_kpc));
+        M.m[mc::J_N0U] = R(1.0 / cr_profile(P.obs_kpc));
         M.m[mc::J_IH1] = R(1.0 / th[14]);
         M.m[mc::J_IH2] = R(1.0 / th[15]);
         M.m[mc::J_ZH] = R(th[9]);
@@ -286,6 +288,13 @@ int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* 
     if (rc != SYNAX_OK) return rc;
     if (prob->model_id == SYNAX_MODEL_TOY) return SYNAX_ENOTSUP;
     if (!grad_dev) return SYNAX_EINVAL;
+    if (n_pix == 0) {
+        // Empty pixel range: the gradient (and chi^2) are zero whatever the mode.
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t err = cudaMemsetAsync(grad_dev, 0, sizeof(double) * prob->n_theta, st);
+        if (err == cudaSuccess && chi2_dev) err = cudaMemsetAsync(chi2_dev, 0, sizeof(double), st);
+        return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
+    }
     const bool chi2_mode = gmaps_dev == nullptr;
     if (chi2_mode) {
         if (!target_dev) return SYNAX_EINVAL;

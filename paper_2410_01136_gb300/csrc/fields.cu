@@ -20,7 +20,8 @@ k_eval_fields(const MapParams<R> P, const double* __restrict__ pos, const double
     R B[3], N0, ne;
     const R x = R(pos[3 * i]), y = R(pos[3 * i + 1]), z = R(pos[3 * i + 2]);
     const ArmCoord<R> ac = arm_coord_direct<R>(x, y, M<R>::sqrt(x * x + y * y));
-    Model<MODEL>::eval(P.m, s_arms, R(tdist[i]), x, y, z, ac, B, N0, ne);
+    FieldLocal<R> loc;
+    Model<MODEL>::eval(P.m, s_arms, R(tdist[i]), x, y, z, ac, B, N0, ne, loc);
     out[5 * i + 0] = (double)B[0];
     out[5 * i + 1] = (double)B[1];
     out[5 * i + 2] = (double)B[2];

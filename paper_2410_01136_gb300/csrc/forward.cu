@@ -45,10 +45,8 @@ k_forward(const MapParams<R> P, R* __restrict__ maps) {
     if (ray < P.n_pix) {
         Los<R> L;
         ff nd[3];
-        if constexpr (sizeof(R) == 4) healpix_los_dd(P.nside, P.pix_begin + ray, L, nd);
-        else healpix_los<R>(P.nside, P.pix_begin + ray, L);
-        const R dr = P.box_clip ? box_exit<R>(P.obs, P.box_half, L.n) / R(P.n_steps) : P.dr;
-        const R dr_lo = P.box_clip ? R(0) : P.dr_lo;
+        R dr, dr_lo;
+        ray_setup<R>(P, ray, L, nd, dr, dr_lo);
         PT cd[NF];
 #pragma unroll
         for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale(P.crev[k], dr) : P.cdr[k];
@@ -56,44 +54,10 @@ k_forward(const MapParams<R> P, R* __restrict__ maps) {
         const int N = P.n_steps;
         const int n0 = (int)(((long long)lane * N) >> 5);
         const int n1 = (int)(((long long)(lane + 1) * N) >> 5);
-
-        R accI = R(0);
+        R accI;
         R zr[NF], zi[NF];
-#pragma unroll
-        for (int k = 0; k < NF; ++k) { zr[k] = R(0); zi[k] = R(0); }
-        PT S = Ph::zero();
-        ArmTracker<R> trk;
-        if constexpr (MODEL == SYNAX_MODEL_JF12) {
-            if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
-        }
-
-        for (int n = n0; n < n1; ++n) {
-            if constexpr (MODEL == SYNAX_MODEL_JF12) {
-                if (n > n0) trk.step(+1);
-            }
-            const R nh = R(n) + R(0.5);
-            const R t = fma(nh, dr, nh * dr_lo);         // (n + 1/2) dr, dr as hi + lo
-            const R x = P.obs[0] + t * L.n[0];
-            const R y = P.obs[1] + t * L.n[1];
-            const R z = P.obs[2] + t * L.n[2];
-            R B[3], N0, ne;
-            ArmCoord<R> ac{0, R(0)};
-            if constexpr (MODEL == SYNAX_MODEL_JF12) ac = trk.coord(x, y, M<R>::sqrt(x * x + y * y));
-            Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne);
-            const Emit<R> e = emit<R>(B, N0, ne, L, P.q);
-            accI += e.jI;
-            const PT s_n = Ph::add(S, P.w_own * e.f);    // RM at the midpoint (Eq. 7)
-            S = Ph::add(S, e.f);
-#pragma unroll
-            for (int k = 0; k < NF; ++k) {
-                if (k < P.n_freq) {
-                    R sn, cs;
-                    M<R>::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
-                    zr[k] += e.pc * cs - e.ps * sn;       // (pc + i ps) e^{i phi}
-                    zi[k] += e.pc * sn + e.ps * cs;
-                }
-            }
-        }
+        PT S;
+        march_lane<MODEL, NF, R>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
 
         // RM offset of this lane's chunk, then rotate its partial sums.
         const PT O = warp_exclusive_scan<R>(S, lane);

@@ -510,13 +510,34 @@ template <> struct ArmTracker<float> {
     }
 };
 
+// Intermediates of a field evaluation kept for the adjoint (parameter
+// derivatives of B, N0, n_e at the sample).  The forward march ignores them.
+template <typename R>
+struct FieldLocal {
+    R c, s;              // rho-hat = (c, s)
+    R az, rho, ri;
+    // WMAP-type
+    R env, cpsi, spsi, cchi, schi, lnr8, thz, in_range;
+    // JF12-type
+    R disc_unit;         // 5 W (1 - L(z)) / rho, so that |B_disc| = beta * disc_unit
+    int ka, kb;          // arms blended at this point and their weights
+    R wa, wb;
+    R halo_unit;         // B_halo = B_h * halo_unit (phi-hat)
+    R rp, xe, xmag_unit; // X field: rp, e^{-rp/4.8}, |B_X| / B_X
+    R sz;
+    R ne1, ne2;          // thick and thin n_e discs
+    // both
+    R n0_unit;           // N0 / N0_obs
+    R ne_unit;           // WMAP: n_e / ne0
+};
+
 template <int MODEL> struct Model;
 
 template <> struct Model<SYNAX_MODEL_TOY> {
     template <typename R>
     static __device__ __forceinline__ void eval(const R* m, const R* /*arms*/, R t, R /*x*/, R /*y*/,
                                                 R /*z*/, const ArmCoord<R>& /*ac*/, R B[3], R& N0,
-                                                R& ne) {
+                                                R& ne, FieldLocal<R>& /*loc*/) {
         const bool in = t < m[mc::TOY_R0];
         B[0] = in ? m[mc::TOY_B + 0] : R(0);
         B[1] = in ? m[mc::TOY_B + 1] : R(0);
@@ -529,7 +550,8 @@ template <> struct Model<SYNAX_MODEL_TOY> {
 template <> struct Model<SYNAX_MODEL_WMAP> {
     template <typename R>
     static __device__ __forceinline__ void eval(const R* m, const R* /*arms*/, R /*t*/, R x, R y, R z,
-                                                const ArmCoord<R>& /*ac*/, R B[3], R& N0, R& ne) {
+                                                const ArmCoord<R>& /*ac*/, R B[3], R& N0, R& ne,
+                                                FieldLocal<R>& loc) {
         using F = M<R>;
         const R rho2 = x * x + y * y;
         const bool has_rho = rho2 > R(0);
@@ -540,13 +562,17 @@ template <> struct Model<SYNAX_MODEL_WMAP> {
         const R e2 = F::exp(R(-2) * az);                      // e^{-2|z|}
         const R inv1 = F::div(R(1), R(1) + e2);
         const R sech2 = R(4) * e2 * inv1 * inv1;
-        R psi = R(0), chi = R(0);
-        if (rho >= R(3) && rho <= R(20)) {
-            psi = m[mc::W_PSI0] + m[mc::W_PSI1] * F::log(F::div(rho, R(8)));
-            const R th = (R(1) - e2) * inv1;                 // tanh |z|
-            chi = m[mc::W_CHI0] * (z < R(0) ? -th : th);
+        R psi = R(0), chi = R(0), lnr8 = R(0), th = R(0);
+        const bool in_range = rho >= R(3) && rho <= R(20);
+        if (in_range) {
+            lnr8 = F::log(F::div(rho, R(8)));
+            psi = m[mc::W_PSI0] + m[mc::W_PSI1] * lnr8;
+            th = (R(1) - e2) * inv1;                         // tanh |z|
+            th = z < R(0) ? -th : th;
+            chi = m[mc::W_CHI0] * th;
         }
-        const R amp = m[mc::W_B0] * F::exp(-(F::mulc(rho, 0.125) + az));
+        const R env = F::exp(-(F::mulc(rho, 0.125) + az));
+        const R amp = m[mc::W_B0] * env;
         R sp, cp, sc, cc;
         F::sincos(psi, &sp, &cp);
         F::sincos(chi, &sc, &cc);
@@ -554,15 +580,22 @@ template <> struct Model<SYNAX_MODEL_WMAP> {
         B[0] = br * c - bp * s + m[mc::W_BUX];
         B[1] = br * s + bp * c;
         B[2] = amp * sc;
-        N0 = cr_density<R>(m[mc::W_N0N], rho, az);
-        ne = m[mc::W_NE0] * F::exp(-F::mulc(rho, 0.05)) * sech2;
+        const R n0u = cr_density<R>(m[mc::W_N0U], rho, az);
+        N0 = m[mc::W_N0OBS] * n0u;
+        const R neu = F::exp(-F::mulc(rho, 0.05)) * sech2;
+        ne = m[mc::W_NE0] * neu;
+        loc.c = c; loc.s = s; loc.az = az; loc.rho = rho;
+        loc.env = env; loc.cpsi = cp; loc.spsi = sp; loc.cchi = cc; loc.schi = sc;
+        loc.lnr8 = lnr8; loc.thz = th; loc.in_range = in_range ? R(1) : R(0);
+        loc.n0_unit = n0u; loc.ne_unit = neu;
     }
 };
 
 template <> struct Model<SYNAX_MODEL_JF12> {
     template <typename R>
     static __device__ __forceinline__ void eval(const R* m, const R* arms, R /*t*/, R x, R y, R z,
-                                                const ArmCoord<R>& ac, R B[3], R& N0, R& ne) {
+                                                const ArmCoord<R>& ac, R B[3], R& N0, R& ne,
+                                                FieldLocal<R>& loc) {
         using F = M<R>;
         const R rho2 = x * x + y * y;
         const bool has_rho = rho2 > R(0);
@@ -575,6 +608,7 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         R Lz, omLz;
         logistic_pair<R>(az, 0.4, 0.27, Lz, omLz);
         R br = R(0), bp = R(0), bz = R(0);
+        loc.disc_unit = R(0); loc.ka = 0; loc.kb = 0; loc.wa = R(0); loc.wb = R(0);
 
         // disc: 8 smooth log-spiral arms inside a smooth radial window
         const R W = smoothstep01<R>((rho - R(4.75)) * R(2)) * smoothstep01<R>((R(20.25) - rho) * R(2));
@@ -583,28 +617,34 @@ template <> struct Model<SYNAX_MODEL_JF12> {
             const R f = ac.f;
             // b_k at the arm centre u = k + 1/2, C^1 smoothstep towards the
             // neighbouring centre on either side
-            R beta;
+            int ka, kb;
+            R wgt;
             if (f < R(0.5)) {
-                const R prev = arms[(k + 7) & 7];
-                beta = prev + (arms[k] - prev) * smoothstep01<R>(f + R(0.5));
+                ka = (k + 7) & 7; kb = k; wgt = smoothstep01<R>(f + R(0.5));
             } else {
-                const R cur = arms[k];
-                beta = cur + (arms[(k + 1) & 7] - cur) * smoothstep01<R>(f - R(0.5));
+                ka = k; kb = (k + 1) & 7; wgt = smoothstep01<R>(f - R(0.5));
             }
-            const R amp = beta * R(5) * ri * W * omLz;
+            const R beta = arms[ka] + (arms[kb] - arms[ka]) * wgt;
+            const R unit = R(5) * ri * W * omLz;
+            const R amp = beta * unit;
             br += amp * R(kPitchSin);
             bp += amp * R(kPitchCos);
+            loc.disc_unit = unit; loc.ka = ka; loc.kb = kb; loc.wa = R(1) - wgt; loc.wb = wgt;
         }
 
         // toroidal halo: (1 - L(rho; 9.22, 0.2)) is the second member of the pair
         R Lr, omLr;
         logistic_pair<R>(rho, 9.22, 0.2, Lr, omLr);
-        bp += m[mc::J_BH] * F::exp(-F::div(az, m[mc::J_ZH])) * Lz * omLr * sz;
+        const R hu = F::exp(-F::div(az, m[mc::J_ZH])) * Lz * omLr * sz;
+        bp += m[mc::J_BH] * hu;
 
         // X field
         const R rp = rho - az * m[mc::J_COTX];
+        R xe = R(0), xu = R(0);
         if (rp > R(0)) {
-            const R mag = m[mc::J_BX] * F::exp(-F::mulc(rp, 1.0 / 4.8)) * rp * ri;
+            xe = F::exp(-F::mulc(rp, 1.0 / 4.8));
+            xu = xe * rp * ri;
+            const R mag = m[mc::J_BX] * xu;
             br += mag * sz * m[mc::J_COSX];
             bz += mag * m[mc::J_SINX];
         }
@@ -612,9 +652,14 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         B[1] = br * s + bp * c;
         B[2] = bz;
 
-        N0 = cr_density<R>(m[mc::J_N0N], rho, az);
-        ne = R(0.025) * F::exp(-(F::mulc(rho, 0.05) + F::div(az, m[mc::J_H1]))) +
-             R(0.10) * F::exp(-(F::mulc(rho, 0.25) + F::div(az, m[mc::J_H2])));
+        const R n0u = cr_density<R>(m[mc::J_N0U], rho, az);
+        N0 = m[mc::J_N0OBS] * n0u;
+        const R ne1 = R(0.025) * F::exp(-(F::mulc(rho, 0.05) + F::div(az, m[mc::J_H1])));
+        const R ne2 = R(0.10) * F::exp(-(F::mulc(rho, 0.25) + F::div(az, m[mc::J_H2])));
+        ne = ne1 + ne2;
+        loc.c = c; loc.s = s; loc.az = az; loc.rho = rho; loc.ri = ri;
+        loc.halo_unit = hu; loc.rp = rp; loc.xe = xe; loc.xmag_unit = xu; loc.sz = sz;
+        loc.ne1 = ne1; loc.ne2 = ne2; loc.n0_unit = n0u;
     }
 };
 
@@ -649,6 +694,71 @@ __device__ __forceinline__ Emit<R> emit(const R B[3], R N0, R ne, const Los<R>& 
     e.ps = nw * (R(2) * bl * bb);
     e.f = -ne * bn;
     return e;
+}
+
+}  // namespace synax
+
+namespace synax {
+
+// One lane's share of the forward march of one ray (Sec. 2.3, Eq. 2, 5-9):
+// samples [n0, n1) of the ray with LOS triad L (and double-float direction
+// nd for the FP32 arm tracker).  Returns the lane's sum of j_I terms, per
+// frequency the complex sum of j_P e^{2i chi_0} e^{i phi_local} (phase of the
+// RM accumulated from the chunk start), and the chunk total S of
+// f = n_e B_par (Eq. 7 integrand).
+template <int MODEL, int NF, typename R>
+__device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arms, const Los<R>& L,
+                                           const ff* nd, int n0, int n1, R dr, R dr_lo,
+                                           const typename PhaseOps<R>::T* cd, R& accI, R* zr, R* zi,
+                                           typename PhaseOps<R>::T& S) {
+    using Ph = PhaseOps<R>;
+    using PT = typename Ph::T;
+    accI = R(0);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) { zr[k] = R(0); zi[k] = R(0); }
+    S = Ph::zero();
+    ArmTracker<R> trk;
+    if constexpr (MODEL == SYNAX_MODEL_JF12) {
+        if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
+    }
+    for (int n = n0; n < n1; ++n) {
+        if constexpr (MODEL == SYNAX_MODEL_JF12) {
+            if (n > n0) trk.step(+1);
+        }
+        const R nh = R(n) + R(0.5);
+        const R t = fma(nh, dr, nh * dr_lo);            // (n + 1/2) dr, dr as hi + lo
+        const R x = P.obs[0] + t * L.n[0];
+        const R y = P.obs[1] + t * L.n[1];
+        const R z = P.obs[2] + t * L.n[2];
+        R B[3], N0, ne;
+        ArmCoord<R> ac{0, R(0)};
+        if constexpr (MODEL == SYNAX_MODEL_JF12) ac = trk.coord(x, y, M<R>::sqrt(x * x + y * y));
+        FieldLocal<R> loc;
+        Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
+        const Emit<R> e = emit<R>(B, N0, ne, L, P.q);
+        accI += e.jI;
+        const PT s_n = Ph::add(S, P.w_own * e.f);      // RM at the midpoint (Eq. 7)
+        S = Ph::add(S, e.f);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            if (k < P.n_freq) {
+                R sn, cs;
+                M<R>::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
+                zr[k] += e.pc * cs - e.ps * sn;         // (pc + i ps) e^{i phi}
+                zi[k] += e.pc * sn + e.ps * cs;
+            }
+        }
+    }
+}
+
+// Per-ray LOS setup shared by the kernels.
+template <typename R>
+__device__ __forceinline__ void ray_setup(const MapParams<R>& P, long long ray, Los<R>& L, ff* nd, R& dr,
+                                          R& dr_lo) {
+    if constexpr (sizeof(R) == 4) healpix_los_dd(P.nside, P.pix_begin + ray, L, nd);
+    else healpix_los<R>(P.nside, P.pix_begin + ray, L);
+    dr = P.box_clip ? box_exit<R>(P.obs, P.box_half, L.n) / R(P.n_steps) : P.dr;
+    dr_lo = P.box_clip ? R(0) : P.dr_lo;
 }
 
 }  // namespace synax
