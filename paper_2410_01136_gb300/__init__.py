@@ -22,7 +22,7 @@ __all__ = ["forward", "adjoint", "eval_fields", "adjoint_workspace_bytes", "Syna
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    from .build import build as _build
+    from .cuda_build import build as _build
     return _build(force=force, verbose=verbose)
 
 

@@ -87,7 +87,7 @@ def lib():
                 raise RuntimeError(
                     f"libsynax is not built ({LIB_PATH} missing); run "
                     "`python -c 'import __graft_entry__ as g; g.build()'` or "
-                    "`python paper_2410_01136_gb300/build.py`")
+                    "`python paper_2410_01136_gb300/cuda_build.py`")
             L = ctypes.CDLL(LIB_PATH)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(L, name)

@@ -158,3 +158,10 @@ def test_problem_struct_roundtrip():
     assert s.nside == 64 and s.n_steps == 512 and s.n_freq == 4 and s.n_theta == 16
     assert s.flags == _native.SYNAX_F64 and s.rm_rule == 2 and s.pix_begin == 5 and s.pix_count == 7
     assert np.allclose(list(s.theta)[:16], p.theta)
+
+
+def test_build_function_not_shadowed_by_submodule():
+    import paper_2410_01136_gb300 as pkg
+    pkg.build()
+    from paper_2410_01136_gb300 import build
+    assert callable(build)
