@@ -119,6 +119,26 @@ int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* 
                   double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
                   void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* synax_adjoint without a caller-provided workspace (the paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory, e.g. a host program that links only this library and the CUDA
+ * runtime and has no device allocator of its own, or code that must not
+ * allocate, and so synchronise the device, inside its sampling loop).
+ * Arguments and results are those of synax_adjoint; the scratch partials live
+ * in a 4 MiB array compiled into the library, held on every GPU that loads
+ * it until the process exits, so the call allocates nothing.  Problems whose
+ * workspace (synax_adjoint_workspace_bytes) exceeds 4 MiB are rejected with
+ * SYNAX_ESPACE before anything is enqueued: up to 246,720 pixels (Nside 128)
+ * for the 16-parameter JF12-type model, 466,032 for the 8-parameter
+ * WMAP-type model.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make it before
+ * any stream capture.  Every call shares the array and it keeps the last
+ * call's contents (nothing needs clearing: each call writes what it reads),
+ * so calls that overlap on the GPU race and must be serialised by the caller. */
+int synax_adjoint_noalloc(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
+                          double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
+                          void* stream);
+
 /* Field models evaluated at arbitrary points (diagnostics and unit tests of
  * the device field code, which is the code the march runs).
  * pos_dev: [n][3] doubles (kpc, galactocentric); t_dev: [n] doubles, the

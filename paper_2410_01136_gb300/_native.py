@@ -64,6 +64,9 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                      ctypes.c_void_p]),
+    "synax_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "synax_eval_fields": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                          ctypes.c_void_p]),
