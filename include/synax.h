@@ -148,6 +148,15 @@ int synax_adjoint_noalloc(const synax_problem* prob, const void* gmaps_dev, cons
 int synax_eval_fields(const synax_problem* prob, const double* pos_dev, const double* t_dev,
                       int64_t n, double* out_dev, void* stream);
 
+/* Launch tuning (no counterpart in the paper): lanes of a warp that march
+ * one ray, 8, 16 or 32.  lanes = 0 restores the built-in rule.  With
+ * n_steps_min >= 0 the value applies to maps whose step count falls in the
+ * tuning bin containing n_steps_min (bins edges 64, 128, 256, ..., 4096);
+ * with n_steps_min < 0 it is forced for every map.  Results do not depend on
+ * the choice beyond rounding; the autotuner (paper_2410_01136_gb300/tune.py)
+ * measures the candidates and installs the fastest.  Process-wide setting. */
+int synax_set_lanes_per_ray(int n_steps_min, int lanes);
+
 /* Last CUDA error code seen by this thread in a call that returned SYNAX_ECUDA. */
 int synax_last_cuda_error(void);
 

@@ -70,6 +70,7 @@ SIGNATURES = {
     "synax_eval_fields": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                          ctypes.c_void_p]),
+    "synax_set_lanes_per_ray": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "synax_last_cuda_error": (ctypes.c_int, []),
     "synax_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "synax_version": (ctypes.c_int, []),

@@ -213,6 +213,7 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         for (int k = 0; k < 8; ++k) M.m[mc::J_B + k] = R(th[k]);
         M.m[mc::J_BH] = R(th[8]);
         M.m[mc::J_IZH] = R(1.0 / th[9]);
+        M.m[mc::J_IZH_LO] = R(1.0 / th[9] - (double)R(1.0 / th[9]));
         M.m[mc::J_BX] = R(th[10]);
         M.m[mc::J_COSX] = R(std::cos(th[11]));
         M.m[mc::J_SINX] = R(std::sin(th[11]));
@@ -221,6 +222,8 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         M.m[mc::J_N0U] = R(1.0 / cr_profile(P.obs_kpc));
         M.m[mc::J_IH1] = R(1.0 / th[14]);
         M.m[mc::J_IH2] = R(1.0 / th[15]);
+        M.m[mc::J_IH1_LO] = R(1.0 / th[14] - (double)R(1.0 / th[14]));
+        M.m[mc::J_IH2_LO] = R(1.0 / th[15] - (double)R(1.0 / th[15]));
         M.m[mc::J_ZH] = R(th[9]);
         M.m[mc::J_THX] = R(th[11]);
         M.m[mc::J_H1] = R(th[14]);

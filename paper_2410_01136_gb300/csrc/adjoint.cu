@@ -29,8 +29,7 @@
 
 namespace synax {
 
-constexpr int kAdjRays = 8;
-constexpr int kAdjThreads = 32 * kAdjRays;
+constexpr int kAdjThreads = 256;
 
 template <int MODEL> struct Grad;
 
@@ -86,7 +85,7 @@ template <> struct Grad<SYNAX_MODEL_WMAP> {
     }
 };
 
-template <int MODEL, int NF, typename R>
+template <int MODEL, int NF, int LPR, typename R>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmaps,
           const R* __restrict__ target, R* __restrict__ maps_out, double* __restrict__ partial) {
@@ -94,12 +93,16 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
     using PT = typename Ph::T;
     using F = M<R>;
     constexpr int NT = Grad<MODEL>::NT;
+    constexpr int RAYS = kAdjThreads / LPR;
+    constexpr int WARPS = kAdjThreads / 32;
     __shared__ R s_arms[8];
-    __shared__ R s_stage[3 * NF][kAdjRays];
-    __shared__ double s_part[kAdjRays][NT + 1];
+    __shared__ R s_stage[3 * NF][RAYS];
+    __shared__ double s_part[WARPS][NT + 1];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    const int sub = lane & (LPR - 1);
+    const int slot = threadIdx.x / LPR;
     if (threadIdx.x < 8) s_arms[threadIdx.x] = P.m[threadIdx.x];
     __syncthreads();
 
@@ -108,25 +111,30 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
     for (int j = 0; j < NT; ++j) g[j] = R(0);
     R chi2_ray = R(0);
 
-    const long long ray = (long long)blockIdx.x * kAdjRays + warp;
-    if (ray < P.n_pix) {
+    const long long ray0 = (long long)blockIdx.x * RAYS;
+    const long long ray = ray0 + slot;
+    const long long warp_first = ray0 + (long long)warp * (32 / LPR);
+    if (warp_first < P.n_pix) {
+        // idle segments (past the end of the map) march a valid ray with zero seeds
+        const bool live = ray < P.n_pix;
+        const long long r_eff = live ? ray : P.n_pix - 1;
         Los<R> L;
         ff nd[3];
         R dr, dr_lo;
-        ray_setup<R>(P, ray, L, nd, dr, dr_lo);
+        ray_setup<R>(P, r_eff, L, nd, dr, dr_lo);
         PT cd[NF];
 #pragma unroll
         for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale(P.crev[k], dr) : P.cdr[k];
         const int N = P.n_steps;
-        const int n0 = (int)(((long long)lane * N) >> 5);
-        const int n1 = (int)(((long long)(lane + 1) * N) >> 5);
+        const int n0 = (int)(((long long)sub * N) / LPR);
+        const int n1 = (int)(((long long)(sub + 1) * N) / LPR);
 
         // ---- pass 1: forward march of the lane, RM offset, rotation ----
         R accI;
         R zr[NF], zi[NF];
         PT S;
         march_lane<MODEL, NF, R>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
-        const PT O = warp_exclusive_scan<R>(S, lane);
+        const PT O = seg_exclusive_scan<LPR, R>(S, sub);
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
             if (k < P.n_freq) {
@@ -140,7 +148,7 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
         }
 
         // ---- maps of this ray, seeds, per-ray adjoint constants ----
-        const R accI_t = warp_sum<R>(accI);
+        const R accI_t = seg_sum<LPR, R>(accI);
         R hr[NF], hi[NF], c2[NF];
         R GI = R(0), GIp = R(0), D = R(0);
 #pragma unroll
@@ -149,19 +157,21 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
             hi[k] = R(0);
             c2[k] = R(0);
             if (k < P.n_freq) {
-                const R zr_t = warp_sum<R>(zr[k]);
-                const R zi_t = warp_sum<R>(zi[k]);
+                const R zr_t = seg_sum<LPR, R>(zr[k]);
+                const R zi_t = seg_sum<LPR, R>(zi[k]);
                 const R MI = P.aI[k] * dr * accI_t;
                 const R MQ = P.aP[k] * dr * zr_t;
                 const R MU = P.aP[k] * dr * zi_t;
-                if (lane == 0) {
-                    s_stage[3 * k + 0][warp] = MI;
-                    s_stage[3 * k + 1][warp] = MQ;
-                    s_stage[3 * k + 2][warp] = MU;
+                if (sub == 0 && live) {
+                    s_stage[3 * k + 0][slot] = MI;
+                    s_stage[3 * k + 1][slot] = MQ;
+                    s_stage[3 * k + 2][slot] = MU;
                 }
-                const long long row = (long long)(3 * k) * P.n_pix + ray;
+                const long long row = (long long)(3 * k) * P.n_pix + r_eff;
                 R gI, gQ, gU;
-                if (A.mode_chi2) {
+                if (!live) {
+                    gI = gQ = gU = R(0);
+                } else if (A.mode_chi2) {
                     const R dI = MI - target[row];
                     const R dQ = MQ - target[row + P.n_pix];
                     const R dU = MU - target[row + 2 * P.n_pix];
@@ -182,7 +192,7 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
                 D -= c2[k] * (hr[k] * zi[k] + hi[k] * zr[k]);   // -Im(h' Z_lane)
             }
         }
-        R after = warp_exclusive_suffix<R>(D, lane);
+        R after = seg_exclusive_suffix<LPR, R>(D, sub);
 
         // ---- pass 2: reverse march of the lane's chunk ----
         if (n0 < n1) {
@@ -265,8 +275,11 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
                 Grad<MODEL>::accum(P.m, loc, bxb, byb, bzb, n0bar, neb, g);
             }
         }
+        // all lanes hold partial gradients of their ray: one full-warp sum
+        // gives the warp's share of the CTA partial
 #pragma unroll
         for (int j = 0; j < NT; ++j) g[j] = warp_sum<R>(g[j]);
+        chi2_ray = warp_sum<R>(sub == 0 ? chi2_ray : R(0));
     }
     if (lane == 0) {
 #pragma unroll
@@ -277,16 +290,15 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
     if (threadIdx.x <= NT) {
         double acc = 0.0;
 #pragma unroll
-        for (int w = 0; w < kAdjRays; ++w) acc += s_part[w][threadIdx.x];
+        for (int w = 0; w < WARPS; ++w) acc += s_part[w][threadIdx.x];
         partial[(long long)blockIdx.x * (NT + 1) + threadIdx.x] = acc;
     }
     if (maps_out) {
-        const long long base = (long long)blockIdx.x * kAdjRays;
         const int rows = 3 * P.n_freq;
-        for (int idx = threadIdx.x; idx < rows * kAdjRays; idx += kAdjThreads) {
-            const int row = idx / kAdjRays;
-            const int col = idx - row * kAdjRays;
-            const long long r = base + col;
+        for (int idx = threadIdx.x; idx < rows * RAYS; idx += kAdjThreads) {
+            const int row = idx / RAYS;
+            const int col = idx - row * RAYS;
+            const long long r = ray0 + col;
             if (r < P.n_pix) maps_out[(long long)row * P.n_pix + r] = s_stage[row][col];
         }
     }
@@ -312,23 +324,36 @@ k_reduce_partials(const double* __restrict__ partial, long long n_blocks, int n_
     }
 }
 
-static long long adj_blocks(long long n_pix) { return (n_pix + kAdjRays - 1) / kAdjRays; }
-
-size_t adjoint_workspace_bytes(long long n_pix, int n_theta) {
-    return (size_t)adj_blocks(n_pix) * (size_t)(n_theta + 1) * sizeof(double);
+static long long adj_blocks(long long n_pix, int lpr) {
+    const int rays = kAdjThreads / lpr;
+    return (n_pix + rays - 1) / rays;
 }
 
-template <int MODEL, int NF, typename R>
-static int launch_adj_nf(const MapParams<R>& P, const AdjParams<R>& A, const R* gmaps, const R* target,
-                         double* grad, double* chi2, R* maps, double* partial, cudaStream_t st) {
+// Sized for the largest grid (32 lanes per ray), whatever the tuning picks.
+size_t adjoint_workspace_bytes(long long n_pix, int n_theta) {
+    return (size_t)adj_blocks(n_pix, 32) * (size_t)(n_theta + 1) * sizeof(double);
+}
+
+template <int MODEL, int NF, int LPR, typename R>
+static int launch_adj_lpr(const MapParams<R>& P, const AdjParams<R>& A, const R* gmaps, const R* target,
+                          double* grad, double* chi2, R* maps, double* partial, cudaStream_t st) {
     constexpr int NT = Grad<MODEL>::NT;
-    const long long blocks = adj_blocks(P.n_pix);
-    k_adjoint<MODEL, NF, R><<<(unsigned)blocks, kAdjThreads, 0, st>>>(P, A, gmaps, target, maps, partial);
+    const long long blocks = adj_blocks(P.n_pix, LPR);
+    k_adjoint<MODEL, NF, LPR, R><<<(unsigned)blocks, kAdjThreads, 0, st>>>(P, A, gmaps, target, maps, partial);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return record_cuda_error((int)err);
     k_reduce_partials<<<NT + 1, 256, 0, st>>>(partial, blocks, NT + 1, NT, grad, chi2);
     err = cudaGetLastError();
     return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
+}
+
+template <int MODEL, int NF, typename R>
+static int launch_adj_nf(const MapParams<R>& P, const AdjParams<R>& A, const R* gmaps, const R* target,
+                         double* grad, double* chi2, R* maps, double* partial, cudaStream_t st) {
+    const int lpr = lanes_per_ray(P.n_steps, P.n_pix);
+    if (lpr == 8) return launch_adj_lpr<MODEL, NF, 8, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
+    if (lpr == 16) return launch_adj_lpr<MODEL, NF, 16, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
+    return launch_adj_lpr<MODEL, NF, 32, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
 }
 
 template <int MODEL, typename R>

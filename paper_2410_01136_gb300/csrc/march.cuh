@@ -81,6 +81,19 @@ template <> struct M<float> {
         const float lo = (float)(c - (double)hi);
         return fmaf(x, hi, x * lo);
     }
+    // 1/x and 1/sqrt(x) from the PTX approximation plus one Newton step
+    // whose residual is formed with an FMA (error ~1 ulp, no systematic sign).
+    static __device__ __forceinline__ float rcp_nr(float x) {
+        const float y = rcp_approx(x);
+        return fmaf(y, fmaf(-x, y, 1.0f), y);
+    }
+    static __device__ __forceinline__ float rsqrt_nr(float x) {
+        const float y = rsqrt_approx(x);
+        const float h = x * y;
+        return fmaf(0.5f * y, fmaf(-h, y, 1.0f), y);
+    }
+    // x * c for a runtime constant given as hi + lo
+    static __device__ __forceinline__ float mul_hl(float x, float hi, float lo) { return fmaf(x, hi, x * lo); }
     static __device__ __forceinline__ float exp2_fast(float x) { return ex2_approx(x); }
     static __device__ __forceinline__ float log2_fast(float x) { return lg2_approx(x); }
     static __device__ __forceinline__ float rcp_fast(float x) { return rcp_approx(x); }
@@ -106,6 +119,9 @@ template <> struct M<double> {
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
     static __device__ __forceinline__ double mulc(double x, double c) { return x * c; }
+    static __device__ __forceinline__ double rcp_nr(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double rsqrt_nr(double x) { return 1.0 / ::sqrt(x); }
+    static __device__ __forceinline__ double mul_hl(double x, double hi, double lo) { return x * (hi + lo); }
     static __device__ __forceinline__ double exp2_fast(double x) { return ::exp2(x); }
     static __device__ __forceinline__ double log2_fast(double x) { return ::log2(x); }
     static __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
@@ -170,11 +186,8 @@ template <> struct PhaseOps<float> {
         float k = rintf(p);
         return __fadd_rn(__fsub_rn(p, k), e);
     }
-    static __device__ __forceinline__ T shfl_up(T v, int d) {
-        return ff{__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
-    }
-    static __device__ __forceinline__ T shfl_down(T v, int d) {
-        return ff{__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+    static __device__ __forceinline__ T shfl_up(T v, int d, int width) {
+        return ff{__shfl_up_sync(0xffffffffu, v.hi, d, width), __shfl_up_sync(0xffffffffu, v.lo, d, width)};
     }
     static __device__ __forceinline__ T neg(T v) { return ff{-v.hi, -v.lo}; }
     static __device__ __forceinline__ float to_real(T v) { return v.hi + v.lo; }
@@ -189,8 +202,9 @@ template <> struct PhaseOps<double> {
         double x = c * s;
         return x - rint(x);
     }
-    static __device__ __forceinline__ T shfl_up(T v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
-    static __device__ __forceinline__ T shfl_down(T v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+    static __device__ __forceinline__ T shfl_up(T v, int d, int width) {
+        return __shfl_up_sync(0xffffffffu, v, d, width);
+    }
     static __device__ __forceinline__ T neg(T v) { return -v; }
     static __device__ __forceinline__ double to_real(T v) { return v; }
 };
@@ -202,30 +216,38 @@ __device__ __forceinline__ R warp_sum(R v) {
     return v;
 }
 
-// Exclusive prefix sum of a per-lane phase value across the warp
-// (Kogge-Stone inclusive scan, then shift by one lane).
-template <typename R>
-__device__ __forceinline__ typename PhaseOps<R>::T warp_exclusive_scan(typename PhaseOps<R>::T v, int lane) {
-    using Ph = PhaseOps<R>;
+// Sum over a segment of L consecutive lanes (L a power of two <= 32).
+template <int L, typename R>
+__device__ __forceinline__ R seg_sum(R v) {
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        auto o = Ph::shfl_up(v, d);
-        if (lane >= d) v = Ph::add(v, o);
-    }
-    auto e = Ph::shfl_up(v, 1);
-    return lane == 0 ? Ph::zero() : e;
+    for (int d = L / 2; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
 }
 
-// Exclusive suffix sum (sum over higher lanes) of a plain value.
-template <typename R>
-__device__ __forceinline__ R warp_exclusive_suffix(R v, int lane) {
+// Exclusive prefix sum of a per-lane phase value over a segment of L lanes
+// (Kogge-Stone inclusive scan, then shift by one lane); sub = lane % L.
+template <int L, typename R>
+__device__ __forceinline__ typename PhaseOps<R>::T seg_exclusive_scan(typename PhaseOps<R>::T v, int sub) {
+    using Ph = PhaseOps<R>;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        R o = __shfl_down_sync(0xffffffffu, v, d);
-        if (lane + d < 32) v += o;
+    for (int d = 1; d < L; d <<= 1) {
+        auto o = Ph::shfl_up(v, d, L);
+        if (sub >= d) v = Ph::add(v, o);
     }
-    R e = __shfl_down_sync(0xffffffffu, v, 1);
-    return lane == 31 ? R(0) : e;
+    auto e = Ph::shfl_up(v, 1, L);
+    return sub == 0 ? Ph::zero() : e;
+}
+
+// Exclusive suffix sum (sum over higher lanes of the segment) of a plain value.
+template <int L, typename R>
+__device__ __forceinline__ R seg_exclusive_suffix(R v, int sub) {
+#pragma unroll
+    for (int d = 1; d < L; d <<= 1) {
+        R o = __shfl_down_sync(0xffffffffu, v, d, L);
+        if (sub + d < L) v += o;
+    }
+    R e = __shfl_down_sync(0xffffffffu, v, 1, L);
+    return sub == L - 1 ? R(0) : e;
 }
 
 // ---------------------------------------------------------------------------
@@ -379,7 +401,7 @@ template <typename R>
 __device__ __forceinline__ void logistic_pair(R x, double h, double w, R& L, R& omL) {
     using F = M<R>;
     const R e = F::exp(F::mulc(x - R(h), 2.0 / w));          // e^{2(x-h)/w}, may be +inf
-    omL = F::div(R(1), R(1) + e);
+    omL = e < R(1e30) ? F::rcp_nr(R(1) + e) : R(0);
     L = e > R(1) ? R(1) - omL : e * omL;
 }
 
@@ -600,11 +622,11 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         const R rho2 = x * x + y * y;
         const bool has_rho = rho2 > R(0);
         const R rho = F::sqrt(rho2);
-        const R ri = has_rho ? F::div(R(1), rho) : R(0);
+        const R ri = has_rho ? F::rcp_nr(rho) : R(0);
         const R c = has_rho ? x * ri : R(1);
         const R s = has_rho ? y * ri : R(0);
         const R az = F::abs(z);
-        const R sz = F::div(z, F::sqrt(z * z + R(0.01)));                 // smooth sign
+        const R sz = z * F::rsqrt_nr(z * z + R(0.01));                    // smooth sign
         R Lz, omLz;
         logistic_pair<R>(az, 0.4, 0.27, Lz, omLz);
         R br = R(0), bp = R(0), bz = R(0);
@@ -635,7 +657,7 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         // toroidal halo: (1 - L(rho; 9.22, 0.2)) is the second member of the pair
         R Lr, omLr;
         logistic_pair<R>(rho, 9.22, 0.2, Lr, omLr);
-        const R hu = F::exp(-F::div(az, m[mc::J_ZH])) * Lz * omLr * sz;
+        const R hu = F::exp(-F::mul_hl(az, m[mc::J_IZH], m[mc::J_IZH_LO])) * Lz * omLr * sz;
         bp += m[mc::J_BH] * hu;
 
         // X field
@@ -654,8 +676,8 @@ template <> struct Model<SYNAX_MODEL_JF12> {
 
         const R n0u = cr_density<R>(m[mc::J_N0U], rho, az);
         N0 = m[mc::J_N0OBS] * n0u;
-        const R ne1 = R(0.025) * F::exp(-(F::mulc(rho, 0.05) + F::div(az, m[mc::J_H1])));
-        const R ne2 = R(0.10) * F::exp(-(F::mulc(rho, 0.25) + F::div(az, m[mc::J_H2])));
+        const R ne1 = R(0.025) * F::exp(-(F::mulc(rho, 0.05) + F::mul_hl(az, m[mc::J_IH1], m[mc::J_IH1_LO])));
+        const R ne2 = R(0.10) * F::exp(-(F::mulc(rho, 0.25) + F::mul_hl(az, m[mc::J_IH2], m[mc::J_IH2_LO])));
         ne = ne1 + ne2;
         loc.c = c; loc.s = s; loc.az = az; loc.rho = rho; loc.ri = ri;
         loc.halo_unit = hu; loc.rp = rp; loc.xe = xe; loc.xmag_unit = xu; loc.sz = sz;
