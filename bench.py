@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="synax", choices=["synax", "reference"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-set ensemble measurement")
     return ap.parse_args()
 
 
@@ -182,6 +183,57 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def bench_batch(sx, inputs, torch, dev, n_runs: int = 3, sets=None, name=None) -> dict:
+    """An ensemble of map+gradient evaluations: one persistent graph-captured
+    launch per evaluation, against the same sets as one-map synax_adjoint
+    calls in a row.  Default: the 256-set ensemble (Nside 16-128, 128-1024
+    steps, theta ~ 5% around the fiducial)."""
+    import numpy as np
+    sets = inputs.config4() if sets is None else sets
+    targets = []
+    for i, p in enumerate(sets):
+        t = sx.forward(p.with_theta(inputs.perturbed_theta(p.theta, seed=100 + i))).contiguous()
+        targets.append(t)
+    samples = sum(p.samples for p in sets)
+    plan = sx.BatchPlan(sets)
+    info = plan.info()
+    stream = torch.cuda.current_stream(dev)
+    grads, chi2 = plan.run(targets=targets, sigma=0.5)            # captures the graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n_runs):
+        plan.run(targets=targets, sigma=0.5, grads=grads, chi2=chi2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / n_runs
+    lat = plan.latencies()
+    plan.close()
+    ws = torch.empty(max(sx.adjoint_workspace_bytes(p) for p in sets), dtype=torch.uint8, device=dev)
+    for p, t in zip(sets[:4], targets[:4]):
+        sx.adjoint(p, target=t, sigma=0.5, workspace=ws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for p, t in zip(sets, targets):
+        sx.adjoint(p, target=t, sigma=0.5, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    return {
+        "workload": name or "256 JF12-type sets, Nside {16..128} x steps {128..1024}, chi^2 map+gradient",
+        "samples_per_run": samples,
+        "ms_per_run": ms_batch,
+        "samples_per_s": samples / (ms_batch * 1e-3),
+        "maps_grad_per_s": len(sets) / (ms_batch * 1e-3),
+        "latency_ms_p50": float(np.percentile(lat, 50)),
+        "latency_ms_p99": float(np.percentile(lat, 99)),
+        "sequential_ms": ms_seq,
+        "sequential_maps_grad_per_s": len(sets) / (ms_seq * 1e-3),
+        "speedup_vs_sequential": ms_seq / ms_batch,
+        "plan": info,
+    }
+
+
 def run_synax(args):
     import numpy as np
     import torch
@@ -196,8 +248,9 @@ def run_synax(args):
     dev = torch.device("cuda", torch.cuda.current_device())
 
     import paper_2410_01136_gb300 as sx
-    from paper_2410_01136_gb300 import inputs
+    from paper_2410_01136_gb300 import inputs, tune
     sx.build()
+    lanes_table = tune.load_or_tune()          # launch width per step-count bin (cached per device)
 
     prob, th_target, sigma = inputs.config3(seed=3 + rank)
     # target: forward map of the perturbed parameters plus N(0, sigma^2) noise
@@ -328,7 +381,14 @@ def run_synax(args):
                 "h2d_bytes_per_step": int(target.numel() * 4),
                 "d2h_bytes_per_step": int(maps.numel() * 4 + 16 * 8 + 8)},
         "gpu_launches": 2 * args.steps,
+        "lanes_per_ray": {str(k): v for k, v in lanes_table.items()},
     }
+    if rank == 0 and not args.no_batch:
+        out["batch"] = bench_batch(sx, inputs, torch, dev)
+        chains = [p.replace(nside=16, n_steps=256) for p in inputs.config4()]
+        out["batch_low_res"] = bench_batch(sx, inputs, torch, dev, n_runs=20, sets=chains,
+                                           name="256 chains, Nside 16, 256 steps, chi^2 map+gradient")
+        out["gpu_launches_batch_per_run"] = 2
     if rank == 0:
         try:
             rate, dt, threads, desc = oracle_map_grad_rate(8192)

@@ -119,6 +119,46 @@ int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* 
                   double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
                   void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* ---- persistent batch: many parameter sets in one launch ----
+ * An ensemble of map+gradient evaluations (e.g. the chains of an HMC
+ * sampler, each its own theta, Nside and step count) runs as one persistent
+ * kernel: tiles of rays, ordered by cost, are handed out through an atomic
+ * counter, every CTA runs the adjoint march of its tiles, and a second
+ * kernel reduces each set's partials in fixed order.  The first run captures
+ * descriptor upload, counter reset and both kernels into a CUDA graph; later
+ * runs rewrite the per-set descriptors and replay it.
+ *
+ * synax_batch_plan_create: sets[0..n_sets) share model (WMAP or JF12) and
+ * frequency count, FP32 only (SYNAX_F64 -> SYNAX_ENOTSUP), non-empty pixel
+ * ranges.  Allocates the plan's device buffers (descriptors, tile table,
+ * counters, tile partials of 8 * (n_theta + 1) bytes per tile); SYNAX_ENOMEM
+ * on failure.  The plan belongs to the device current at creation. */
+typedef struct synax_batch_plan synax_batch_plan;
+int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_plan** plan);
+
+/* Run the batch.  thetas: host array [n_sets][n_theta] of new parameters, or
+ * NULL to keep the previous ones.  seeds_dev: host array of n_sets device
+ * pointers: chi^2 targets (vjp = 0, with sigma_K as in synax_adjoint) or VJP
+ * seed maps (vjp = 1), each [n_freq][3][n_pix_s] float32.  maps_dev: NULL or
+ * a host array of n_sets device pointers (entries may be NULL) receiving the
+ * maps.  grads_dev: device [n_sets][n_theta] doubles; chi2_dev: device
+ * [n_sets] doubles or NULL.  Asynchronous on `stream`; the call waits on the
+ * host for the plan's previous run if it is still in flight, because that
+ * run reads the descriptors this one rewrites. */
+int synax_batch_run(synax_batch_plan* plan, const double* thetas, const void* const* seeds_dev, int vjp,
+                    double sigma_K, void* const* maps_dev, double* grads_dev, double* chi2_dev,
+                    void* stream);
+
+/* Per-set completion time of the last run, ms after its first tile started
+ * (device global timer); waits for the run.  ms_out: host [n_sets]. */
+int synax_batch_latencies(synax_batch_plan* plan, double* ms_out);
+
+/* Tile count, lanes per ray and persistent grid size chosen by the plan. */
+int synax_batch_plan_info(const synax_batch_plan* plan, long long* n_tiles, int* lanes_per_ray,
+                          int* grid);
+
+void synax_batch_plan_destroy(synax_batch_plan* plan);
+
 /* synax_adjoint without a caller-provided workspace (the paper has no
  * counterpart: this is an interface for callers that cannot allocate device
  * memory, e.g. a host program that links only this library and the CUDA

@@ -15,9 +15,10 @@ from __future__ import annotations
 import ctypes
 
 from . import inputs
+from . import _native
 from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
 
-__all__ = ["forward", "adjoint", "eval_fields", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
+__all__ = ["forward", "adjoint", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
            "SynaxError"]
 
 
@@ -123,6 +124,102 @@ def adjoint(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=None, wo
     if target is not None:
         return grad, chi2
     return grad
+
+
+class BatchPlan:
+    """A persistent, graph-captured batch of map+gradient evaluations
+    (synax_batch_* of include/synax.h): one launch for many parameter sets of
+    uneven Nside and step count.
+
+        plan = BatchPlan(problems)                    # allocates once
+        grads, chi2 = plan.run(targets=[...], sigma=0.5, thetas=new_thetas)
+        plan.latencies()                              # per-set completion, ms
+    """
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        n = len(self.problems)
+        arr = (_native.SynaxProblem * max(n, 1))()
+        for i, p in enumerate(self.problems):
+            arr[i] = problem_struct(p)
+        self._n = n
+        self._n_theta = len(self.problems[0].theta) if n else 0
+        h = ctypes.c_void_p()
+        check(lib().synax_batch_plan_create(arr, n, ctypes.byref(h)), "synax_batch_plan_create")
+        self._h = h
+
+    def info(self) -> dict:
+        nt = ctypes.c_longlong()
+        lpr = ctypes.c_int()
+        grid = ctypes.c_int()
+        check(lib().synax_batch_plan_info(self._h, ctypes.byref(nt), ctypes.byref(lpr), ctypes.byref(grid)),
+              "synax_batch_plan_info")
+        return {"n_tiles": nt.value, "lanes_per_ray": lpr.value, "grid": grid.value}
+
+    def run(self, targets=None, seeds=None, sigma: float = 1.0, thetas=None, maps=None, grads=None,
+            chi2=None, stream=None):
+        """chi^2 mode (targets) or VJP mode (seeds): lists of per-set CUDA tensors
+        [F, 3, n_pix_s].  thetas: [n_sets, n_theta] array or None to keep the
+        previous parameters.  Returns (grads [n_sets, n_theta], chi2 [n_sets])
+        as CUDA float64 tensors (chi2 is None in VJP mode)."""
+        import numpy as np
+        torch = _torch()
+        if (targets is None) == (seeds is None):
+            raise ValueError("give exactly one of targets (chi^2) or seeds (VJP)")
+        src = targets if targets is not None else seeds
+        if len(src) != self._n:
+            raise ValueError("one target/seed map per set")
+        for t, p in zip(src, self.problems):
+            _check_map_tensor(torch, t, p, "target/seed")
+        if maps is not None:
+            for t, p in zip(maps, self.problems):
+                if t is not None:
+                    _check_map_tensor(torch, t, p, "maps")
+        if grads is None:
+            grads = torch.empty((self._n, self._n_theta), dtype=torch.float64, device="cuda")
+        if chi2 is None and targets is not None:
+            chi2 = torch.empty(self._n, dtype=torch.float64, device="cuda")
+        th_ptr = None
+        if thetas is not None:
+            th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(self._n, self._n_theta))
+            self._thetas = th
+            for i in range(self._n):
+                self.problems[i] = self.problems[i].with_theta(th[i])
+            th_ptr = th.ctypes.data_as(ctypes.c_void_p)
+        seed_arr = (ctypes.c_void_p * self._n)(*[t.data_ptr() for t in src])
+        map_arr = None
+        if maps is not None:
+            map_arr = (ctypes.c_void_p * self._n)(*[(t.data_ptr() if t is not None else None) for t in maps])
+        check(lib().synax_batch_run(self._h, th_ptr, seed_arr, 0 if targets is not None else 1,
+                                    ctypes.c_double(float(sigma)), map_arr,
+                                    ctypes.c_void_p(grads.data_ptr()),
+                                    ctypes.c_void_p(chi2.data_ptr() if chi2 is not None else 0),
+                                    _stream_handle(torch, stream)), "synax_batch_run")
+        return grads, chi2
+
+    def latencies(self):
+        import numpy as np
+        out = np.zeros(self._n, dtype=np.float64)
+        check(lib().synax_batch_latencies(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+              "synax_batch_latencies")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().synax_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_lanes_per_ray(lanes: int, n_steps_min: int = -1) -> None:
+    """Launch tuning: 8, 16 or 32 lanes per ray (0 = built-in rule), for every
+    map (n_steps_min < 0) or for the step-count bin containing n_steps_min."""
+    check(lib().synax_set_lanes_per_ray(int(n_steps_min), int(lanes)), "synax_set_lanes_per_ray")
 
 
 class SynaxMaps:

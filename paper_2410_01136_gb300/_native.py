@@ -71,6 +71,15 @@ SIGNATURES = {
                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                          ctypes.c_void_p]),
     "synax_set_lanes_per_ray": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "synax_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_void_p)]),
+    "synax_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "synax_batch_latencies": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "synax_batch_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "synax_batch_plan_destroy": (None, [ctypes.c_void_p]),
     "synax_last_cuda_error": (ctypes.c_int, []),
     "synax_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "synax_version": (ctypes.c_int, []),

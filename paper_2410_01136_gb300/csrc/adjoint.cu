@@ -25,284 +25,18 @@
 // order, so the gradient is bitwise reproducible.
 #include <cuda_runtime.h>
 
-#include "march.cuh"
+#include "adjoint.cuh"
 
 namespace synax {
 
-constexpr int kAdjThreads = 256;
-
-template <int MODEL> struct Grad;
-
-// JF12-type: theta = [b_1..b_8, B_h, z_h, B_X, theta_X, N0_obs, p, h1, h2].
-template <> struct Grad<SYNAX_MODEL_JF12> {
-    static constexpr int NT = 16;
-    static constexpr int P_INDEX = 13;
-    template <typename R>
-    static __device__ __forceinline__ void accum(const R* m, const FieldLocal<R>& L, R bxb, R byb, R bzb,
-                                                 R n0b, R neb, R* g) {
-        const R brb = bxb * L.c + byb * L.s;    // adjoint of the cylindrical components
-        const R bpb = -bxb * L.s + byb * L.c;
-        const R beta_b = L.disc_unit * (brb * R(kPitchSin) + bpb * R(kPitchCos));
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-            g[kk] += beta_b * ((kk == L.ka ? L.wa : R(0)) + (kk == L.kb ? L.wb : R(0)));
-        g[8] += bpb * L.halo_unit;
-        g[9] += bpb * m[mc::J_BH] * L.halo_unit * L.az * m[mc::J_IZH] * m[mc::J_IZH];
-        if (L.rp > R(0)) {
-            const R proj = brb * L.sz * m[mc::J_COSX] + bzb * m[mc::J_SINX];
-            g[10] += L.xmag_unit * proj;
-            const R dmag_drp = m[mc::J_BX] * L.xe * L.ri * (R(1) - L.rp * R(1.0 / 4.8));
-            const R drp_dth = L.az * m[mc::J_SIN2X];
-            g[11] += dmag_drp * drp_dth * proj +
-                     m[mc::J_BX] * L.xmag_unit * (-brb * L.sz * m[mc::J_SINX] + bzb * m[mc::J_COSX]);
-        }
-        g[12] += n0b * L.n0_unit;
-        g[14] += neb * L.ne1 * L.az * m[mc::J_IH1] * m[mc::J_IH1];
-        g[15] += neb * L.ne2 * L.az * m[mc::J_IH2] * m[mc::J_IH2];
-    }
-};
-
-// WMAP-type: theta = [b0, psi0, psi1, chi0B, Bux, N0_obs, p, ne0].
-template <> struct Grad<SYNAX_MODEL_WMAP> {
-    static constexpr int NT = 8;
-    static constexpr int P_INDEX = 6;
-    template <typename R>
-    static __device__ __forceinline__ void accum(const R* m, const FieldLocal<R>& L, R bxb, R byb, R bzb,
-                                                 R n0b, R neb, R* g) {
-        const R brb = bxb * L.c + byb * L.s;
-        const R bpb = -bxb * L.s + byb * L.c;
-        g[0] += L.env * (brb * L.cpsi * L.cchi + bpb * L.spsi * L.cchi + bzb * L.schi);
-        if (L.in_range > R(0)) {
-            const R amp = m[mc::W_B0] * L.env;
-            const R dpsi = amp * L.cchi * (-brb * L.spsi + bpb * L.cpsi);
-            g[1] += dpsi;
-            g[2] += dpsi * L.lnr8;
-            g[3] += amp * L.thz * (-brb * L.cpsi * L.schi - bpb * L.spsi * L.schi + bzb * L.cchi);
-        }
-        g[4] += bxb;
-        g[5] += n0b * L.n0_unit;
-        g[7] += neb * L.ne_unit;
-    }
-};
-
-template <int MODEL, int NF, int LPR, typename R>
-__global__ void __launch_bounds__(kAdjThreads)
-k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmaps,
-          const R* __restrict__ target, R* __restrict__ maps_out, double* __restrict__ partial) {
-    using Ph = PhaseOps<R>;
-    using PT = typename Ph::T;
-    using F = M<R>;
-    constexpr int NT = Grad<MODEL>::NT;
-    constexpr int RAYS = kAdjThreads / LPR;
-    constexpr int WARPS = kAdjThreads / 32;
-    __shared__ R s_arms[8];
-    __shared__ R s_stage[3 * NF][RAYS];
-    __shared__ double s_part[WARPS][NT + 1];
-
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int sub = lane & (LPR - 1);
-    const int slot = threadIdx.x / LPR;
-    if (threadIdx.x < 8) s_arms[threadIdx.x] = P.m[threadIdx.x];
-    __syncthreads();
-
-    R g[NT];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) g[j] = R(0);
-    R chi2_ray = R(0);
-
-    const long long ray0 = (long long)blockIdx.x * RAYS;
-    const long long ray = ray0 + slot;
-    const long long warp_first = ray0 + (long long)warp * (32 / LPR);
-    if (warp_first < P.n_pix) {
-        // idle segments (past the end of the map) march a valid ray with zero seeds
-        const bool live = ray < P.n_pix;
-        const long long r_eff = live ? ray : P.n_pix - 1;
-        Los<R> L;
-        ff nd[3];
-        R dr, dr_lo;
-        ray_setup<R>(P, r_eff, L, nd, dr, dr_lo);
-        PT cd[NF];
-#pragma unroll
-        for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale(P.crev[k], dr) : P.cdr[k];
-        const int N = P.n_steps;
-        const int n0 = (int)(((long long)sub * N) / LPR);
-        const int n1 = (int)(((long long)(sub + 1) * N) / LPR);
-
-        // ---- pass 1: forward march of the lane, RM offset, rotation ----
-        R accI;
-        R zr[NF], zi[NF];
-        PT S;
-        march_lane<MODEL, NF, R>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
-        const PT O = seg_exclusive_scan<LPR, R>(S, sub);
-#pragma unroll
-        for (int k = 0; k < NF; ++k) {
-            if (k < P.n_freq) {
-                R sn, cs;
-                F::sincos_rev(Ph::frac_mul(cd[k], O), &sn, &cs);
-                const R a = zr[k] * cs - zi[k] * sn;
-                const R b = zr[k] * sn + zi[k] * cs;
-                zr[k] = a;
-                zi[k] = b;
-            }
-        }
-
-        // ---- maps of this ray, seeds, per-ray adjoint constants ----
-        const R accI_t = seg_sum<LPR, R>(accI);
-        R hr[NF], hi[NF], c2[NF];
-        R GI = R(0), GIp = R(0), D = R(0);
-#pragma unroll
-        for (int k = 0; k < NF; ++k) {
-            hr[k] = R(0);
-            hi[k] = R(0);
-            c2[k] = R(0);
-            if (k < P.n_freq) {
-                const R zr_t = seg_sum<LPR, R>(zr[k]);
-                const R zi_t = seg_sum<LPR, R>(zi[k]);
-                const R MI = P.aI[k] * dr * accI_t;
-                const R MQ = P.aP[k] * dr * zr_t;
-                const R MU = P.aP[k] * dr * zi_t;
-                if (sub == 0 && live) {
-                    s_stage[3 * k + 0][slot] = MI;
-                    s_stage[3 * k + 1][slot] = MQ;
-                    s_stage[3 * k + 2][slot] = MU;
-                }
-                const long long row = (long long)(3 * k) * P.n_pix + r_eff;
-                R gI, gQ, gU;
-                if (!live) {
-                    gI = gQ = gU = R(0);
-                } else if (A.mode_chi2) {
-                    const R dI = MI - target[row];
-                    const R dQ = MQ - target[row + P.n_pix];
-                    const R dU = MU - target[row + 2 * P.n_pix];
-                    gI = R(2) * A.inv_sigma2 * dI;
-                    gQ = R(2) * A.inv_sigma2 * dQ;
-                    gU = R(2) * A.inv_sigma2 * dU;
-                    chi2_ray += (dI * dI + dQ * dQ + dU * dU) * A.inv_sigma2;
-                } else {
-                    gI = gmaps[row];
-                    gQ = gmaps[row + P.n_pix];
-                    gU = gmaps[row + 2 * P.n_pix];
-                }
-                GI += gI * P.aI[k] * dr;
-                GIp += gI * P.aI[k] * dr * A.dlnaI_dp[k];
-                hr[k] = gQ * P.aP[k] * dr;               // h = conj(gQ + i gU) aP dr
-                hi[k] = -gU * P.aP[k] * dr;
-                c2[k] = R(6.283185307179586) * R(Ph::to_real(cd[k]));
-                D -= c2[k] * (hr[k] * zi[k] + hi[k] * zr[k]);   // -Im(h' Z_lane)
-            }
-        }
-        R after = seg_exclusive_suffix<LPR, R>(D, sub);
-
-        // ---- pass 2: reverse march of the lane's chunk ----
-        if (n0 < n1) {
-            PT Rloc = S;
-            ArmTracker<R> trk;
-            if constexpr (MODEL == SYNAX_MODEL_JF12) trk.init(P, nd, n1 - 1, dr, dr_lo);
-            const R q = P.q;
-            for (int n = n1 - 1; n >= n0; --n) {
-                if constexpr (MODEL == SYNAX_MODEL_JF12) {
-                    if (n < n1 - 1) trk.step(-1);
-                }
-                const R nh = R(n) + R(0.5);
-                const R t = fma(nh, dr, nh * dr_lo);
-                const R x = P.obs[0] + t * L.n[0];
-                const R y = P.obs[1] + t * L.n[1];
-                const R z = P.obs[2] + t * L.n[2];
-                R B[3], N0, ne;
-                ArmCoord<R> ac{0, R(0)};
-                if constexpr (MODEL == SYNAX_MODEL_JF12) ac = trk.coord(x, y, F::sqrt(x * x + y * y));
-                FieldLocal<R> loc;
-                Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
-
-                const R bn = B[0] * L.n[0] + B[1] * L.n[1] + B[2] * L.n[2];
-                const R ba = B[0] * L.el[0] + B[1] * L.el[1];
-                const R bb = B[0] * L.eb[0] + B[1] * L.eb[1] + B[2] * L.eb[2];
-                const R bp2 = ba * ba + bb * bb;
-                const bool lit = bp2 > R(1e-30);
-                const R lg = lit ? F::log2_fast(bp2) : R(0);
-                const R w = lit ? F::exp2_fast(q * lg) : R(0);
-                const R nw = N0 * w;
-                const R jI = nw * bp2;
-                const R pc = nw * (ba * ba - bb * bb);
-                const R ps = nw * (R(2) * ba * bb);
-                const R f = -ne * bn;
-
-                Rloc = Ph::add(Rloc, -f);                    // sum of f before sample n
-                const PT s_n = Ph::add(Ph::add(O, Rloc), P.w_own * f);
-                R Or = R(0), Oi = R(0), Opr = R(0), Opi = R(0), Odr = R(0), Odi = R(0);
-#pragma unroll
-                for (int k = 0; k < NF; ++k) {
-                    if (k < P.n_freq) {
-                        R sn, cs;
-                        F::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
-                        const R ur = hr[k] * cs - hi[k] * sn;   // h_f e^{i phi_f}
-                        const R ui = hr[k] * sn + hi[k] * cs;
-                        Or += ur;
-                        Oi += ui;
-                        Opr += A.dlnaP_dp[k] * ur;
-                        Opi += A.dlnaP_dp[k] * ui;
-                        Odr += c2[k] * ur;
-                        Odi += c2[k] * ui;
-                    }
-                }
-                const R d = -(Odr * ps + Odi * pc);            // dL/dS_n = -Im(Omega' E)
-                const R fbar = after + P.w_own * d;
-                after += d;
-
-                R abar = R(0), bbar = R(0), n0bar = R(0), pbar = R(0);
-                if (lit) {
-                    const R t1 = Or * ba - Oi * bb;             // Omega z
-                    const R t2 = Or * bb + Oi * ba;
-                    const R t3 = t1 * ba - t2 * bb;             // Re(Omega z^2)
-                    const R u1 = Opr * ba - Opi * bb;
-                    const R u2 = Opr * bb + Opi * ba;
-                    const R u3 = u1 * ba - u2 * bb;             // Re(Omega_p z^2)
-                    const R ibp2 = R(1) / bp2;
-                    const R half_p1 = R(2) * q + R(2);          // (p + 1)/2
-                    abar = nw * (GI * half_p1 * ba + R(2) * t1 + R(2) * q * ba * t3 * ibp2);
-                    bbar = nw * (GI * half_p1 * bb - R(2) * t2 + R(2) * q * bb * t3 * ibp2);
-                    n0bar = w * (GI * bp2 + t3);
-                    pbar = nw * ((GI * bp2 + t3) * lg * R(0.25 * kLn2) + GIp * bp2 + u3);
-                }
-                (void)jI;
-                const R bnb = -ne * fbar;                        // d f / d(B.n) = -n_e
-                const R neb = -bn * fbar;                        // d f / d n_e = -B.n
-                const R bxb = abar * L.el[0] + bbar * L.eb[0] + bnb * L.n[0];
-                const R byb = abar * L.el[1] + bbar * L.eb[1] + bnb * L.n[1];
-                const R bzb = bbar * L.eb[2] + bnb * L.n[2];
-                g[Grad<MODEL>::P_INDEX] += pbar;
-                Grad<MODEL>::accum(P.m, loc, bxb, byb, bzb, n0bar, neb, g);
-            }
-        }
-        // all lanes hold partial gradients of their ray: one full-warp sum
-        // gives the warp's share of the CTA partial
-#pragma unroll
-        for (int j = 0; j < NT; ++j) g[j] = warp_sum<R>(g[j]);
-        chi2_ray = warp_sum<R>(sub == 0 ? chi2_ray : R(0));
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < NT; ++j) s_part[warp][j] = (double)g[j];
-        s_part[warp][NT] = (double)chi2_ray;
-    }
-    __syncthreads();
-    if (threadIdx.x <= NT) {
-        double acc = 0.0;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) acc += s_part[w][threadIdx.x];
-        partial[(long long)blockIdx.x * (NT + 1) + threadIdx.x] = acc;
-    }
-    if (maps_out) {
-        const int rows = 3 * P.n_freq;
-        for (int idx = threadIdx.x; idx < rows * RAYS; idx += kAdjThreads) {
-            const int row = idx / RAYS;
-            const int col = idx - row * RAYS;
-            const long long r = ray0 + col;
-            if (r < P.n_pix) maps_out[(long long)row * P.n_pix + r] = s_stage[row][col];
-        }
-    }
-}
+#define SYNAX_DECL(name, R)                                                                        \
+    int name(const MapParams<R>& P, const AdjParams<R>& A, const R* gmaps, const R* target, double* grad, \
+             double* chi2, R* maps, double* partial, cudaStream_t st);
+SYNAX_DECL(adjoint_wmap_f32, float)
+SYNAX_DECL(adjoint_jf12_f32, float)
+SYNAX_DECL(adjoint_wmap_f64, double)
+SYNAX_DECL(adjoint_jf12_f64, double)
+#undef SYNAX_DECL
 
 // Fixed-order reduction of per-CTA partials: block j sums column j.
 __global__ void __launch_bounds__(256)
@@ -324,48 +58,9 @@ k_reduce_partials(const double* __restrict__ partial, long long n_blocks, int n_
     }
 }
 
-static long long adj_blocks(long long n_pix, int lpr) {
-    const int rays = kAdjThreads / lpr;
-    return (n_pix + rays - 1) / rays;
-}
-
 // Sized for the largest grid (32 lanes per ray), whatever the tuning picks.
 size_t adjoint_workspace_bytes(long long n_pix, int n_theta) {
     return (size_t)adj_blocks(n_pix, 32) * (size_t)(n_theta + 1) * sizeof(double);
-}
-
-template <int MODEL, int NF, int LPR, typename R>
-static int launch_adj_lpr(const MapParams<R>& P, const AdjParams<R>& A, const R* gmaps, const R* target,
-                          double* grad, double* chi2, R* maps, double* partial, cudaStream_t st) {
-    constexpr int NT = Grad<MODEL>::NT;
-    const long long blocks = adj_blocks(P.n_pix, LPR);
-    k_adjoint<MODEL, NF, LPR, R><<<(unsigned)blocks, kAdjThreads, 0, st>>>(P, A, gmaps, target, maps, partial);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return record_cuda_error((int)err);
-    k_reduce_partials<<<NT + 1, 256, 0, st>>>(partial, blocks, NT + 1, NT, grad, chi2);
-    err = cudaGetLastError();
-    return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
-}
-
-template <int MODEL, int NF, typename R>
-static int launch_adj_nf(const MapParams<R>& P, const AdjParams<R>& A, const R* gmaps, const R* target,
-                         double* grad, double* chi2, R* maps, double* partial, cudaStream_t st) {
-    const int lpr = lanes_per_ray(P.n_steps, P.n_pix);
-    if (lpr == 8) return launch_adj_lpr<MODEL, NF, 8, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-    if (lpr == 16) return launch_adj_lpr<MODEL, NF, 16, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-    return launch_adj_lpr<MODEL, NF, 32, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-}
-
-template <int MODEL, typename R>
-static int launch_adj_model(const MapParams<R>& P, const AdjParams<R>& A, const R* gmaps, const R* target,
-                            double* grad, double* chi2, R* maps, double* partial, cudaStream_t st) {
-    const int F = P.n_freq;
-    if (F == 1) return launch_adj_nf<MODEL, 1, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-    if (F == 2) return launch_adj_nf<MODEL, 2, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-    if (F == 3) return launch_adj_nf<MODEL, 3, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-    if (F == 4) return launch_adj_nf<MODEL, 4, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-    if (F <= 8) return launch_adj_nf<MODEL, 8, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
-    return launch_adj_nf<MODEL, 16, R>(P, A, gmaps, target, grad, chi2, maps, partial, st);
 }
 
 template <typename R>
@@ -383,10 +78,18 @@ static int launch_adjoint_t(const MapParams<R>& P, const AdjParams<R>& A, const 
     const R* tg = (const R*)target;
     R* mo = (R*)maps;
     double* part = (double*)workspace;
-    switch (P.model) {
-    case SYNAX_MODEL_WMAP: return launch_adj_model<SYNAX_MODEL_WMAP, R>(P, A, g, tg, grad, chi2, mo, part, st);
-    case SYNAX_MODEL_JF12: return launch_adj_model<SYNAX_MODEL_JF12, R>(P, A, g, tg, grad, chi2, mo, part, st);
-    default: return SYNAX_ENOTSUP;
+    if constexpr (sizeof(R) == 4) {
+        switch (P.model) {
+        case SYNAX_MODEL_WMAP: return adjoint_wmap_f32(P, A, g, tg, grad, chi2, mo, part, st);
+        case SYNAX_MODEL_JF12: return adjoint_jf12_f32(P, A, g, tg, grad, chi2, mo, part, st);
+        default: return SYNAX_ENOTSUP;
+        }
+    } else {
+        switch (P.model) {
+        case SYNAX_MODEL_WMAP: return adjoint_wmap_f64(P, A, g, tg, grad, chi2, mo, part, st);
+        case SYNAX_MODEL_JF12: return adjoint_jf12_f64(P, A, g, tg, grad, chi2, mo, part, st);
+        default: return SYNAX_ENOTSUP;
+        }
     }
 }
 

@@ -1,0 +1,282 @@
+// batch.cu -- host side of the persistent batch (synax_batch_* in synax.h).
+//
+// A plan fixes the ensemble's shape (sets, their Nside and step counts), the
+// tile order and every device buffer; it is the only place where this entry
+// family allocates.  Each run rewrites the per-set descriptors (parameters,
+// seed/target and output pointers) in a pinned host buffer and launches one
+// CUDA graph, captured on the first run: descriptor upload -> counter reset
+// -> persistent kernel -> per-set reduction.  Later runs replay the graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "batch.cuh"
+
+namespace synax {
+int batch_kernels_jf12(int nf, int lpr, BatchKernels* out);
+int batch_kernels_wmap(int nf, int lpr, BatchKernels* out);
+}  // namespace synax
+
+using namespace synax;
+
+struct synax_batch_plan {
+    int device = -1;
+    int n_sets = 0;
+    int model = 0;
+    int nf = 0;        // frequency-count variant of the kernels
+    int lpr = 32;
+    int rays = 8;
+    int grid = 0;
+    int n_theta = 0;
+    long long n_tiles = 0;
+    BatchKernels kern{};
+    std::vector<synax_problem> probs;
+    std::vector<long long> npix;
+    std::vector<int> order;          // processing position -> set
+    std::vector<long long> begin;    // processing position -> first tile
+    std::vector<long long> pos_of;   // set -> processing position
+    BatchSet* d_sets = nullptr;
+    long long* d_begin = nullptr;
+    int* d_order = nullptr;
+    unsigned long long* d_counter = nullptr;
+    unsigned long long* d_done = nullptr;
+    unsigned long long* d_done_ns = nullptr;
+    unsigned long long* d_t0 = nullptr;
+    double* d_partial = nullptr;
+    BatchSet* h_sets = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+namespace {
+
+void plan_free(synax_batch_plan* p) {
+    if (!p) return;
+    if (p->pending && p->done) cudaEventSynchronize(p->done);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    cudaFree(p->d_sets);
+    cudaFree(p->d_begin);
+    cudaFree(p->d_order);
+    cudaFree(p->d_counter);
+    cudaFree(p->d_done);
+    cudaFree(p->d_done_ns);
+    cudaFree(p->d_t0);
+    cudaFree(p->d_partial);
+    if (p->h_sets) cudaFreeHost(p->h_sets);
+    delete p;
+}
+
+int nf_variant(int n_freq) {
+    if (n_freq <= 2) return n_freq;
+    if (n_freq <= 4) return 4;
+    if (n_freq <= 8) return 8;
+    return 16;
+}
+
+int capture_graph(synax_batch_plan* p) {
+    cudaError_t err = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    const size_t desc_bytes = sizeof(BatchSet) * (size_t)p->n_sets;
+    cudaMemcpyAsync(p->d_sets, p->h_sets, desc_bytes, cudaMemcpyHostToDevice, p->cap);
+    cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), p->cap);
+    cudaMemsetAsync(p->d_done, 0, sizeof(unsigned long long) * (size_t)p->n_sets, p->cap);
+    int n_sets = p->n_sets;
+    long long n_tiles = p->n_tiles;
+    void* args[] = {&p->d_sets, &p->d_begin, &p->d_order, &n_sets, &n_tiles, &p->d_counter,
+                    &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0};
+    cudaLaunchKernel(p->kern.batch, dim3(p->grid), dim3(kAdjThreads), args, 0, p->cap);
+    void* rargs[] = {&p->d_sets, &p->d_partial};
+    cudaLaunchKernel(p->kern.reduce, dim3(p->n_sets), dim3(256), rargs, 0, p->cap);
+    err = cudaStreamEndCapture(p->cap, &p->graph);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    err = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    return SYNAX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_plan** out) {
+    if (!out) return SYNAX_EINVAL;
+    *out = nullptr;
+    if (!sets || n_sets < 1) return SYNAX_EINVAL;
+    std::vector<long long> npix(n_sets);
+    for (int s = 0; s < n_sets; ++s) {
+        const int rc = validate_problem(&sets[s], &npix[s]);
+        if (rc != SYNAX_OK) return rc;
+        if (sets[s].flags & SYNAX_F64) return SYNAX_ENOTSUP;       // the batch marches in FP32
+        if (sets[s].model_id != sets[0].model_id || sets[s].n_freq != sets[0].n_freq) return SYNAX_EINVAL;
+        if (npix[s] == 0) return SYNAX_EINVAL;
+    }
+    const int model = sets[0].model_id;
+    if (model != SYNAX_MODEL_JF12 && model != SYNAX_MODEL_WMAP) return SYNAX_ENOTSUP;
+
+    synax_batch_plan* p = new (std::nothrow) synax_batch_plan();
+    if (!p) return SYNAX_ENOMEM;
+    cudaError_t err = cudaGetDevice(&p->device);
+    if (err != cudaSuccess) { plan_free(p); return record_cuda_error((int)err); }
+    p->n_sets = n_sets;
+    p->model = model;
+    p->nf = nf_variant(sets[0].n_freq);
+    p->probs.assign(sets, sets + n_sets);
+    p->npix = npix;
+
+    // lanes per ray from the tuning table at the ensemble's sample-weighted step count
+    long long tot_rays = 0;
+    double wsteps = 0.0, wsum = 0.0;
+    for (int s = 0; s < n_sets; ++s) {
+        tot_rays += npix[s];
+        wsteps += (double)npix[s] * sets[s].n_steps * sets[s].n_steps;
+        wsum += (double)npix[s] * sets[s].n_steps;
+    }
+    p->lpr = lanes_per_ray((int)std::lround(wsteps / wsum), tot_rays);
+    if (model == SYNAX_MODEL_WMAP) p->lpr = 32;
+    p->rays = kAdjThreads / p->lpr;
+    int rc = model == SYNAX_MODEL_JF12 ? batch_kernels_jf12(p->nf, p->lpr, &p->kern)
+                                       : batch_kernels_wmap(p->nf, p->lpr, &p->kern);
+    if (rc != SYNAX_OK) { plan_free(p); return rc; }
+    p->n_theta = p->kern.n_theta;
+
+    // tile order: most steps per ray first (longest-processing-time order)
+    p->order.resize(n_sets);
+    std::iota(p->order.begin(), p->order.end(), 0);
+    std::stable_sort(p->order.begin(), p->order.end(), [&](int a, int b) {
+        if (sets[a].n_steps != sets[b].n_steps) return sets[a].n_steps > sets[b].n_steps;
+        return npix[a] > npix[b];
+    });
+    p->begin.resize(n_sets + 1);
+    p->pos_of.resize(n_sets);
+    long long t = 0;
+    for (int k = 0; k < n_sets; ++k) {
+        p->begin[k] = t;
+        p->pos_of[p->order[k]] = k;
+        t += (npix[p->order[k]] + p->rays - 1) / p->rays;
+    }
+    p->begin[n_sets] = t;
+    p->n_tiles = t;
+
+    int per_sm = 0, sms = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern.batch, kAdjThreads, 0);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (err != cudaSuccess || per_sm < 1) { plan_free(p); return record_cuda_error((int)(err ? err : cudaErrorInvalidValue)); }
+    p->grid = (int)std::min<long long>((long long)per_sm * sms, p->n_tiles);
+
+    const size_t part_bytes = sizeof(double) * (size_t)p->n_tiles * (size_t)(p->n_theta + 1);
+    bool ok = cudaMalloc(&p->d_sets, sizeof(BatchSet) * n_sets) == cudaSuccess &&
+              cudaMalloc(&p->d_begin, sizeof(long long) * (n_sets + 1)) == cudaSuccess &&
+              cudaMalloc(&p->d_order, sizeof(int) * n_sets) == cudaSuccess &&
+              cudaMalloc(&p->d_counter, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&p->d_done, sizeof(unsigned long long) * n_sets) == cudaSuccess &&
+              cudaMalloc(&p->d_done_ns, sizeof(unsigned long long) * n_sets) == cudaSuccess &&
+              cudaMalloc(&p->d_t0, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&p->d_partial, part_bytes) == cudaSuccess &&
+              cudaMallocHost(&p->h_sets, sizeof(BatchSet) * n_sets) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); plan_free(p); return SYNAX_ENOMEM; }
+    std::memset(p->h_sets, 0, sizeof(BatchSet) * n_sets);
+    ok = cudaMemcpy(p->d_begin, p->begin.data(), sizeof(long long) * (n_sets + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->d_order, p->order.data(), sizeof(int) * n_sets, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(p->d_done_ns, 0, sizeof(unsigned long long) * n_sets) == cudaSuccess &&
+         cudaMemset(p->d_t0, 0, sizeof(unsigned long long)) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { const int e = (int)cudaGetLastError(); plan_free(p); return record_cuda_error(e); }
+    *out = p;
+    return SYNAX_OK;
+}
+
+int synax_batch_run(synax_batch_plan* p, const double* thetas, const void* const* seeds_dev, int vjp,
+                    double sigma_K, void* const* maps_dev, double* grads_dev, double* chi2_dev, void* stream) {
+    if (!p || !seeds_dev || !grads_dev) return SYNAX_EINVAL;
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    if (dev != p->device) return SYNAX_EINVAL;
+    if (!vjp) {
+        if (!std::isfinite(sigma_K)) return SYNAX_ENONFINITE;
+        if (!(sigma_K > 0.0)) return SYNAX_EINVAL;
+    }
+    // validate every new parameter vector before touching the plan
+    std::vector<synax_problem> next = p->probs;
+    for (int s = 0; s < p->n_sets; ++s) {
+        if (!seeds_dev[s]) return SYNAX_EINVAL;
+        if (thetas)
+            for (int j = 0; j < next[s].n_theta; ++j) next[s].theta[j] = thetas[(size_t)s * next[s].n_theta + j];
+        long long n = 0;
+        const int rc = validate_problem(&next[s], &n);
+        if (rc != SYNAX_OK) return rc;
+    }
+    // the previous run's graph reads h_sets: let it finish before rewriting
+    if (p->pending) {
+        err = cudaEventSynchronize(p->done);
+        if (err != cudaSuccess) return record_cuda_error((int)err);
+        p->pending = false;
+    }
+    p->probs = next;
+    for (int s = 0; s < p->n_sets; ++s) {
+        BatchSet& d = p->h_sets[s];
+        fill_params<float>(p->probs[s], p->npix[s], d.P);
+        fill_adj<float>(p->probs[s], d.A);
+        d.A.mode_chi2 = vjp ? 0 : 1;
+        d.A.inv_sigma2 = vjp ? 0.0f : (float)(1.0 / (sigma_K * sigma_K));
+        d.seed = (const float*)seeds_dev[s];
+        d.maps = maps_dev ? (float*)maps_dev[s] : nullptr;
+        d.grad = grads_dev + (size_t)s * p->n_theta;
+        d.chi2 = chi2_dev ? chi2_dev + s : nullptr;
+        const long long k = p->pos_of[s];
+        d.tile_begin = p->begin[k];
+        d.n_tiles = p->begin[k + 1] - p->begin[k];
+    }
+    if (!p->exec) {
+        const int rc = capture_graph(p);
+        if (rc != SYNAX_OK) return rc;
+    }
+    err = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    err = cudaEventRecord(p->done, (cudaStream_t)stream);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    p->pending = true;
+    return SYNAX_OK;
+}
+
+int synax_batch_latencies(synax_batch_plan* p, double* ms_out) {
+    if (!p || !ms_out) return SYNAX_EINVAL;
+    if (p->pending) {
+        const cudaError_t err = cudaEventSynchronize(p->done);
+        if (err != cudaSuccess) return record_cuda_error((int)err);
+        p->pending = false;
+    }
+    std::vector<unsigned long long> done(p->n_sets);
+    unsigned long long t0 = 0;
+    cudaError_t err = cudaMemcpy(done.data(), p->d_done_ns, sizeof(unsigned long long) * p->n_sets,
+                                 cudaMemcpyDeviceToHost);
+    if (err == cudaSuccess) err = cudaMemcpy(&t0, p->d_t0, sizeof(t0), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    for (int s = 0; s < p->n_sets; ++s)
+        ms_out[s] = done[s] >= t0 ? (double)(done[s] - t0) * 1e-6 : 0.0;
+    return SYNAX_OK;
+}
+
+int synax_batch_plan_info(const synax_batch_plan* p, long long* n_tiles, int* lanes_per_ray, int* grid) {
+    if (!p) return SYNAX_EINVAL;
+    if (n_tiles) *n_tiles = p->n_tiles;
+    if (lanes_per_ray) *lanes_per_ray = p->lpr;
+    if (grid) *grid = p->grid;
+    return SYNAX_OK;
+}
+
+void synax_batch_plan_destroy(synax_batch_plan* p) { plan_free(p); }
+
+}  // extern "C"

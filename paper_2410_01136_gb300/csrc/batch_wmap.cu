@@ -1,0 +1,8 @@
+// Instantiation of the persistent batch kernels for the WMAP-type model.
+#include "batch.cuh"
+
+namespace synax {
+int batch_kernels_wmap(int nf, int lpr, BatchKernels* out) {
+    return batch_kernels_for<SYNAX_MODEL_WMAP>(nf, lpr, out);
+}
+}  // namespace synax

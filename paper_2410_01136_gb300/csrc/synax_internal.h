@@ -76,6 +76,11 @@ struct AdjParams {
     R inv_sigma2;
 };
 
+// Host-side problem handling (abi.cu).
+int validate_problem(const synax_problem* P, long long* n_pix);
+template <typename R> void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M);
+template <typename R> void fill_adj(const synax_problem& P, AdjParams<R>& A);
+
 // Lanes per ray (32, 16 or 8) for a map of n_pix rays of n_steps samples:
 // the launch tuning table (tune.cu), overridable per process.
 int lanes_per_ray(int n_steps, long long n_pix);

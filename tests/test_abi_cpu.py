@@ -44,7 +44,7 @@ def test_exports_every_declared_symbol(L):
         assert re.search(rf"\bT {n}\b", out), n
     # and the binding declares a signature for every one of them
     for n in names:
-        assert n in _native.SIGNATURES or n.startswith("synax_batch") or n.startswith("synax_surrogate"), n
+        assert n in _native.SIGNATURES, n
 
 
 def test_struct_layout_matches_header(tmp_path):
@@ -165,3 +165,31 @@ def test_build_function_not_shadowed_by_submodule():
     pkg.build()
     from paper_2410_01136_gb300 import build
     assert callable(build)
+
+
+def test_batch_plan_validation_on_host(L):
+    """Plan validation happens before any CUDA call."""
+    a = _native.problem_struct(good())
+    arr = (_native.SynaxProblem * 2)(a, a)
+    h = ctypes.c_void_p()
+    assert L.synax_batch_plan_create(arr, 0, ctypes.byref(h)) == _native.SYNAX_EINVAL
+    assert L.synax_batch_plan_create(None, 2, ctypes.byref(h)) == _native.SYNAX_EINVAL
+    b = _native.problem_struct(good().replace(freq_hz=(1e9,)))
+    arr2 = (_native.SynaxProblem * 2)(a, b)
+    assert L.synax_batch_plan_create(arr2, 2, ctypes.byref(h)) == _native.SYNAX_EINVAL
+    c = _native.problem_struct(good().replace(f64=True))
+    arr3 = (_native.SynaxProblem * 1)(c)
+    assert L.synax_batch_plan_create(arr3, 1, ctypes.byref(h)) == _native.SYNAX_ENOTSUP
+    bad = _native.problem_struct(good())
+    bad.nside = 3
+    arr4 = (_native.SynaxProblem * 1)(bad)
+    assert L.synax_batch_plan_create(arr4, 1, ctypes.byref(h)) == _native.SYNAX_EINVAL
+    assert L.synax_batch_run(None, None, None, 0, 1.0, None, None, None, None) == _native.SYNAX_EINVAL
+
+
+def test_set_lanes_per_ray_validation(L):
+    assert L.synax_set_lanes_per_ray(-1, 12) == _native.SYNAX_EINVAL
+    assert L.synax_set_lanes_per_ray(512, 7) == _native.SYNAX_EINVAL
+    for lanes in (8, 16, 32, 0):
+        assert L.synax_set_lanes_per_ray(512, lanes) == _native.SYNAX_OK
+    assert L.synax_set_lanes_per_ray(-1, 0) == _native.SYNAX_OK

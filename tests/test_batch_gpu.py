@@ -1,0 +1,123 @@
+"""The persistent, graph-captured batch (synax_batch_*) against one-map
+synax_adjoint calls on the same sets, and chi^2 against the FP64 oracle.
+
+The batch runs the same per-CTA adjoint code, inlined into another kernel and
+with one lanes-per-ray width for the whole ensemble, so per-ray FP32 rounding
+may differ from the one-map call: gradients are compared at FP32 precision
+(1e-5 relative, 1e-6 of the largest component), bitwise only between replays."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_01136_gb300 import BatchPlan, adjoint, forward, inputs
+
+from .parity import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    assert _t.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2410_01136_gb300 import build
+    build()
+    oracle.build()
+    return _t
+
+
+def small_sets(n=10, seed=4):
+    sets = inputs.config4(n_sets=n, seed=seed)
+    nsides = (2, 4, 8)
+    steps = (32, 64, 100, 128)
+    return [s.replace(nside=nsides[i % 3], n_steps=steps[i % 4]) for i, s in enumerate(sets)]
+
+
+def targets_for(torch, sets, seed=3):
+    out = []
+    for i, p in enumerate(sets):
+        th = inputs.perturbed_theta(p.theta, seed=seed + i)
+        t = oracle.forward(p.with_theta(th)) + inputs.target_noise((p.n_freq, 3, p.npix), seed=seed + i)
+        out.append(torch.tensor(t, dtype=torch.float32, device="cuda"))
+    return out
+
+
+def test_batch_matches_single_adjoint(torch):
+    sets = small_sets()
+    tg = targets_for(torch, sets)
+    plan = BatchPlan(sets)
+    maps = [torch.empty_like(t) for t in tg]
+    grads, chi2 = plan.run(targets=tg, sigma=0.5, maps=maps)
+    torch.cuda.synchronize()
+    g = grads.cpu().numpy()
+    c = chi2.cpu().numpy()
+    for i, p in enumerate(sets):
+        gi, ci = adjoint(p, target=tg[i], sigma=0.5)
+        gi = gi.cpu().numpy()
+        assert np.allclose(g[i], gi, rtol=1e-5, atol=1e-6 * np.abs(gi).max()), i
+        assert c[i] == pytest.approx(float(ci.item()), rel=1e-6)
+        assert_parity(maps[i].cpu().numpy(), forward(p).cpu().numpy(), 1e-6, 1e-6, f"set {i} maps")
+        # chi^2 against the oracle's maps
+        ora = oracle.chi2(oracle.forward(p), tg[i].cpu().numpy(), 0.5)
+        assert c[i] == pytest.approx(ora, rel=1e-5)
+    lat = plan.latencies()
+    assert np.all(np.isfinite(lat)) and np.all(lat >= 0)
+    info = plan.info()
+    assert info["n_tiles"] > 0 and info["grid"] > 0
+    plan.close()
+
+
+def test_graph_replay_new_thetas_and_vjp(torch):
+    sets = small_sets(6, seed=9)
+    tg = targets_for(torch, sets, seed=20)
+    plan = BatchPlan(sets)
+    g0, _ = plan.run(targets=tg, sigma=0.5)
+    g0 = g0.cpu().numpy()
+    g0b, _ = plan.run(targets=tg, sigma=0.5)            # replay, same inputs: bitwise equal
+    assert np.array_equal(g0, g0b.cpu().numpy())
+    new = np.stack([inputs.perturbed_theta(p.theta, seed=50 + i, frac=0.02) for i, p in enumerate(sets)])
+    new[:, 13] = np.clip(new[:, 13], 2.8, 3.2)
+    g1, c1 = plan.run(targets=tg, sigma=0.5, thetas=new)
+    g1 = g1.cpu().numpy()
+    for i, p in enumerate(sets):
+        gi, ci = adjoint(p.with_theta(new[i]), target=tg[i], sigma=0.5)
+        assert np.allclose(g1[i], gi.cpu().numpy(), rtol=1e-5, atol=1e-6 * np.abs(g1[i]).max())
+    # VJP mode through the same plan (new graph launch, same descriptors layout)
+    seeds = [torch.tensor(inputs.normal(70 + i, p.n_freq * 3 * p.npix).reshape(p.n_freq, 3, p.npix),
+                          dtype=torch.float32, device="cuda") for i, p in enumerate(sets)]
+    gv, cv = plan.run(seeds=seeds)
+    assert cv is None
+    gv = gv.cpu().numpy()
+    for i, p in enumerate(sets):
+        ref = adjoint(p.with_theta(new[i]), gmaps=seeds[i]).cpu().numpy()
+        assert np.allclose(gv[i], ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+    plan.close()
+
+
+@pytest.mark.slow
+def test_ensemble_workload_subset(torch):
+    """16 sets of the 256-set ensemble draw (Nside 16-128, 128-1024 steps)."""
+    sets = inputs.config4()[:16]
+    tg = [forward(p.with_theta(inputs.perturbed_theta(p.theta, seed=5 + i))).contiguous()
+          for i, p in enumerate(sets)]
+    plan = BatchPlan(sets)
+    grads, chi2 = plan.run(targets=tg, sigma=0.5)
+    g = grads.cpu().numpy()
+    for i, p in enumerate(sets):
+        gi, _ = adjoint(p, target=tg[i], sigma=0.5)
+        gi = gi.cpu().numpy()
+        assert np.allclose(g[i], gi, rtol=1e-5, atol=1e-6 * np.abs(gi).max()), i
+    lat = plan.latencies()
+    assert np.all(lat > 0)
+    plan.close()
+
+
+def test_plan_validation(torch):
+    from paper_2410_01136_gb300 import SynaxError
+    a = inputs.config2().replace(nside=2, n_steps=16)
+    with pytest.raises(SynaxError):
+        BatchPlan([a, a.replace(freq_hz=(1e9,))])             # mixed frequency counts
+    with pytest.raises(SynaxError):
+        BatchPlan([a.replace(f64=True)])                       # FP64 batch
+    with pytest.raises(SynaxError):
+        BatchPlan([inputs.toy_problem(nside=2, n_steps=8)])     # no adjoint for the toy
