@@ -159,6 +159,15 @@ int synax_batch_plan_info(const synax_batch_plan* plan, long long* n_tiles, int*
 
 void synax_batch_plan_destroy(synax_batch_plan* plan);
 
+/* BF16 tensor-core GEMM of the surrogate network (tcgen05, FP32 accumulate):
+ * C[M][N] = A[M][K] . B[N][K]^T, A and B row-major BF16 with row pitches
+ * lda, ldb (elements, multiples of 8, >= K), K a multiple of 64, pointers
+ * 16-byte aligned; C row-major FP32 with pitch ldc >= N.  *err_dev (device
+ * int) is set to 1 if a bounded on-chip wait gave up (results then invalid);
+ * the caller zeroes it.  Exposed for tests of the kernel the surrogate runs. */
+int synax_gemm_bf16(const void* a_dev, int lda, const void* b_dev, int ldb, int M, int N, int K, float* c_dev,
+                    int ldc, int* err_dev, void* stream);
+
 /* synax_adjoint without a caller-provided workspace (the paper has no
  * counterpart: this is an interface for callers that cannot allocate device
  * memory, e.g. a host program that links only this library and the CUDA

@@ -80,6 +80,9 @@ SIGNATURES = {
     "synax_batch_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "synax_batch_plan_destroy": (None, [ctypes.c_void_p]),
+    "synax_gemm_bf16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "synax_last_cuda_error": (ctypes.c_int, []),
     "synax_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "synax_version": (ctypes.c_int, []),

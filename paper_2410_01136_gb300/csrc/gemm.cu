@@ -1,0 +1,288 @@
+// gemm.cu -- BF16 tensor-core GEMM with FP32 accumulation on tcgen05 (sm_103a),
+// C[M][N] = A[M][K] . B[N][K]^T, both operands K-major, with fused epilogues
+// for the surrogate MLP (bias, GELU, GELU', transposed copies).
+//
+// One CTA of 128 threads computes a 128 x BN tile:
+//   thread 0 (warp 0)  TMA producer: 4-stage ring of 128x64 A and BNx64 B
+//                      BF16 tiles (128-byte swizzle), one mbarrier per stage
+//                      carrying the transaction bytes;
+//   thread 32 (warp 1) MMA issuer: 4 tcgen05.mma (K = 16 each) per stage into
+//                      a TMEM accumulator of BN FP32 columns, then
+//                      tcgen05.commit to the stage's "empty" barrier so the
+//                      producer may refill it, and finally to "done";
+//   warps 0-3          epilogue: tcgen05.ld of their 32 accumulator rows,
+//                      epilogue arithmetic, masked stores.
+// Every mbarrier wait gives up after ~1 s of SM clocks and sets *err; the
+// kernel then still frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "synax_internal.h"
+#include "tcgen05.cuh"
+
+namespace synax {
+
+enum GemmEpi : int {
+    EPI_F32 = 0,        // out_f32 = acc
+    EPI_BIAS_F32 = 1,   // out_f32 = acc + bias
+    EPI_BIAS_GELU = 2,  // z = acc + bias -> out_z (f32); gelu(z) -> out_bf16, out_bf16_t
+    EPI_GELU_BWD = 3,   // d = acc * gelu'(aux) -> out_bf16, out_bf16_t
+};
+
+struct GemmEpiParams {
+    const float* bias;
+    float* out_f32;
+    int ld_f32;
+    float* out_z;
+    int ld_z;
+    __nv_bfloat16* out_bf16;
+    int ld_bf16;
+    __nv_bfloat16* out_bf16_t;   // transposed copy: [N][ld_t]
+    int ld_t;
+    const float* aux;            // GELU' argument, [M][ld_aux]
+    int ld_aux;
+};
+
+constexpr int kGemmBM = 128;
+constexpr int kGemmBK = 64;
+constexpr int kGemmStages = 4;
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ bool mbar_wait_clock(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1)
+k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+            int K, GemmEpiParams ep, int* err) {
+    constexpr uint32_t A_BYTES = kGemmBM * kGemmBK * 2;
+    constexpr uint32_t B_BYTES = BN * kGemmBK * 2;
+    constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kGemmStages * A_BYTES;
+    uint64_t* full = (uint64_t*)(sB + kGemmStages * B_BYTES);
+    uint64_t* empty = full + kGemmStages;
+    uint64_t* done = empty + kGemmStages;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        tc::prefetch_tmap(&tmA);
+        tc::prefetch_tmap(&tmB);
+        for (int s = 0; s < kGemmStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    const int m0 = blockIdx.y * kGemmBM;
+    const int n0 = blockIdx.x * BN;
+    const int KT = K / kGemmBK;
+    bool ok = true;
+    int issued = 0;     // stage loads issued by the producer
+
+    if (warp == 0 && lane == 0) {
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % kGemmStages;
+            if (kt >= kGemmStages && !mbar_wait_clock(&empty[s], ((kt / kGemmStages) - 1) & 1)) {
+                ok = false;
+                break;
+            }
+            tc::mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+            tc::tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kt * kGemmBK, m0);
+            tc::tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kt * kGemmBK, n0);
+            ++issued;
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(kGemmBM, BN);
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % kGemmStages;
+            if (!mbar_wait_clock(&full[s], (kt / kGemmStages) & 1)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
+            const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
+                tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
+                             idesc, (kt | kk) != 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(done);
+    }
+    __syncwarp();
+
+    const bool have = __all_sync(0xffffffffu, mbar_wait_clock(done, 0) ? 1 : 0) != 0;
+    tc::fence_after_sync();
+    if (!have || !ok) atomicExch(err, 1);
+    if (have) {
+        const int row = m0 + warp * 32 + lane;
+        const bool row_ok = row < M;
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            if (!row_ok) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int col = n0 + c + i;
+                if (col >= N) break;
+                float x = v[i];
+                if constexpr (EPI == EPI_F32) {
+                    ep.out_f32[(long long)row * ep.ld_f32 + col] = x;
+                } else if constexpr (EPI == EPI_BIAS_F32) {
+                    ep.out_f32[(long long)row * ep.ld_f32 + col] = x + ep.bias[col];
+                } else if constexpr (EPI == EPI_BIAS_GELU) {
+                    const float z = x + ep.bias[col];
+                    if (ep.out_z) ep.out_z[(long long)row * ep.ld_z + col] = z;
+                    const __nv_bfloat16 a = __float2bfloat16_rn(gelu_f(z));
+                    ep.out_bf16[(long long)row * ep.ld_bf16 + col] = a;
+                    if (ep.out_bf16_t) ep.out_bf16_t[(long long)col * ep.ld_t + row] = a;
+                } else {
+                    const float z = ep.aux[(long long)row * ep.ld_aux + col];
+                    const __nv_bfloat16 d = __float2bfloat16_rn(x * gelu_grad_f(z));
+                    ep.out_bf16[(long long)row * ep.ld_bf16 + col] = d;
+                    if (ep.out_bf16_t) ep.out_bf16_t[(long long)col * ep.ld_t + row] = d;
+                }
+            }
+        }
+    }
+    // on failure, let the loads that may still be in flight (the last
+    // min(issued, stages) ones) land before the CTA exits
+    if (threadIdx.x == 0 && !ok) {
+        const int first = issued > kGemmStages ? issued - kGemmStages : 0;
+        for (int j = first; j < issued; ++j) mbar_wait_clock(&full[j % kGemmStages], (j / kGemmStages) & 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// 2-D BF16 tensor map of a row-major [rows][ld] matrix, box 64 x box_rows.
+int make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return SYNAX_ECUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SYNAX_OK : SYNAX_EINVAL;
+}
+
+template <int BN, int EPI>
+int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const GemmEpiParams& ep,
+                  int* err, cudaStream_t st) {
+    const size_t smem = 1024 + (size_t)kGemmStages * (kGemmBM + BN) * kGemmBK * 2 + 256;
+    static std::once_flag attr;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr, [&] {
+        attr_err = cudaFuncSetAttribute(k_gemm_bf16<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return record_cuda_error((int)attr_err);
+    dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM);
+    k_gemm_bf16<BN, EPI><<<grid, 128, smem, st>>>(ma, mb, M, N, K, ep, err);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
+}
+
+template <int EPI>
+int launch_gemm_bn(const CUtensorMap& ma, const void* B, int N, int K, int ldb, int M, const GemmEpiParams& ep,
+                   int* err, cudaStream_t st) {
+    // tile width: 256 for wide outputs, 64 for narrow ones
+    CUtensorMap mb;
+    if (N >= 2048) {
+        if (make_map(&mb, B, N, K, ldb, 256) != SYNAX_OK) return SYNAX_EINVAL;
+        return launch_gemm_t<256, EPI>(ma, mb, M, N, K, ep, err, st);
+    }
+    if (N >= 256) {
+        if (make_map(&mb, B, N, K, ldb, 128) != SYNAX_OK) return SYNAX_EINVAL;
+        return launch_gemm_t<128, EPI>(ma, mb, M, N, K, ep, err, st);
+    }
+    if (make_map(&mb, B, N, K, ldb, 64) != SYNAX_OK) return SYNAX_EINVAL;
+    return launch_gemm_t<64, EPI>(ma, mb, M, N, K, ep, err, st);
+}
+
+}  // namespace
+
+// C = A[M][K] . B[N][K]^T with the given epilogue.  A, B: BF16 row-major with
+// row pitches lda, ldb (elements); K a multiple of 64; pitches multiples of
+// 8; base pointers 16-byte aligned.
+int gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int epi,
+              const GemmEpiParams& ep, int* err, cudaStream_t st) {
+    if (M < 1 || N < 1 || K < kGemmBK || K % kGemmBK != 0) return SYNAX_EINVAL;
+    if (lda < K || ldb < K || lda % 8 != 0 || ldb % 8 != 0) return SYNAX_EINVAL;
+    if (((uintptr_t)A | (uintptr_t)B) & 15) return SYNAX_EINVAL;
+    CUtensorMap ma;
+    if (make_map(&ma, A, M, K, lda, kGemmBM) != SYNAX_OK) return SYNAX_EINVAL;
+    switch (epi) {
+    case EPI_F32: return launch_gemm_bn<EPI_F32>(ma, B, N, K, ldb, M, ep, err, st);
+    case EPI_BIAS_F32: return launch_gemm_bn<EPI_BIAS_F32>(ma, B, N, K, ldb, M, ep, err, st);
+    case EPI_BIAS_GELU: return launch_gemm_bn<EPI_BIAS_GELU>(ma, B, N, K, ldb, M, ep, err, st);
+    case EPI_GELU_BWD: return launch_gemm_bn<EPI_GELU_BWD>(ma, B, N, K, ldb, M, ep, err, st);
+    default: return SYNAX_EINVAL;
+    }
+}
+
+}  // namespace synax
+
+using namespace synax;
+
+extern "C" int synax_gemm_bf16(const void* a_dev, int lda, const void* b_dev, int ldb, int M, int N, int K,
+                               float* c_dev, int ldc, int* err_dev, void* stream) {
+    if (!a_dev || !b_dev || !c_dev || !err_dev || ldc < N) return SYNAX_EINVAL;
+    GemmEpiParams ep{};
+    ep.out_f32 = c_dev;
+    ep.ld_f32 = ldc;
+    return gemm_bf16(a_dev, lda, b_dev, ldb, M, N, K, EPI_F32, ep, err_dev, (cudaStream_t)stream);
+}
