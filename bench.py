@@ -43,6 +43,9 @@ ADJ_FACTOR = 3
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
+# DRAM bytes (read + write) of one k_adjoint launch of this workload, from the
+# ncu capture summarised in profiles/k_adjoint_jf12_nside64_512steps.md
+ADJ_DRAM_BYTES = 2.432e6
 
 
 def parse():
@@ -52,6 +55,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="synax", choices=["synax", "reference"])
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-set ensemble measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the CPU oracle")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 8, 16, 32],
+                    help="lanes per ray for every launch (0: autotune per step-count bin)")
     return ap.parse_args()
 
 
@@ -248,9 +254,14 @@ def run_synax(args):
     dev = torch.device("cuda", torch.cuda.current_device())
 
     import paper_2410_01136_gb300 as sx
-    from paper_2410_01136_gb300 import inputs, tune
+    from paper_2410_01136_gb300 import _native, inputs, tune
     sx.build()
-    lanes_table = tune.load_or_tune()          # launch width per step-count bin (cached per device)
+    if args.lanes:
+        tune.reset()
+        _native.check(_native.lib().synax_set_lanes_per_ray(-1, args.lanes), "synax_set_lanes_per_ray")
+        lanes_table = {n: args.lanes for n in tune.STEP_BINS}
+    else:
+        lanes_table = tune.load_or_tune()      # launch width per step-count bin (cached per device)
 
     prob, th_target, sigma = inputs.config3(seed=3 + rank)
     # target: forward map of the perturbed parameters plus N(0, sigma^2) noise
@@ -358,7 +369,7 @@ def run_synax(args):
         "peak": fp32_peak if bound_is_fp32 else mufu_peak,
         "unit": "T FP32 op/s" if bound_is_fp32 else "T MUFU op/s",
         "frac": (fp32_ach / fp32_peak) if bound_is_fp32 else (mufu_ach / mufu_peak),
-        "traffic": None,
+        "traffic": ADJ_DRAM_BYTES,
         "kernel": "k_adjoint (+ k_reduce_partials)",
         "ops_per_sample": {"fp32": ADJ_FACTOR * FWD_FP32_OPS, "mufu": ADJ_FACTOR * FWD_MUFU_OPS},
         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x median SM clock "
@@ -389,7 +400,7 @@ def run_synax(args):
         out["batch_low_res"] = bench_batch(sx, inputs, torch, dev, n_runs=20, sets=chains,
                                            name="256 chains, Nside 16, 256 steps, chi^2 map+gradient")
         out["gpu_launches_batch_per_run"] = 2
-    if rank == 0:
+    if rank == 0 and not args.no_cpu_baseline:
         try:
             rate, dt, threads, desc = oracle_map_grad_rate(8192)
             out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
@@ -397,6 +408,7 @@ def run_synax(args):
         except Exception as exc:  # the oracle is a baseline; report why it is absent
             out["cpu_baseline"] = {"value": None, "unit": "samples/s", "cores": os.cpu_count(),
                                    "kind": "oracle", "sample": f"failed: {exc}"}
+    if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
