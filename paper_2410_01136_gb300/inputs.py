@@ -256,3 +256,47 @@ def sample_pixels(npix: int, count: int, seed: int = 11) -> np.ndarray:
     count = min(count, npix)
     keys = splitmix64(substream(seed, npix), npix)
     return np.sort(np.argsort(keys, kind="stable")[:count]).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate (parameters -> basis coefficients of a 408 MHz map)
+# ---------------------------------------------------------------------------
+
+SURROGATE_FREQ_HZ = (408e6,)
+SURROGATE_WIDTHS = (16, 1024, 1024, 1024, 1024, 3 * 3072)
+
+
+def config5_box(frac: float = 0.2) -> tuple[np.ndarray, np.ndarray]:
+    """The training box theta_fid -/+ frac * scale_i as (lo, hi)."""
+    fid = jf12_fiducial(2)
+    scale = jf12_scales(fid)
+    return fid - frac * scale, fid + frac * scale
+
+
+def config5_problem() -> Problem:
+    """The map the surrogate emulates: Nside 64, 512 steps, 408 MHz, JF12-type."""
+    return config2().replace(freq_hz=SURROGATE_FREQ_HZ)
+
+
+def surrogate_basis_spec(nside: int, n_basis: int, seed: int = 5) -> tuple[np.ndarray, np.ndarray]:
+    """Seeded draws defining the basis: a sign per pixel (+1/-1, int8) and
+    n_basis distinct row indices in [0, 12 nside^2) (int32, in draw order)."""
+    npix = 12 * nside * nside
+    if not 1 <= n_basis <= npix:
+        raise ValueError("n_basis must be in [1, npix]")
+    signs = np.where((splitmix64(substream(seed, 1), npix) >> np.uint64(63)) == 0, 1, -1).astype(np.int8)
+    keys = splitmix64(substream(seed, 2), npix)
+    rows = np.argsort(keys, kind="stable")[:n_basis].astype(np.int32)
+    return signs, rows
+
+
+def mlp_init(widths=SURROGATE_WIDTHS, seed: int = 7) -> list[tuple[np.ndarray, np.ndarray]]:
+    """Initial weights: W_l ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) of shape
+    [out, in] (float32), biases zero."""
+    params = []
+    for l in range(len(widths) - 1):
+        fan_in, fan_out = widths[l], widths[l + 1]
+        b = 1.0 / math.sqrt(fan_in)
+        w = uniform(substream(seed, l + 1), fan_out * fan_in, -b, b).reshape(fan_out, fan_in)
+        params.append((w.astype(np.float32), np.zeros(fan_out, dtype=np.float32)))
+    return params
