@@ -197,6 +197,125 @@ int synax_adjoint_noalloc(const synax_problem* prob, const void* gmaps_dev, cons
 int synax_eval_fields(const synax_problem* prob, const double* pos_dev, const double* t_dev,
                       int64_t n, double* out_dev, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate (no counterpart in the paper: an extension that
+ * emulates the simulator).  A multilayer perceptron maps the model parameters theta to the
+ * coefficients of the single-frequency I/Q/U brightness-temperature maps in
+ * a seeded orthonormal basis of the HEALPix pixels:
+ *   e_i[p] = sign[p] * H_N[rows[i]][p] / sqrt(N),  N = 12 nside^2,
+ *   H_N = H_12 (x) H_M, M = nside^2 (Paley order-12 Hadamard matrix times
+ *   Sylvester's; rows i of the same H_N are orthogonal),
+ * so coefficient c[s][i] = sum_p e_i[p] map[s][p] (s = I, Q, U) and the
+ * in-subspace RMS residual of a coefficient vector is ||dc||_2 / sqrt(N).
+ * Network: x = 2 (theta - lo) / (hi - lo) - 1 -> depth hidden layers of
+ * `width` with GELU (exact erf form) -> 3 n_basis outputs y; c = mean + scale * y.
+ * Matrix products run on the BF16 tensor cores with FP32 accumulation;
+ * master weights and Adam moments are FP32.  It is trained on maps that
+ * synax_forward renders, and synax_surrogate_judge compares it with those
+ * maps and falls back to them.  The library owns every buffer of the handle;
+ * all calls are on one device and, unless stated, asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+typedef struct synax_surrogate_s synax_surrogate_t;
+
+typedef struct {
+    int32_t n_theta;       /* inputs, 1..64 (the JF12-type model: 16) */
+    int32_t width;         /* hidden width, a multiple of 64, <= 8192 */
+    int32_t depth;         /* hidden layers, 1..8 */
+    int32_t nside;         /* map resolution of the basis, power of two, 4..256 */
+    int32_t n_basis;       /* coefficients per Stokes parameter, a multiple of 64, <= 12 nside^2 */
+    int32_t batch;         /* training batch, a multiple of 64, 64..65536 */
+    int32_t max_eval;      /* rows per internal chunk of synax_surrogate, 1..65536 */
+    int32_t map_chunk;     /* maps rendered per projection chunk (dataset, judge), 1..1024 */
+    int32_t total_steps;   /* length of the cosine learning-rate schedule, >= 1 */
+    int32_t reserved;
+    double lr, lr_min;     /* Adam step size: cosine decay lr -> lr_min over total_steps */
+    double beta1, beta2, eps;
+    double theta_lo[64], theta_hi[64];   /* input box (physical units), hi > lo */
+    const int8_t* basis_sign;            /* host [12 nside^2], each +1 or -1; copied */
+    const int32_t* basis_rows;           /* host [n_basis], distinct, in [0, 12 nside^2); copied */
+} synax_surrogate_cfg;
+
+enum {
+    SYNAX_SUR_PARAMS = 0,   /* flat parameters: per layer W [out][in] (in_0 = n_theta), then b [out] */
+    SYNAX_SUR_GRADS = 1,    /* gradient of the last synax_surrogate_step / training step, same layout */
+    SYNAX_SUR_ADAM_M = 2,   /* Adam first moments, same layout */
+    SYNAX_SUR_ADAM_V = 3,   /* Adam second moments, same layout */
+    SYNAX_SUR_NORM = 4,     /* output normalisation: mean [3 n_basis] then scale (n = 3 n_basis + 1) */
+    SYNAX_SUR_LOSS = 5      /* losses of the last n optimiser steps, oldest first (n <= 65536) */
+};
+
+/* Create a surrogate: allocates all device buffers, builds the basis,
+ * zero weights (set them with synax_surrogate_set_params).  Synchronous. */
+int synax_surrogate_create(const synax_surrogate_cfg* cfg, synax_surrogate_t** out);
+void synax_surrogate_destroy(synax_surrogate_t* s);
+
+/* Number of floats of the flat parameter layout. */
+size_t synax_surrogate_param_count(const synax_surrogate_t* s);
+
+/* Replace the weights (host, flat layout) and reset the Adam state and step
+ * counter.  Synchronous. */
+int synax_surrogate_set_params(synax_surrogate_t* s, const float* host, size_t n);
+
+/* Copy a quantity (SYNAX_SUR_*) to host memory; waits for the device. */
+int synax_surrogate_get(synax_surrogate_t* s, int what, float* host, size_t n);
+
+/* Output normalisation c = mean + scale * y (host mean [3 n_basis], scale > 0).
+ * synax_surrogate_dataset sets it from the training maps. */
+int synax_surrogate_set_normalization(synax_surrogate_t* s, const float* mean_host, float scale);
+
+/* Project maps onto the basis: maps_dev [n_rows][12 nside^2] float32 ->
+ * coeffs_dev [n_rows][n_basis] float32 (one row per Stokes map). */
+int synax_surrogate_project(synax_surrogate_t* s, const float* maps_dev, long long n_rows, float* coeffs_dev,
+                            void* stream);
+
+/* Training set: renders the map of `fiducial` (one frequency, full sky,
+ * FP32, nside and n_theta of the surrogate) for each parameter row of
+ * theta_host [n][n_theta] (host doubles), projects it, and stores
+ * (theta, normalised coefficients) on the device; sets the output
+ * normalisation from them.  n in [batch, 2^30].  Waits for the device. */
+int synax_surrogate_dataset(synax_surrogate_t* s, const synax_problem* fiducial, const double* theta_host,
+                            long long n, void* stream);
+
+/* One forward + backward pass on an explicit batch: theta_dev [batch][n_theta],
+ * coeff_dev [batch][3 n_basis] physical coefficients (device float32).  Loss =
+ * mean over the batch and outputs of (y - (c - mean) / scale)^2, written to
+ * loss_dev (device float) if not NULL; the gradient is readable with
+ * SYNAX_SUR_GRADS.  update = 1 also takes one Adam step. */
+int synax_surrogate_step(synax_surrogate_t* s, const float* theta_dev, const float* coeff_dev, int n, int update,
+                         float* loss_dev, void* stream);
+
+/* n_steps Adam steps over the training set: each step draws `batch` samples
+ * without replacement within an epoch (a seeded counter-based shuffle per
+ * epoch).  The step is captured once into a CUDA graph and replayed.
+ * Per-step losses are readable with SYNAX_SUR_LOSS.  n_steps <= 65536. */
+int synax_surrogate_train(synax_surrogate_t* s, int n_steps, uint64_t seed, void* stream);
+
+/* Evaluate: theta_dev [n][n_theta] -> coeffs_dev [n][3][n_basis] (device
+ * float32, physical units).  With gcoeff_dev [n][3][n_basis] (a seed
+ * dL/dc) also writes gtheta_dev [n][n_theta] = dL/dtheta (both or neither). */
+int synax_surrogate(synax_surrogate_t* s, const float* theta_dev, int n, float* coeffs_dev,
+                    const float* gcoeff_dev, float* gtheta_dev, void* stream);
+
+/* Judge and fall back: renders the map of each parameter row of theta_host
+ * [n][n_theta] with synax_forward (as in synax_surrogate_dataset), projects
+ * it, and forms rms[s] = ||coeffs[s] - c_march[s]||_2 / sqrt(12 nside^2) for
+ * s = I, Q, U.  Where any rms exceeds rms_max_K (kelvin) the row of
+ * coeffs_dev is replaced by the march's coefficients and fell_back = 1.
+ * rms_dev [n][3] floats and fell_back_dev [n] ints (device) may be NULL. */
+int synax_surrogate_judge(synax_surrogate_t* s, const synax_problem* fiducial, const double* theta_host, int n,
+                          float* coeffs_dev, double rms_max_K, float* rms_dev, int* fell_back_dev,
+                          void* stream);
+
+/* Waits for `stream`; SYNAX_ETIMEOUT if a bounded wait of a tensor-core
+ * kernel of this surrogate gave up since creation, else SYNAX_OK. */
+int synax_surrogate_status(synax_surrogate_t* s, void* stream);
+
+/* Checkpoint: weights, Adam moments, step counter, normalisation, basis
+ * definition and input box to a binary file; load requires a surrogate
+ * created with the same configuration and basis.  Synchronous. */
+int synax_surrogate_save(synax_surrogate_t* s, const char* path);
+int synax_surrogate_load(synax_surrogate_t* s, const char* path);
+
 /* Launch tuning (no counterpart in the paper): lanes of a warp that march
  * one ray, 8, 16 or 32.  lanes = 0 restores the built-in rule.  With
  * n_steps_min >= 0 the value applies to maps whose step count falls in the

@@ -56,6 +56,23 @@ class SynaxProblem(ctypes.Structure):
 
 
 #: Exported symbols of include/synax.h with (restype, argtypes).
+class SynaxSurrogateCfg(ctypes.Structure):
+    """Mirror of synax_surrogate_cfg (include/synax.h)."""
+    _fields_ = [
+        ("n_theta", ctypes.c_int32), ("width", ctypes.c_int32), ("depth", ctypes.c_int32),
+        ("nside", ctypes.c_int32), ("n_basis", ctypes.c_int32), ("batch", ctypes.c_int32),
+        ("max_eval", ctypes.c_int32), ("map_chunk", ctypes.c_int32), ("total_steps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("lr", ctypes.c_double), ("lr_min", ctypes.c_double), ("beta1", ctypes.c_double),
+        ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+        ("theta_lo", ctypes.c_double * 64), ("theta_hi", ctypes.c_double * 64),
+        ("basis_sign", ctypes.POINTER(ctypes.c_int8)), ("basis_rows", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+SUR_PARAMS, SUR_GRADS, SUR_ADAM_M, SUR_ADAM_V, SUR_NORM, SUR_LOSS = range(6)
+_VP = ctypes.c_void_p
+
 SIGNATURES = {
     "synax_forward": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p, ctypes.c_void_p]),
     "synax_adjoint_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(SynaxProblem),
@@ -83,6 +100,22 @@ SIGNATURES = {
     "synax_gemm_bf16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "synax_surrogate_create": (ctypes.c_int, [ctypes.POINTER(SynaxSurrogateCfg), ctypes.POINTER(_VP)]),
+    "synax_surrogate_destroy": (None, [_VP]),
+    "synax_surrogate_param_count": (ctypes.c_size_t, [_VP]),
+    "synax_surrogate_set_params": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "synax_surrogate_get": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t]),
+    "synax_surrogate_set_normalization": (ctypes.c_int, [_VP, _VP, ctypes.c_float]),
+    "synax_surrogate_project": (ctypes.c_int, [_VP, _VP, ctypes.c_longlong, _VP, _VP]),
+    "synax_surrogate_dataset": (ctypes.c_int, [_VP, ctypes.POINTER(SynaxProblem), _VP, ctypes.c_longlong, _VP]),
+    "synax_surrogate_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "synax_surrogate_train": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint64, _VP]),
+    "synax_surrogate": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "synax_surrogate_judge": (ctypes.c_int, [_VP, ctypes.POINTER(SynaxProblem), _VP, ctypes.c_int, _VP,
+                                             ctypes.c_double, _VP, _VP, _VP]),
+    "synax_surrogate_status": (ctypes.c_int, [_VP, _VP]),
+    "synax_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "synax_surrogate_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "synax_last_cuda_error": (ctypes.c_int, []),
     "synax_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "synax_version": (ctypes.c_int, []),

@@ -20,31 +20,11 @@
 
 #include <mutex>
 
+#include "gemm.cuh"
 #include "synax_internal.h"
 #include "tcgen05.cuh"
 
 namespace synax {
-
-enum GemmEpi : int {
-    EPI_F32 = 0,        // out_f32 = acc
-    EPI_BIAS_F32 = 1,   // out_f32 = acc + bias
-    EPI_BIAS_GELU = 2,  // z = acc + bias -> out_z (f32); gelu(z) -> out_bf16, out_bf16_t
-    EPI_GELU_BWD = 3,   // d = acc * gelu'(aux) -> out_bf16, out_bf16_t
-};
-
-struct GemmEpiParams {
-    const float* bias;
-    float* out_f32;
-    int ld_f32;
-    float* out_z;
-    int ld_z;
-    __nv_bfloat16* out_bf16;
-    int ld_bf16;
-    __nv_bfloat16* out_bf16_t;   // transposed copy: [N][ld_t]
-    int ld_t;
-    const float* aux;            // GELU' argument, [M][ld_aux]
-    int ld_aux;
-};
 
 constexpr int kGemmBM = 128;
 constexpr int kGemmBK = 64;
@@ -141,36 +121,78 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const bool have = __all_sync(0xffffffffu, mbar_wait_clock(done, 0) ? 1 : 0) != 0;
     tc::fence_after_sync();
     if (!have || !ok) atomicExch(err, 1);
+    float sq = 0.0f;     // EPI_MSE: this thread's sum of squared residuals
     if (have) {
         const int row = m0 + warp * 32 + lane;
         const bool row_ok = row < M;
+        long long trow = row;
+        if constexpr (EPI == EPI_MSE) {
+            if (row_ok && ep.target_rows) trow = ep.target_rows[row];
+        }
         for (int c = 0; c < BN; c += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (!row_ok) continue;
+            if (!row_ok || n0 + c >= N) continue;
+            const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
+            const int col0 = n0 + c;
+            if constexpr (EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC) {
+                float* o = ep.out_f32 + (long long)row * ep.ld_f32 + col0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int col = n0 + c + i;
-                if (col >= N) break;
-                float x = v[i];
-                if constexpr (EPI == EPI_F32) {
-                    ep.out_f32[(long long)row * ep.ld_f32 + col] = x;
-                } else if constexpr (EPI == EPI_BIAS_F32) {
-                    ep.out_f32[(long long)row * ep.ld_f32 + col] = x + ep.bias[col];
-                } else if constexpr (EPI == EPI_BIAS_GELU) {
-                    const float z = x + ep.bias[col];
-                    if (ep.out_z) ep.out_z[(long long)row * ep.ld_z + col] = z;
-                    const __nv_bfloat16 a = __float2bfloat16_rn(gelu_f(z));
-                    ep.out_bf16[(long long)row * ep.ld_bf16 + col] = a;
-                    if (ep.out_bf16_t) ep.out_bf16_t[(long long)col * ep.ld_t + row] = a;
+                for (int i = 0; i < 16; ++i) {
+                    if (i >= nv) break;
+                    const int col = col0 + i;
+                    float x = v[i];
+                    if constexpr (EPI == EPI_BIAS_F32) x += ep.bias[col];
+                    if constexpr (EPI == EPI_AFFINE) {
+                        if (ep.bias) x += ep.bias[col];
+                        x *= ep.colscale ? ep.colscale[col] : ep.scale;
+                        if (ep.shift) x += ep.shift[col];
+                    }
+                    if constexpr (EPI == EPI_SCALE_ACC) x = ep.accumulate ? fmaf(ep.scale, x, o[i]) : ep.scale * x;
+                    o[i] = x;
+                }
+            } else {
+                __nv_bfloat16 r[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int col = col0 + (i < nv ? i : 0);
+                    float x = v[i];
+                    if constexpr (EPI == EPI_BIAS_GELU) {
+                        const float z = x + ep.bias[col];
+                        if (ep.out_z && i < nv) ep.out_z[(long long)row * ep.ld_z + col] = z;
+                        x = gelu_f(z);
+                    } else if constexpr (EPI == EPI_GELU_BWD) {
+                        x *= gelu_grad_f(ep.aux[(long long)row * ep.ld_aux + col]);
+                    } else {   // EPI_MSE
+                        const float d = x + ep.bias[col] - ep.target[trow * ep.ld_target + col];
+                        if (i < nv) sq = fmaf(d, d, sq);
+                        x = ep.coef * d;
+                    }
+                    r[i] = __float2bfloat16_rn(x);
+                }
+                __nv_bfloat16* o = ep.out_bf16 + (long long)row * ep.ld_bf16 + col0;
+                if (nv == 16 && (((uintptr_t)o) & 15) == 0) {
+                    const uint4* src = reinterpret_cast<const uint4*>(r);
+                    reinterpret_cast<uint4*>(o)[0] = src[0];
+                    reinterpret_cast<uint4*>(o)[1] = src[1];
                 } else {
-                    const float z = ep.aux[(long long)row * ep.ld_aux + col];
-                    const __nv_bfloat16 d = __float2bfloat16_rn(x * gelu_grad_f(z));
-                    ep.out_bf16[(long long)row * ep.ld_bf16 + col] = d;
-                    if (ep.out_bf16_t) ep.out_bf16_t[(long long)col * ep.ld_t + row] = d;
+                    for (int i = 0; i < nv; ++i) o[i] = r[i];
+                }
+                if (ep.out_bf16_t) {
+                    for (int i = 0; i < nv; ++i) ep.out_bf16_t[(long long)(col0 + i) * ep.ld_t + row] = r[i];
                 }
             }
         }
+    }
+    if constexpr (EPI == EPI_MSE) {
+        // fixed-order CTA reduction of the squared residuals
+        __shared__ float red[4];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[warp] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            ep.loss_partial[blockIdx.y * gridDim.x + blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
     }
     // on failure, let the loads that may still be in flight (the last
     // min(issued, stages) ones) land before the CTA exits
@@ -186,6 +208,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// tile width: 256 for wide outputs, 128 for medium, 64 for narrow ones
+static int gemm_bn_for(int N) { return N >= 2048 ? 256 : (N >= 256 ? 128 : 64); }
+
 namespace {
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -221,17 +246,29 @@ int make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int
 }
 
 template <int BN, int EPI>
+constexpr size_t gemm_smem() {
+    return 1024 + (size_t)kGemmStages * (kGemmBM + BN) * kGemmBK * 2 + 256;
+}
+
+template <int BN, int EPI>
+cudaError_t set_smem_attr() {
+    return cudaFuncSetAttribute(k_gemm_bf16<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gemm_smem<BN, EPI>());
+}
+
+template <int EPI>
+cudaError_t set_smem_attrs() {
+    cudaError_t e = set_smem_attr<64, EPI>();
+    if (e == cudaSuccess) e = set_smem_attr<128, EPI>();
+    if (e == cudaSuccess) e = set_smem_attr<256, EPI>();
+    return e;
+}
+
+template <int BN, int EPI>
 int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const GemmEpiParams& ep,
                   int* err, cudaStream_t st) {
-    const size_t smem = 1024 + (size_t)kGemmStages * (kGemmBM + BN) * kGemmBK * 2 + 256;
-    static std::once_flag attr;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr, [&] {
-        attr_err = cudaFuncSetAttribute(k_gemm_bf16<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
-    if (attr_err != cudaSuccess) return record_cuda_error((int)attr_err);
     dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM);
-    k_gemm_bf16<BN, EPI><<<grid, 128, smem, st>>>(ma, mb, M, N, K, ep, err);
+    k_gemm_bf16<BN, EPI><<<grid, 128, gemm_smem<BN, EPI>(), st>>>(ma, mb, M, N, K, ep, err);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
 }
@@ -239,13 +276,13 @@ int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, in
 template <int EPI>
 int launch_gemm_bn(const CUtensorMap& ma, const void* B, int N, int K, int ldb, int M, const GemmEpiParams& ep,
                    int* err, cudaStream_t st) {
-    // tile width: 256 for wide outputs, 64 for narrow ones
     CUtensorMap mb;
-    if (N >= 2048) {
+    const int bn = gemm_bn_for(N);
+    if (bn == 256) {
         if (make_map(&mb, B, N, K, ldb, 256) != SYNAX_OK) return SYNAX_EINVAL;
         return launch_gemm_t<256, EPI>(ma, mb, M, N, K, ep, err, st);
     }
-    if (N >= 256) {
+    if (bn == 128) {
         if (make_map(&mb, B, N, K, ldb, 128) != SYNAX_OK) return SYNAX_EINVAL;
         return launch_gemm_t<128, EPI>(ma, mb, M, N, K, ep, err, st);
     }
@@ -255,6 +292,28 @@ int launch_gemm_bn(const CUtensorMap& ma, const void* B, int N, int K, int ldb, 
 
 }  // namespace
 
+// Opt every instantiation into its dynamic shared memory once, so that no
+// attribute call happens later (for instance while a stream is captured).
+int gemm_init() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = set_smem_attrs<EPI_F32>();
+        if (err == cudaSuccess) err = set_smem_attrs<EPI_BIAS_F32>();
+        if (err == cudaSuccess) err = set_smem_attrs<EPI_BIAS_GELU>();
+        if (err == cudaSuccess) err = set_smem_attrs<EPI_GELU_BWD>();
+        if (err == cudaSuccess) err = set_smem_attrs<EPI_MSE>();
+        if (err == cudaSuccess) err = set_smem_attrs<EPI_AFFINE>();
+        if (err == cudaSuccess) err = set_smem_attrs<EPI_SCALE_ACC>();
+    });
+    return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
+}
+
+int gemm_tiles(int M, int N) {
+    const int bn = gemm_bn_for(N);
+    return ((N + bn - 1) / bn) * ((M + kGemmBM - 1) / kGemmBM);
+}
+
 // C = A[M][K] . B[N][K]^T with the given epilogue.  A, B: BF16 row-major with
 // row pitches lda, ldb (elements); K a multiple of 64; pitches multiples of
 // 8; base pointers 16-byte aligned.
@@ -263,6 +322,8 @@ int gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int 
     if (M < 1 || N < 1 || K < kGemmBK || K % kGemmBK != 0) return SYNAX_EINVAL;
     if (lda < K || ldb < K || lda % 8 != 0 || ldb % 8 != 0) return SYNAX_EINVAL;
     if (((uintptr_t)A | (uintptr_t)B) & 15) return SYNAX_EINVAL;
+    const int rc = gemm_init();
+    if (rc != SYNAX_OK) return rc;
     CUtensorMap ma;
     if (make_map(&ma, A, M, K, lda, kGemmBM) != SYNAX_OK) return SYNAX_EINVAL;
     switch (epi) {
@@ -270,6 +331,9 @@ int gemm_bf16(const void* A, int lda, const void* B, int ldb, int M, int N, int 
     case EPI_BIAS_F32: return launch_gemm_bn<EPI_BIAS_F32>(ma, B, N, K, ldb, M, ep, err, st);
     case EPI_BIAS_GELU: return launch_gemm_bn<EPI_BIAS_GELU>(ma, B, N, K, ldb, M, ep, err, st);
     case EPI_GELU_BWD: return launch_gemm_bn<EPI_GELU_BWD>(ma, B, N, K, ldb, M, ep, err, st);
+    case EPI_MSE: return launch_gemm_bn<EPI_MSE>(ma, B, N, K, ldb, M, ep, err, st);
+    case EPI_AFFINE: return launch_gemm_bn<EPI_AFFINE>(ma, B, N, K, ldb, M, ep, err, st);
+    case EPI_SCALE_ACC: return launch_gemm_bn<EPI_SCALE_ACC>(ma, B, N, K, ldb, M, ep, err, st);
     default: return SYNAX_EINVAL;
     }
 }
