@@ -1,19 +1,27 @@
 // gemm.cu -- BF16 tensor-core GEMM with FP32 accumulation on tcgen05 (sm_103a),
 // C[M][N] = A[M][K] . B[N][K]^T, both operands K-major, with fused epilogues
-// for the surrogate MLP (bias, GELU, GELU', transposed copies).
+// for the surrogate MLP (bias, GELU, GELU', MSE, affine output, transposed
+// copies).
 //
-// One CTA of 128 threads computes a 128 x BN tile:
-//   thread 0 (warp 0)  TMA producer: 4-stage ring of 128x64 A and BNx64 B
-//                      BF16 tiles (128-byte swizzle), one mbarrier per stage
-//                      carrying the transaction bytes;
-//   thread 32 (warp 1) MMA issuer: 4 tcgen05.mma (K = 16 each) per stage into
-//                      a TMEM accumulator of BN FP32 columns, then
-//                      tcgen05.commit to the stage's "empty" barrier so the
-//                      producer may refill it, and finally to "done";
-//   warps 0-3          epilogue: tcgen05.ld of their 32 accumulator rows,
-//                      epilogue arithmetic, masked stores.
-// Every mbarrier wait gives up after ~1 s of SM clocks and sets *err; the
-// kernel then still frees its TMEM and returns.
+// Persistent and warp-specialised: min(tiles, SMs) CTAs of 192 threads walk
+// the 128 x BN output tiles (row-major tile order, so concurrent CTAs share
+// A row blocks and the whole B operand stays in L2):
+//   warp 0 (one thread)  TMA producer: a ring of ST stages, each a 128x64 A
+//                        and a BNx64 B BF16 tile (128-byte swizzle) with a
+//                        "full" mbarrier carrying the transaction bytes;
+//   warp 1 (one thread)  MMA issuer: 4 tcgen05.mma (K = 16) per stage into
+//                        one of two TMEM accumulators of BN FP32 columns;
+//                        tcgen05.commit frees the stage ("empty") and, after
+//                        a tile's last stage, hands the accumulator to the
+//                        epilogue ("acc_full");
+//   warps 2-5            epilogue: tcgen05.ld of their 32 TMEM lanes (warp w
+//                        reads lanes 32 (w % 4) .. +31), epilogue arithmetic,
+//                        vectorised row stores (coalesced transposed stores),
+//                        then release the accumulator ("acc_empty").
+// With two accumulators the MMAs of tile i+1 run while tile i is stored.
+// Every mbarrier wait gives up after ~1 s of SM clocks and sets *err; each
+// role then stops, the MMA issuer waits (bounded) for its issued MMAs, the
+// producer for its loads in flight, and the CTA frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -28,8 +36,17 @@ namespace synax {
 
 constexpr int kGemmBM = 128;
 constexpr int kGemmBK = 64;
-constexpr int kGemmStages = 4;
+constexpr int kGemmThreads = 192;
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+
+template <int BN>
+struct GemmCfg {
+    static constexpr int ST = BN == 256 ? 4 : 6;                       // pipeline stages
+    static constexpr uint32_t A_BYTES = kGemmBM * kGemmBK * 2;
+    static constexpr uint32_t B_BYTES = BN * kGemmBK * 2;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;                      // two accumulators
+    static constexpr size_t SMEM = 1024 + (size_t)ST * (A_BYTES + B_BYTES) + 256;
+};
 
 __device__ __forceinline__ bool mbar_wait_clock(uint64_t* bar, uint32_t parity) {
     const long long t0 = clock64();
@@ -39,170 +56,242 @@ __device__ __forceinline__ bool mbar_wait_clock(uint64_t* bar, uint32_t parity) 
     return true;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
+// Epilogue of 16 consecutive columns col0.. of one row (nv of them valid).
+template <int EPI>
+__device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float* v, int row, int col0, int nv,
+                                           long long trow, float& sq) {
+    if constexpr (EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC) {
+        float* o = ep.out_f32 + (long long)row * ep.ld_f32 + col0;
+        float r[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int col = col0 + (i < nv ? i : 0);
+            float x = v[i];
+            if constexpr (EPI == EPI_BIAS_F32) x += ep.bias[col];
+            if constexpr (EPI == EPI_AFFINE) {
+                if (ep.bias) x += ep.bias[col];
+                x *= ep.colscale ? ep.colscale[col] : ep.scale;
+                if (ep.shift) x += ep.shift[col];
+            }
+            if constexpr (EPI == EPI_SCALE_ACC) x = ep.accumulate ? fmaf(ep.scale, x, o[i < nv ? i : 0]) : ep.scale * x;
+            r[i] = x;
+        }
+        if (nv == 16 && (((uintptr_t)o) & 15) == 0) {
+            float4* d = reinterpret_cast<float4*>(o);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+        } else {
+            for (int i = 0; i < nv; ++i) o[i] = r[i];
+        }
+    } else {
+        __nv_bfloat16 r[16];
+        float z16[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int col = col0 + (i < nv ? i : 0);
+            float x = v[i];
+            if constexpr (EPI == EPI_BIAS_GELU) {
+                const float z = x + ep.bias[col];
+                z16[i] = z;
+                x = gelu_f(z);
+            } else if constexpr (EPI == EPI_GELU_BWD) {
+                x *= gelu_grad_f(ep.aux[(long long)row * ep.ld_aux + col]);
+            } else {   // EPI_MSE
+                const float d = x + ep.bias[col] - ep.target[trow * ep.ld_target + col];
+                if (i < nv) sq = fmaf(d, d, sq);
+                x = ep.coef * d;
+            }
+            r[i] = __float2bfloat16_rn(x);
+        }
+        if constexpr (EPI == EPI_BIAS_GELU) {
+            if (ep.out_z) {
+                float* oz = ep.out_z + (long long)row * ep.ld_z + col0;
+                if (nv == 16 && (((uintptr_t)oz) & 15) == 0) {
+                    float4* d = reinterpret_cast<float4*>(oz);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        d[q] = make_float4(z16[4 * q], z16[4 * q + 1], z16[4 * q + 2], z16[4 * q + 3]);
+                } else {
+                    for (int i = 0; i < nv; ++i) oz[i] = z16[i];
+                }
+            }
+        }
+        __nv_bfloat16* o = ep.out_bf16 + (long long)row * ep.ld_bf16 + col0;
+        if (nv == 16 && (((uintptr_t)o) & 15) == 0) {
+            const uint4* src = reinterpret_cast<const uint4*>(r);
+            reinterpret_cast<uint4*>(o)[0] = src[0];
+            reinterpret_cast<uint4*>(o)[1] = src[1];
+        } else {
+            for (int i = 0; i < nv; ++i) o[i] = r[i];
+        }
+        if (ep.out_bf16_t) {
+            for (int i = 0; i < nv; ++i) ep.out_bf16_t[(long long)(col0 + i) * ep.ld_t + row] = r[i];
+        }
+    }
+}
+
 template <int BN, int EPI>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
             int K, GemmEpiParams ep, int* err) {
-    constexpr uint32_t A_BYTES = kGemmBM * kGemmBK * 2;
-    constexpr uint32_t B_BYTES = BN * kGemmBK * 2;
-    constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    using C = GemmCfg<BN>;
+    constexpr int ST = C::ST;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
-    uint8_t* sB = smem + kGemmStages * A_BYTES;
-    uint64_t* full = (uint64_t*)(sB + kGemmStages * B_BYTES);
-    uint64_t* empty = full + kGemmStages;
-    uint64_t* done = empty + kGemmStages;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    uint8_t* sB = smem + ST * C::A_BYTES;
+    uint64_t* full = (uint64_t*)(sB + ST * C::B_BYTES);
+    uint64_t* empty = full + ST;
+    uint64_t* acc_full = empty + ST;      // [2]
+    uint64_t* acc_empty = acc_full + 2;   // [2]
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    __shared__ float red[4];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         tc::prefetch_tmap(&tmA);
         tc::prefetch_tmap(&tmB);
-        for (int s = 0; s < kGemmStages; ++s) {
+        for (int s = 0; s < ST; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 4);
+        }
+        tc::mbar_init(drain, 1);
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == 1) tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    const int m0 = blockIdx.y * kGemmBM;
-    const int n0 = blockIdx.x * BN;
+    const int tiles_n = (N + BN - 1) / BN;
+    const int tiles = tiles_n * ((M + kGemmBM - 1) / kGemmBM);
     const int KT = K / kGemmBK;
     bool ok = true;
-    int issued = 0;     // stage loads issued by the producer
+    float sq = 0.0f;
 
-    if (warp == 0 && lane == 0) {
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % kGemmStages;
-            if (kt >= kGemmStages && !mbar_wait_clock(&empty[s], ((kt / kGemmStages) - 1) & 1)) {
-                ok = false;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;   // stage loads issued
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int m0 = (t / tiles_n) * kGemmBM, n0 = (t % tiles_n) * BN;
+                for (int kt = 0; kt < KT; ++kt, ++it) {
+                    const int s = it % ST;
+                    if (it >= ST && !mbar_wait_clock(&empty[s], ((it / ST) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&full[s], C::A_BYTES + C::B_BYTES);
+                    tc::tma_load_2d(sA + s * C::A_BYTES, &tmA, &full[s], kt * kGemmBK, m0);
+                    tc::tma_load_2d(sB + s * C::B_BYTES, &tmB, &full[s], kt * kGemmBK, n0);
+                }
             }
-            tc::mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-            tc::tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kt * kGemmBK, m0);
-            tc::tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kt * kGemmBK, n0);
-            ++issued;
+            if (!ok) {
+                // let the loads still in flight (the last min(it, ST)) land
+                for (int j = it > ST ? it - ST : 0; j < it; ++j) mbar_wait_clock(&full[j % ST], (j / ST) & 1);
+            }
         }
-    } else if (warp == 1 && lane == 0) {
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(kGemmBM, BN);
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % kGemmStages;
-            if (!mbar_wait_clock(&full[s], (kt / kGemmStages) & 1)) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kGemmBM, BN);
+            int it = 0, j = 0;
+            bool issued = false;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++j) {
+                const int buf = j & 1;
+                if (j >= 2 && !mbar_wait_clock(&acc_empty[buf], ((j >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t acc = tmem + (uint32_t)(buf * BN);
+                for (int kt = 0; kt < KT; ++kt, ++it) {
+                    const int s = it % ST;
+                    if (!mbar_wait_clock(&full[s], (it / ST) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a0 = tc::smem_u32(sA + s * C::A_BYTES);
+                    const uint32_t b0 = tc::smem_u32(sB + s * C::B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < kGemmBK / 16; ++kk)
+                        tc::mma_bf16(acc, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
+                                     idesc, (kt | kk) != 0 ? 1u : 0u);
+                    issued = true;
+                    tc::mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&acc_full[buf]);
+            }
+            if (issued) {
+                // every MMA of this thread has completed once drain fires
+                tc::mma_commit(drain);
+                if (!mbar_wait_clock(drain, 0)) ok = false;
+            }
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lanes 32 (warp % 4) .. +31
+        const int q = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            const int buf = j & 1;
+            const bool have = __all_sync(0xffffffffu, mbar_wait_clock(&acc_full[buf], (j >> 1) & 1) ? 1 : 0) != 0;
+            if (!have) {
                 ok = false;
                 break;
             }
             tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_u32(sA + s * A_BYTES);
-            const uint32_t b0 = tc::smem_u32(sB + s * B_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < kGemmBK / 16; ++kk) {
-                tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a0 + kk * 32), tc::desc_kmajor_sw128(b0 + kk * 32),
-                             idesc, (kt | kk) != 0 ? 1u : 0u);
+            const int m0 = (t / tiles_n) * kGemmBM, n0 = (t % tiles_n) * BN;
+            const int row = m0 + q * 32 + lane;
+            const bool row_ok = row < M;
+            long long trow = row;
+            if constexpr (EPI == EPI_MSE) {
+                if (row_ok && ep.target_rows) trow = ep.target_rows[row];
             }
-            tc::mma_commit(&empty[s]);
+            const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tc::tmem_ld16(base + (uint32_t)c, v);
+                if (!row_ok || n0 + c >= N) continue;
+                const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
+                epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
-        tc::mma_commit(done);
-    }
-    __syncwarp();
-
-    const bool have = __all_sync(0xffffffffu, mbar_wait_clock(done, 0) ? 1 : 0) != 0;
-    tc::fence_after_sync();
-    if (!have || !ok) atomicExch(err, 1);
-    float sq = 0.0f;     // EPI_MSE: this thread's sum of squared residuals
-    if (have) {
-        const int row = m0 + warp * 32 + lane;
-        const bool row_ok = row < M;
-        long long trow = row;
         if constexpr (EPI == EPI_MSE) {
-            if (row_ok && ep.target_rows) trow = ep.target_rows[row];
-        }
-        for (int c = 0; c < BN; c += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            if (!row_ok || n0 + c >= N) continue;
-            const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
-            const int col0 = n0 + c;
-            if constexpr (EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC) {
-                float* o = ep.out_f32 + (long long)row * ep.ld_f32 + col0;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    if (i >= nv) break;
-                    const int col = col0 + i;
-                    float x = v[i];
-                    if constexpr (EPI == EPI_BIAS_F32) x += ep.bias[col];
-                    if constexpr (EPI == EPI_AFFINE) {
-                        if (ep.bias) x += ep.bias[col];
-                        x *= ep.colscale ? ep.colscale[col] : ep.scale;
-                        if (ep.shift) x += ep.shift[col];
-                    }
-                    if constexpr (EPI == EPI_SCALE_ACC) x = ep.accumulate ? fmaf(ep.scale, x, o[i]) : ep.scale * x;
-                    o[i] = x;
-                }
-            } else {
-                __nv_bfloat16 r[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = col0 + (i < nv ? i : 0);
-                    float x = v[i];
-                    if constexpr (EPI == EPI_BIAS_GELU) {
-                        const float z = x + ep.bias[col];
-                        if (ep.out_z && i < nv) ep.out_z[(long long)row * ep.ld_z + col] = z;
-                        x = gelu_f(z);
-                    } else if constexpr (EPI == EPI_GELU_BWD) {
-                        x *= gelu_grad_f(ep.aux[(long long)row * ep.ld_aux + col]);
-                    } else {   // EPI_MSE
-                        const float d = x + ep.bias[col] - ep.target[trow * ep.ld_target + col];
-                        if (i < nv) sq = fmaf(d, d, sq);
-                        x = ep.coef * d;
-                    }
-                    r[i] = __float2bfloat16_rn(x);
-                }
-                __nv_bfloat16* o = ep.out_bf16 + (long long)row * ep.ld_bf16 + col0;
-                if (nv == 16 && (((uintptr_t)o) & 15) == 0) {
-                    const uint4* src = reinterpret_cast<const uint4*>(r);
-                    reinterpret_cast<uint4*>(o)[0] = src[0];
-                    reinterpret_cast<uint4*>(o)[1] = src[1];
-                } else {
-                    for (int i = 0; i < nv; ++i) o[i] = r[i];
-                }
-                if (ep.out_bf16_t) {
-                    for (int i = 0; i < nv; ++i) ep.out_bf16_t[(long long)(col0 + i) * ep.ld_t + row] = r[i];
-                }
-            }
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) red[warp - 2] = sq;
         }
     }
-    if constexpr (EPI == EPI_MSE) {
-        // fixed-order CTA reduction of the squared residuals
-        __shared__ float red[4];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) red[warp] = sq;
-        __syncthreads();
-        if (threadIdx.x == 0)
-            ep.loss_partial[blockIdx.y * gridDim.x + blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
-    }
-    // on failure, let the loads that may still be in flight (the last
-    // min(issued, stages) ones) land before the CTA exits
-    if (threadIdx.x == 0 && !ok) {
-        const int first = issued > kGemmStages ? issued - kGemmStages : 0;
-        for (int j = first; j < issued; ++j) mbar_wait_clock(&full[j % kGemmStages], (j / kGemmStages) & 1);
-    }
+    if (!ok) atomicExch(err, 1);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+    if constexpr (EPI == EPI_MSE) {
+        // fixed-order reduction of the squared residuals of this CTA's tiles
+        if (threadIdx.x == 0) ep.loss_partial[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+    }
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, C::TMEM_COLS);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -245,15 +334,22 @@ int make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int
     return r == CUDA_SUCCESS ? SYNAX_OK : SYNAX_EINVAL;
 }
 
-template <int BN, int EPI>
-constexpr size_t gemm_smem() {
-    return 1024 + (size_t)kGemmStages * (kGemmBM + BN) * kGemmBK * 2 + 256;
+int sm_count() {
+    static int n = 0;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+    });
+    return n;
 }
 
 template <int BN, int EPI>
 cudaError_t set_smem_attr() {
     return cudaFuncSetAttribute(k_gemm_bf16<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)gemm_smem<BN, EPI>());
+                                (int)GemmCfg<BN>::SMEM);
 }
 
 template <int EPI>
@@ -267,8 +363,9 @@ cudaError_t set_smem_attrs() {
 template <int BN, int EPI>
 int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const GemmEpiParams& ep,
                   int* err, cudaStream_t st) {
-    dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM);
-    k_gemm_bf16<BN, EPI><<<grid, 128, gemm_smem<BN, EPI>(), st>>>(ma, mb, M, N, K, ep, err);
+    const int tiles = ((N + BN - 1) / BN) * ((M + kGemmBM - 1) / kGemmBM);
+    const int grid = tiles < sm_count() ? tiles : sm_count();
+    k_gemm_bf16<BN, EPI><<<grid, kGemmThreads, GemmCfg<BN>::SMEM, st>>>(ma, mb, M, N, K, ep, err);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
 }
@@ -311,7 +408,8 @@ int gemm_init() {
 
 int gemm_tiles(int M, int N) {
     const int bn = gemm_bn_for(N);
-    return ((N + bn - 1) / bn) * ((M + kGemmBM - 1) / kGemmBM);
+    const int tiles = ((N + bn - 1) / bn) * ((M + kGemmBM - 1) / kGemmBM);
+    return tiles < sm_count() ? tiles : sm_count();
 }
 
 // C = A[M][K] . B[N][K]^T with the given epilogue.  A, B: BF16 row-major with

@@ -14,7 +14,7 @@ enum GemmEpi : int {
     EPI_BIAS_GELU = 2,  // z = acc + bias -> out_z (f32, optional); gelu(z) -> out_bf16 (+ out_bf16_t)
     EPI_GELU_BWD = 3,   // d = acc * gelu'(aux) -> out_bf16 (+ out_bf16_t)
     EPI_MSE = 4,        // z = acc + bias; d = z - target[rows[m]][n]; coef * d -> out_bf16 (+ out_bf16_t);
-                        // sum of d^2 of the CTA -> loss_partial[tile]
+                        // sum of d^2 over the CTA's tiles -> loss_partial[CTA]
     EPI_AFFINE = 5,     // out_f32 = (acc + bias?) * (colscale ? colscale[n] : scale) + (shift ? shift[n] : 0)
     EPI_SCALE_ACC = 6,  // out_f32 = scale * acc + (accumulate ? out_f32 : 0)
 };
@@ -35,7 +35,7 @@ struct GemmEpiParams {
     int ld_target;
     const int* target_rows;      // EPI_MSE: row m reads target row target_rows[m]
     float coef;                  // EPI_MSE: gradient factor 2 / (rows * cols)
-    float* loss_partial;         // EPI_MSE: one float per CTA, index blockIdx.y * gridDim.x + blockIdx.x
+    float* loss_partial;         // EPI_MSE: one float per CTA (gemm_tiles of them)
     float scale;                 // EPI_AFFINE, EPI_SCALE_ACC
     const float* colscale;       // EPI_AFFINE
     const float* shift;          // EPI_AFFINE
@@ -46,7 +46,7 @@ struct GemmEpiParams {
 // calls it too).  Call before capturing a stream that will launch GEMMs.
 int gemm_init();
 
-// Number of CTAs (loss partials) of a GEMM with this M and N.
+// Number of CTAs of a GEMM with this M and N (one loss partial each).
 int gemm_tiles(int M, int N);
 
 // Enqueue C = A . B^T with epilogue `epi` on `st`.  A [M][lda], B [N][ldb]
