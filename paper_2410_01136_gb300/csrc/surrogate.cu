@@ -24,7 +24,7 @@
 //
 // Training.  One step = gather a batch (counter-based Feistel shuffle of the
 // stored samples per epoch), forward, MSE, backward, bias gradients, Adam
-// (cosine learning-rate schedule), loss bookkeeping -- 20 kernels for 4
+// (cosine learning-rate schedule), loss bookkeeping -- 21 kernels for 4
 // hidden layers, captured once into a CUDA graph and replayed; the step
 // counter lives in device memory so replays advance it.  Everything is
 // deterministic (no atomics in any sum), so a restored checkpoint replays
@@ -165,19 +165,25 @@ struct GatherArgs {
     const int* t_dev;
 };
 
+// One warp per batch row: lane 0 finds the source sample, the lanes write
+// the 64 normalised (zero-padded) inputs.
 __global__ void k_gather_input(GatherArgs a) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (b >= a.B) return;
     uint32_t src = (uint32_t)b;
     if (a.n) {
-        const uint32_t t = (uint32_t)*a.t_dev;
-        const uint32_t epoch = t / a.steps_per_epoch;
-        const uint32_t pos = (t % a.steps_per_epoch) * (uint32_t)a.B + (uint32_t)b;
-        src = feistel_perm(pos, a.n, a.half_bits, splitmix64_mix(a.seed + 0x632BE59BD9B4E019ull * (epoch + 1)));
+        if (lane == 0) {
+            const uint32_t t = (uint32_t)*a.t_dev;
+            const uint32_t epoch = t / a.steps_per_epoch;
+            const uint32_t pos = (t % a.steps_per_epoch) * (uint32_t)a.B + (uint32_t)b;
+            src = feistel_perm(pos, a.n, a.half_bits, splitmix64_mix(a.seed + 0x632BE59BD9B4E019ull * (epoch + 1)));
+        }
+        src = __shfl_sync(0xffffffffu, src, 0);
     }
-    if (a.rows_out) a.rows_out[b] = (int)src;
+    if (a.rows_out && lane == 0) a.rows_out[b] = (int)src;
     const float* th = a.theta + (long long)src * a.ld;
-    for (int j = 0; j < kInPad; ++j) {
+    for (int j = lane; j < kInPad; j += 32) {
         const float x = j < a.n_theta ? fmaf(th[j] - a.lo[j], a.inv2[j], -1.0f) : 0.0f;
         const bf16 v = __float2bfloat16_rn(x);
         a.X[(long long)b * kInPad + j] = v;
@@ -229,11 +235,15 @@ struct AdamHyper {
     int total_steps;
 };
 
-__device__ inline void adam_coeffs(const AdamHyper& h, int t1, float* lr, float* bc1, float* bc2) {
+// Step size and bias corrections of the coming step t + 1, computed once per
+// step (one thread) into coef[0..2] = (lr, 1 - beta1^(t+1), 1 - beta2^(t+1)).
+__global__ void k_adam_prep(AdamHyper h, const int* t_dev, float* coef) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int t1 = *t_dev + 1;
     const double s = (double)min(t1 - 1, h.total_steps) / (double)max(h.total_steps, 1);
-    *lr = (float)(h.lr_min + 0.5 * ((double)h.lr0 - h.lr_min) * (1.0 + cos(3.14159265358979323846 * s)));
-    *bc1 = (float)(1.0 - pow((double)h.beta1, (double)t1));
-    *bc2 = (float)(1.0 - pow((double)h.beta2, (double)t1));
+    coef[0] = (float)(h.lr_min + 0.5 * ((double)h.lr0 - h.lr_min) * (1.0 + cos(3.14159265358979323846 * s)));
+    coef[1] = (float)(1.0 - pow((double)h.beta1, (double)t1));
+    coef[2] = (float)(1.0 - pow((double)h.beta2, (double)t1));
 }
 
 __device__ inline float adam_update(float w, float g, float& m, float& v, const AdamHyper& h, float lr, float bc1,
@@ -247,8 +257,8 @@ __device__ inline float adam_update(float w, float g, float& m, float& v, const 
 // tiles so that the transposed copy is written coalesced.
 __global__ void __launch_bounds__(256)
 k_adam_weights(LayerTable T, float* __restrict__ W, const float* __restrict__ G, float* __restrict__ Mw,
-               float* __restrict__ Vw, bf16* __restrict__ Wb, bf16* __restrict__ Wt, AdamHyper h, const int* t_dev,
-               int update) {
+               float* __restrict__ Vw, bf16* __restrict__ Wb, bf16* __restrict__ Wt, AdamHyper h,
+               const float* __restrict__ coef, int update) {
     __shared__ bf16 tile[32][34];
     int l = 0;
     while (l + 1 < T.L && (int)blockIdx.x >= T.tile_begin[l + 1]) ++l;
@@ -257,7 +267,11 @@ k_adam_weights(LayerTable T, float* __restrict__ W, const float* __restrict__ G,
     const int tiles_c = (cols + 31) / 32;
     const int tr = local / tiles_c, tc = local % tiles_c;
     float lr = 0.f, bc1 = 1.f, bc2 = 1.f;
-    if (update) adam_coeffs(h, *t_dev + 1, &lr, &bc1, &bc2);
+    if (update) {
+        lr = coef[0];
+        bc1 = coef[1];
+        bc2 = coef[2];
+    }
     const long long off = T.woff[l];
     for (int k = 0; k < 4; ++k) {
         const int r = tr * 32 + threadIdx.y + 8 * k, c = tc * 32 + threadIdx.x;
@@ -284,11 +298,10 @@ k_adam_weights(LayerTable T, float* __restrict__ W, const float* __restrict__ G,
 }
 
 __global__ void k_adam_bias(float* __restrict__ b, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int n, AdamHyper h, const int* t_dev) {
+                            float* __restrict__ v, int n, AdamHyper h, const float* __restrict__ coef) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float lr, bc1, bc2;
-    adam_coeffs(h, *t_dev + 1, &lr, &bc1, &bc2);
+    const float lr = coef[0], bc1 = coef[1], bc2 = coef[2];
     float mi = m[i], vi = v[i];
     b[i] = adam_update(b[i], g[i], mi, vi, h, lr, bc1, bc2);
     m[i] = mi;
@@ -298,9 +311,12 @@ __global__ void k_adam_bias(float* __restrict__ b, const float* __restrict__ g, 
 // loss = sum of the CTA partials (fixed order) / count; advance the step.
 __global__ void k_finalize(const float* __restrict__ part, int n_part, float inv_count, float* __restrict__ hist,
                            int* t_dev, int update, float* loss_out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     double s = 0.0;
-    for (int i = 0; i < n_part; ++i) s += part[i];
+    for (int i = threadIdx.x; i < n_part; i += 32) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x != 0) return;
     const float loss = (float)(s * inv_count);
     const int t = *t_dev;
     hist[t & (kLossHist - 1)] = loss;
@@ -420,6 +436,7 @@ struct synax_surrogate_s {
     int n_part = 0;
     float* loss_hist = nullptr;
     int* t_dev = nullptr;
+    float* adam_coef = nullptr;   // (lr, bias corrections) of the coming step
     int* err = nullptr;
     // evaluation activations
     bf16* eX[kMaxLayers] = {nullptr};
@@ -447,7 +464,7 @@ namespace {
 
 void free_all(synax_surrogate_t* s) {
     void* ptrs[] = {s->W, s->dW, s->mW, s->vW, s->b, s->db, s->mb, s->vb, s->Wb, s->Wt, s->lo, s->inv2, s->mean,
-                    s->rows_dev, s->ybuf, s->loss_part, s->loss_hist, s->t_dev, s->err, s->eD0, s->eD1,
+                    s->rows_dev, s->ybuf, s->loss_part, s->loss_hist, s->t_dev, s->adam_coef, s->err, s->eD0, s->eD1,
                     s->sign_dev, s->basis_rows_dev, s->S, s->maps, s->mhi, s->mlo, s->ctrue, s->ds_theta, s->ds_y};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -491,7 +508,7 @@ AdamHyper hyper(const synax_surrogate_t* s) {
 int refresh_copies(synax_surrogate_t* s, cudaStream_t st, int update) {
     const LayerTable T = layer_table(s, true);
     k_adam_weights<<<T.tile_begin[s->L], dim3(32, 8), 0, st>>>(T, s->W, s->dW, s->mW, s->vW, s->Wb, s->Wt,
-                                                               hyper(s), s->t_dev, update);
+                                                               hyper(s), s->adam_coef, update);
     return launch_status();
 }
 
@@ -554,8 +571,10 @@ int enqueue_train_pass(synax_surrogate_t* s, const float* target, cudaStream_t s
 }
 
 int enqueue_update(synax_surrogate_t* s, cudaStream_t st) {
+    k_adam_prep<<<1, 32, 0, st>>>(hyper(s), s->t_dev, s->adam_coef);
+    SX_TRY(launch_status());
     SX_TRY(refresh_copies(s, st, 1));
-    k_adam_bias<<<(s->n_b + 255) / 256, 256, 0, st>>>(s->b, s->db, s->mb, s->vb, s->n_b, hyper(s), s->t_dev);
+    k_adam_bias<<<(s->n_b + 255) / 256, 256, 0, st>>>(s->b, s->db, s->mb, s->vb, s->n_b, hyper(s), s->adam_coef);
     return launch_status();
 }
 
@@ -717,7 +736,7 @@ int synax_surrogate_create(const synax_surrogate_cfg* cfg, synax_surrogate_t** o
     SX_ALLOC(s->rows_dev, B) SX_ALLOC(s->ybuf, (long long)B * s->n_out)
     s->n_part = gemm_tiles(B, s->n_out);
     SX_ALLOC(s->loss_part, s->n_part) SX_ALLOC(s->loss_hist, kLossHist)
-    SX_ALLOC(s->t_dev, 1) SX_ALLOC(s->err, 1)
+    SX_ALLOC(s->t_dev, 1) SX_ALLOC(s->adam_coef, 4) SX_ALLOC(s->err, 1)
     SX_ALLOC(s->sign_dev, npix) SX_ALLOC(s->basis_rows_dev, c.n_basis)
     SX_ALLOC(s->S, (long long)c.n_basis * npix)
     SX_ALLOC(s->maps, (long long)s->chunk * 3 * npix)
@@ -850,7 +869,7 @@ int synax_surrogate_step(synax_surrogate_t* s, const float* theta_dev, const flo
     if (!s || !theta_dev || !coeff_dev || n != s->B || (update != 0 && update != 1)) return SYNAX_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     GatherArgs a = gather_identity(s, theta_dev, s->B, s->X[0], s->Xt[0], s->rows_dev);
-    k_gather_input<<<(s->B + 127) / 128, 128, 0, st>>>(a);
+    k_gather_input<<<(s->B + 3) / 4, 128, 0, st>>>(a);
     SX_TRY(launch_status());
     k_normalize<<<grid_for((long long)s->B * s->n_out), 256, 0, st>>>(coeff_dev, s->B, s->n_out, s->mean,
                                                                       1.0f / s->scale, s->ybuf);
@@ -971,7 +990,7 @@ int synax_surrogate_train(synax_surrogate_t* s, int n_steps, uint64_t seed, void
         cudaStream_t cs = s->cap;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return record_cuda_error((int)e);
-        k_gather_input<<<(s->B + 127) / 128, 128, 0, cs>>>(a);
+        k_gather_input<<<(s->B + 3) / 4, 128, 0, cs>>>(a);
         int rc = launch_status();
         if (rc == SYNAX_OK) rc = enqueue_train_pass(s, s->ds_y, cs);
         if (rc == SYNAX_OK) rc = enqueue_update(s, cs);
@@ -1013,7 +1032,7 @@ int synax_surrogate(synax_surrogate_t* s, const float* theta_dev, int n, float* 
     for (int r0 = 0; r0 < n; r0 += s->E) {
         const int m = n - r0 < s->E ? n - r0 : s->E;
         GatherArgs a = gather_identity(s, theta_dev + (long long)r0 * nt, m, s->eX[0], nullptr, nullptr);
-        k_gather_input<<<(m + 127) / 128, 128, 0, st>>>(a);
+        k_gather_input<<<(m + 3) / 4, 128, 0, st>>>(a);
         SX_TRY(launch_status());
         for (int l = 0; l < L; ++l) {
             GemmEpiParams ep{};

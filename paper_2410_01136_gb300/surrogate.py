@@ -34,7 +34,7 @@ class Surrogate:
     init: the initial flat parameters or a list of (W, b) (inputs.mlp_init)."""
 
     def __init__(self, n_theta, theta_lo, theta_hi, basis_sign, basis_rows, *, width=1024, depth=4, nside=64,
-                 batch=512, max_eval=4096, map_chunk=128, total_steps=10000, lr=1e-3, lr_min=1e-5,
+                 batch=512, max_eval=16384, map_chunk=128, total_steps=10000, lr=1e-3, lr_min=1e-5,
                  beta1=0.9, beta2=0.999, eps=1e-8, init=None):
         import torch
         self._torch = torch
