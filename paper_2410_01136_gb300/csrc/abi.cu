@@ -230,6 +230,9 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         M.m[mc::J_H2] = R(th[15]);
         M.m[mc::J_N0OBS] = R(th[12]);
         M.m[mc::J_SIN2X] = R(1.0 / (std::sin(th[11]) * std::sin(th[11])));
+        M.m[mc::J_BH_IZH2] = R(th[8] / (th[9] * th[9]));
+        M.m[mc::J_IH1_SQ] = R(1.0 / (th[14] * th[14]));
+        M.m[mc::J_IH2_SQ] = R(1.0 / (th[15] * th[15]));
         break;
     default: break;
     }

@@ -18,17 +18,27 @@ template <int MODEL> struct Grad;
 template <> struct Grad<SYNAX_MODEL_JF12> {
     static constexpr int NT = 16;
     static constexpr int P_INDEX = 13;
+    static constexpr int N_ARM_SLOTS = 8;
+    // garm: this thread's column of the arm-strength slots in shared memory
+    // (slot k at garm[k * stride]); the two arms blended at a point get
+    // their shares there instead of through 8 selects per sample.
     template <typename R>
     static __device__ __forceinline__ void accum(const R* m, const FieldLocal<R>& L, R bxb, R byb, R bzb,
-                                                 R n0b, R neb, R* g) {
-        const R brb = bxb * L.c + byb * L.s;    // adjoint of the cylindrical components
-        const R bpb = -bxb * L.s + byb * L.c;
+                                                 R n0b, R neb, R* g, R* garm, int stride) {
+        R brb, bpb;                             // adjoint of the cylindrical components
+        if constexpr (sizeof(R) == 4) {
+            const float2 v = fma2(dup2(bxb), make_float2(L.c, -L.s), mul2(dup2(byb), make_float2(L.s, L.c)));
+            brb = v.x;
+            bpb = v.y;
+        } else {
+            brb = bxb * L.c + byb * L.s;
+            bpb = -bxb * L.s + byb * L.c;
+        }
         const R beta_b = L.disc_unit * (brb * R(kPitchSin) + bpb * R(kPitchCos));
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-            g[kk] += beta_b * ((kk == L.ka ? L.wa : R(0)) + (kk == L.kb ? L.wb : R(0)));
+        garm[L.ka * stride] += beta_b * L.wa;
+        garm[L.kb * stride] += beta_b * L.wb;
         g[8] += bpb * L.halo_unit;
-        g[9] += bpb * m[mc::J_BH] * L.halo_unit * L.az * m[mc::J_IZH] * m[mc::J_IZH];
+        g[9] += bpb * m[mc::J_BH_IZH2] * L.halo_unit * L.az;
         if (L.rp > R(0)) {
             const R proj = brb * L.sz * m[mc::J_COSX] + bzb * m[mc::J_SINX];
             g[10] += L.xmag_unit * proj;
@@ -38,8 +48,8 @@ template <> struct Grad<SYNAX_MODEL_JF12> {
                      m[mc::J_BX] * L.xmag_unit * (-brb * L.sz * m[mc::J_SINX] + bzb * m[mc::J_COSX]);
         }
         g[12] += n0b * L.n0_unit;
-        g[14] += neb * L.ne1 * L.az * m[mc::J_IH1] * m[mc::J_IH1];
-        g[15] += neb * L.ne2 * L.az * m[mc::J_IH2] * m[mc::J_IH2];
+        g[14] += neb * L.ne1 * L.az * m[mc::J_IH1_SQ];
+        g[15] += neb * L.ne2 * L.az * m[mc::J_IH2_SQ];
     }
 };
 
@@ -47,9 +57,10 @@ template <> struct Grad<SYNAX_MODEL_JF12> {
 template <> struct Grad<SYNAX_MODEL_WMAP> {
     static constexpr int NT = 8;
     static constexpr int P_INDEX = 6;
+    static constexpr int N_ARM_SLOTS = 1;
     template <typename R>
     static __device__ __forceinline__ void accum(const R* m, const FieldLocal<R>& L, R bxb, R byb, R bzb,
-                                                 R n0b, R neb, R* g) {
+                                                 R n0b, R neb, R* g, R* /*garm*/, int /*stride*/) {
         const R brb = bxb * L.c + byb * L.s;
         const R bpb = -bxb * L.s + byb * L.c;
         g[0] += L.env * (brb * L.cpsi * L.cchi + bpb * L.spsi * L.cchi + bzb * L.schi);
@@ -72,6 +83,7 @@ struct AdjSmem {
     R arms[8];
     R stage[3 * NF][kAdjThreads / LPR];
     double part[kAdjThreads / 32][Grad<MODEL>::NT + 1];
+    R garm[Grad<MODEL>::N_ARM_SLOTS][kAdjThreads];   // per-thread arm-strength gradient slots
 };
 
 // One CTA's share of the adjoint: rays [ray0, ray0 + 256/LPR) of map P.
@@ -188,8 +200,12 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
         R after = seg_exclusive_suffix<LPR, R>(D, sub);
 
         // ---- pass 2: reverse march of the lane's chunk ----
+        constexpr int NSLOT = Grad<MODEL>::N_ARM_SLOTS;
+        R* garm = &sm.garm[0][threadIdx.x];
+#pragma unroll
+        for (int kk = 0; kk < NSLOT; ++kk) garm[kk * kAdjThreads] = R(0);
         if (n0 < n1) {
-            PT Rloc = S;
+            PT Q = Ph::add(O, S);                       // O + sum of f before sample n (after the update)
             ArmTracker<R> trk;
             if constexpr (MODEL == SYNAX_MODEL_JF12) trk.init(P, nd, n1 - 1, dr, dr_lo);
             const R q = P.q;
@@ -221,22 +237,60 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 const R ps = nw * (R(2) * ba * bb);
                 const R f = -ne * bn;
 
-                Rloc = Ph::add(Rloc, -f);                    // sum of f before sample n
-                const PT s_n = Ph::add(Ph::add(O, Rloc), P.w_own * f);
+                // Q <- Q - f (the RM before sample n) and s_n = that + w f,
+                // formed from the same Q as Q + (w - 1) f (exact factor)
+                PT s_n;
+                if constexpr (sizeof(R) == 4) {
+                    ff_add_f_pair(Q, make_float2((P.w_own - 1.0f) * f, -f), s_n, Q);
+                } else {
+                    s_n = Ph::add(Q, (P.w_own - R(1)) * f);
+                    Q = Ph::add(Q, -f);
+                }
                 R Or = R(0), Oi = R(0), Opr = R(0), Opi = R(0), Odr = R(0), Odi = R(0);
+                if constexpr (sizeof(R) == 4 && NF >= 2) {
+                    // frequencies in pairs; the pair sums are folded at the end
+                    float2 or2 = dup2(0.f), oi2 = dup2(0.f), opr2 = dup2(0.f), opi2 = dup2(0.f);
+                    float2 odr2 = dup2(0.f), odi2 = dup2(0.f);
 #pragma unroll
-                for (int k = 0; k < NF; ++k) {
-                    if (k < P.n_freq) {
-                        R sn, cs;
-                        F::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
-                        const R ur = hr[k] * cs - hi[k] * sn;   // h_f e^{i phi_f}
-                        const R ui = hr[k] * sn + hi[k] * cs;
-                        Or += ur;
-                        Oi += ui;
-                        Opr += A.dlnaP_dp[k] * ur;
-                        Opi += A.dlnaP_dp[k] * ui;
-                        Odr += c2[k] * ur;
-                        Odi += c2[k] * ui;
+                    for (int k = 0; k < NF; k += 2) {
+                        if (k < P.n_freq) {
+                            float2 sn, cs;
+                            sincos_rev_pair(cd[k], cd[k + 1], s_n, sn, cs);
+                            const float2 h_r = make_float2(hr[k], hr[k + 1]);
+                            const float2 h_i = make_float2(hi[k], hi[k + 1]);
+                            const float2 ur = fma2(h_r, cs, neg2(mul2(h_i, sn)));   // h_f e^{i phi_f}
+                            const float2 ui = fma2(h_r, sn, mul2(h_i, cs));
+                            const float2 dp = make_float2(A.dlnaP_dp[k], A.dlnaP_dp[k + 1]);
+                            const float2 cc = make_float2(c2[k], c2[k + 1]);
+                            or2 = add2(or2, ur);
+                            oi2 = add2(oi2, ui);
+                            opr2 = fma2(dp, ur, opr2);
+                            opi2 = fma2(dp, ui, opi2);
+                            odr2 = fma2(cc, ur, odr2);
+                            odi2 = fma2(cc, ui, odi2);
+                        }
+                    }
+                    Or = or2.x + or2.y;
+                    Oi = oi2.x + oi2.y;
+                    Opr = opr2.x + opr2.y;
+                    Opi = opi2.x + opi2.y;
+                    Odr = odr2.x + odr2.y;
+                    Odi = odi2.x + odi2.y;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) {
+                        if (k < P.n_freq) {
+                            R sn, cs;
+                            F::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
+                            const R ur = hr[k] * cs - hi[k] * sn;   // h_f e^{i phi_f}
+                            const R ui = hr[k] * sn + hi[k] * cs;
+                            Or += ur;
+                            Oi += ui;
+                            Opr += A.dlnaP_dp[k] * ur;
+                            Opi += A.dlnaP_dp[k] * ui;
+                            Odr += c2[k] * ur;
+                            Odi += c2[k] * ui;
+                        }
                     }
                 }
                 const R d = -(Odr * ps + Odi * pc);            // dL/dS_n = -Im(Omega' E)
@@ -261,12 +315,25 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 (void)jI;
                 const R bnb = -ne * fbar;                        // d f / d(B.n) = -n_e
                 const R neb = -bn * fbar;                        // d f / d n_e = -B.n
-                const R bxb = abar * L.el[0] + bbar * L.eb[0] + bnb * L.n[0];
-                const R byb = abar * L.el[1] + bbar * L.eb[1] + bnb * L.n[1];
+                R bxb, byb;
+                if constexpr (sizeof(R) == 4) {
+                    float2 v = mul2(dup2(abar), make_float2(L.el[0], L.el[1]));
+                    v = fma2(dup2(bbar), make_float2(L.eb[0], L.eb[1]), v);
+                    v = fma2(dup2(bnb), make_float2(L.n[0], L.n[1]), v);
+                    bxb = v.x;
+                    byb = v.y;
+                } else {
+                    bxb = abar * L.el[0] + bbar * L.eb[0] + bnb * L.n[0];
+                    byb = abar * L.el[1] + bbar * L.eb[1] + bnb * L.n[1];
+                }
                 const R bzb = bbar * L.eb[2] + bnb * L.n[2];
                 g[Grad<MODEL>::P_INDEX] += pbar;
-                Grad<MODEL>::accum(P.m, loc, bxb, byb, bzb, n0bar, neb, g);
+                Grad<MODEL>::accum(P.m, loc, bxb, byb, bzb, n0bar, neb, g, garm, kAdjThreads);
             }
+        }
+        if constexpr (NSLOT > 1) {
+#pragma unroll
+            for (int kk = 0; kk < NSLOT; ++kk) g[kk] += garm[kk * kAdjThreads];
         }
         // all lanes hold partial gradients of their ray: one full-warp sum
         // gives the warp's share of the CTA partial

@@ -193,6 +193,46 @@ template <> struct PhaseOps<float> {
     static __device__ __forceinline__ float to_real(T v) { return v.hi + v.lo; }
 };
 
+// Paired FP32 arithmetic: sm_100 and later execute two FP32 operations of
+// one thread per instruction (IEEE round-to-nearest per element, as the
+// scalar instructions).  Independent per-frequency work is issued in pairs.
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// Two double-float sums of one double-float a with floats b.x, b.y
+// (ff_add_f twice: TwoSum, then FastTwoSum with a.lo), element by element.
+__device__ __forceinline__ void ff_add_f_pair(const ff& a, float2 b, ff& rx, ff& ry) {
+    const float2 ah = dup2(a.hi);
+    const float2 s = add2(ah, b);
+    const float2 bb = sub2(s, ah);
+    const float2 e = add2(sub2(ah, sub2(s, bb)), sub2(b, bb));
+    const float2 lo = add2(e, dup2(a.lo));
+    const float2 hi = add2(s, lo);
+    const float2 lo2 = sub2(lo, sub2(hi, s));
+    rx = ff{hi.x, lo2.x};
+    ry = ff{hi.y, lo2.y};
+}
+
+// sin and cos of 2 pi frac(c_a s) and 2 pi frac(c_b s) for two frequencies:
+// PhaseOps<float>::frac_mul and sincos_rev, element by element.
+__device__ __forceinline__ void sincos_rev_pair(const ff& ca, const ff& cb, const ff& s, float2& sn, float2& cs) {
+    const float2 ch = make_float2(ca.hi, cb.hi), cl = make_float2(ca.lo, cb.lo);
+    const float2 sh = dup2(s.hi);
+    const float2 p = mul2(ch, sh);
+    float2 e = fma2(ch, sh, neg2(p));
+    e = fma2(ch, dup2(s.lo), e);
+    e = fma2(cl, sh, e);
+    const float2 k = make_float2(rintf(p.x), rintf(p.y));
+    const float2 r = add2(add2(p, neg2(k)), e);
+    const float2 a = mul2(r, dup2(6.2831853071795865f));
+    sn = make_float2(sin_approx(a.x), sin_approx(a.y));
+    cs = make_float2(cos_approx(a.x), cos_approx(a.y));
+}
+
 template <> struct PhaseOps<double> {
     using T = double;
     static __device__ __forceinline__ T zero() { return 0.0; }
@@ -738,6 +778,9 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
     accI = R(0);
 #pragma unroll
     for (int k = 0; k < NF; ++k) { zr[k] = R(0); zi[k] = R(0); }
+    float2 zr2[NF / 2 > 0 ? NF / 2 : 1], zi2[NF / 2 > 0 ? NF / 2 : 1];
+#pragma unroll
+    for (int k = 0; k < (NF / 2 > 0 ? NF / 2 : 1); ++k) { zr2[k] = dup2(0.0f); zi2[k] = dup2(0.0f); }
     S = Ph::zero();
     ArmTracker<R> trk;
     if constexpr (MODEL == SYNAX_MODEL_JF12) {
@@ -759,16 +802,46 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
         Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
         const Emit<R> e = emit<R>(B, N0, ne, L, P.q);
         accI += e.jI;
-        const PT s_n = Ph::add(S, P.w_own * e.f);      // RM at the midpoint (Eq. 7)
-        S = Ph::add(S, e.f);
+        PT s_n;                                        // RM at the midpoint (Eq. 7)
+        if constexpr (sizeof(R) == 4) {
+            ff_add_f_pair(S, make_float2(P.w_own * e.f, e.f), s_n, S);
+        } else {
+            s_n = Ph::add(S, P.w_own * e.f);
+            S = Ph::add(S, e.f);
+        }
+        if constexpr (sizeof(R) == 4 && NF >= 2) {
+            // frequencies in pairs: (pc + i ps) e^{i phi} for two at once
+            const float2 pc = dup2(e.pc), ps = dup2(e.ps);
 #pragma unroll
-        for (int k = 0; k < NF; ++k) {
-            if (k < P.n_freq) {
-                R sn, cs;
-                M<R>::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
-                zr[k] += e.pc * cs - e.ps * sn;         // (pc + i ps) e^{i phi}
-                zi[k] += e.pc * sn + e.ps * cs;
+            for (int k = 0; k < NF; k += 2) {
+                if (k < P.n_freq) {
+                    float2 sn, cs;
+                    sincos_rev_pair(cd[k], cd[k + 1], s_n, sn, cs);
+                    const float2 r = fma2(pc, cs, neg2(mul2(ps, sn)));
+                    const float2 i = fma2(pc, sn, mul2(ps, cs));
+                    zr2[k >> 1] = add2(zr2[k >> 1], r);
+                    zi2[k >> 1] = add2(zi2[k >> 1], i);
+                }
             }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                if (k < P.n_freq) {
+                    R sn, cs;
+                    M<R>::sincos_rev(Ph::frac_mul(cd[k], s_n), &sn, &cs);
+                    zr[k] += e.pc * cs - e.ps * sn;         // (pc + i ps) e^{i phi}
+                    zi[k] += e.pc * sn + e.ps * cs;
+                }
+            }
+        }
+    }
+    if constexpr (sizeof(R) == 4 && NF >= 2) {
+#pragma unroll
+        for (int k = 0; k < NF; k += 2) {
+            zr[k] = zr2[k >> 1].x;
+            zr[k + 1] = zr2[k >> 1].y;
+            zi[k] = zi2[k >> 1].x;
+            zi[k + 1] = zi2[k >> 1].y;
         }
     }
 }

@@ -37,7 +37,8 @@ constexpr int W_B0 = 0, W_PSI0 = 1, W_PSI1 = 2, W_CHI0 = 3, W_BUX = 4, W_N0U = 5
 constexpr int J_B = 0;              // b_1..b_8 at 0..7
 constexpr int J_BH = 8, J_IZH = 9, J_BX = 10, J_COSX = 11, J_SINX = 12, J_COTX = 13,
               J_N0N = 14, J_IH1 = 15, J_IH2 = 16, J_ZH = 17, J_THX = 18, J_H1 = 19, J_H2 = 20,
-              J_N0OBS = 21, J_SIN2X = 22, J_N0U = 23, J_IZH_LO = 24, J_IH1_LO = 25, J_IH2_LO = 26;
+              J_N0OBS = 21, J_SIN2X = 22, J_N0U = 23, J_IZH_LO = 24, J_IH1_LO = 25, J_IH2_LO = 26,
+              J_BH_IZH2 = 27, J_IH1_SQ = 28, J_IH2_SQ = 29;   // B_h / z_h^2, 1 / h1^2, 1 / h2^2 (gradients)
 }  // namespace mc
 
 template <typename R>
