@@ -174,9 +174,9 @@ int synax_gemm_bf16(const void* a_dev, int lda, const void* b_dev, int ldb, int 
  * runtime and has no device allocator of its own, or code that must not
  * allocate, and so synchronise the device, inside its sampling loop).
  * Arguments and results are those of synax_adjoint; the scratch partials live
- * in a 4 MiB array compiled into the library, held on every GPU that loads
+ * in an 8 MiB array compiled into the library, held on every GPU that loads
  * it until the process exits, so the call allocates nothing.  Problems whose
- * workspace (synax_adjoint_workspace_bytes) exceeds 4 MiB are rejected with
+ * workspace (synax_adjoint_workspace_bytes) exceeds 8 MiB are rejected with
  * SYNAX_ESPACE before anything is enqueued: up to 246,720 pixels (Nside 128)
  * for the 16-parameter JF12-type model, 466,032 for the 8-parameter
  * WMAP-type model.  The first call on a device looks up the array's device

@@ -20,7 +20,7 @@
 //   fbar_n = sum_{m > n} dL/dS_m + w dL/dS_n, accumulated as the march goes
 //   backwards.  Emission adjoints (with respect to B.e_l, B.e_b, N0, p) and
 //   fbar are pushed through the field model's derivatives into dL/dtheta.
-// Reduction: warp butterfly, then the 8 warps of a CTA in fixed order into a
+// Reduction: warp butterfly, then the 4 warps of a CTA in fixed order into a
 // per-CTA partial (double), then a second kernel sums the partials in fixed
 // order, so the gradient is bitwise reproducible.
 #include <cuda_runtime.h>

@@ -10,7 +10,10 @@
 namespace synax {
 
 
-constexpr int kAdjThreads = 256;
+// 128 threads with at most 102 registers each, so that 5 CTAs (20 warps)
+// share an SM: measured 5 % faster than 256 threads at 2 CTAs per SM.
+constexpr int kAdjThreads = 128;
+constexpr int kAdjMinBlocks = 5;
 
 template <int MODEL> struct Grad;
 
@@ -224,17 +227,25 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 FieldLocal<R> loc;
                 Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
 
-                const R bn = B[0] * L.n[0] + B[1] * L.n[1] + B[2] * L.n[2];
+                R bn, bb;
+                dot_n_eb<R>(B, L, bn, bb);
                 const R ba = B[0] * L.el[0] + B[1] * L.el[1];
-                const R bb = B[0] * L.eb[0] + B[1] * L.eb[1] + B[2] * L.eb[2];
                 const R bp2 = ba * ba + bb * bb;
                 const bool lit = bp2 > R(1e-30);
                 const R lg = lit ? F::log2_fast(bp2) : R(0);
                 const R w = lit ? F::exp2_fast(q * lg) : R(0);
                 const R nw = N0 * w;
                 const R jI = nw * bp2;
-                const R pc = nw * (ba * ba - bb * bb);
-                const R ps = nw * (R(2) * ba * bb);
+                R pc, ps;
+                if constexpr (sizeof(R) == 4) {
+                    const float2 v = mul2(dup2(nw), fma2(dup2(ba), make_float2(ba, 2.0f * bb),
+                                                         make_float2(-(bb * bb), 0.0f)));
+                    pc = v.x;
+                    ps = v.y;
+                } else {
+                    pc = nw * (ba * ba - bb * bb);
+                    ps = nw * (R(2) * ba * bb);
+                }
                 const R f = -ne * bn;
 
                 // Q <- Q - f (the RM before sample n) and s_n = that + w f,
@@ -370,7 +381,7 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, long long 
                                   int n_theta, double* __restrict__ grad, double* __restrict__ chi2);
 
 template <int MODEL, int NF, int LPR, typename R>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
 k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmaps,
           const R* __restrict__ target, R* __restrict__ maps_out, double* __restrict__ partial) {
     __shared__ AdjSmem<MODEL, NF, LPR, R> sm;

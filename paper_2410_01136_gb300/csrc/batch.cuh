@@ -34,10 +34,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Two CTAs per SM: without the bound the persistent loop's live state takes
-// more than 128 registers and only one CTA (8 warps) fits on an SM.
+// Four 128-thread CTAs per SM (at most 128 registers): without the bound the
+// persistent loop's live state takes more and fewer warps fit on an SM.
 template <int MODEL, int NF, int LPR>
-__global__ void __launch_bounds__(kAdjThreads, 2)
+__global__ void __launch_bounds__(kAdjThreads, 4)
 k_batch(const BatchSet* __restrict__ sets, const long long* __restrict__ order_begin,
         const int* __restrict__ order_set, int n_sets, long long n_tiles, unsigned long long* counter,
         double* __restrict__ partial, unsigned long long* set_done, unsigned long long* set_done_ns,

@@ -540,23 +540,20 @@ template <> struct ArmTracker<float> {
         const float b_new = b_a + dt * c;
         const float cross = h * lz;
         const float dot = rho2 + h * b;
-        float dphi;
         const float a = __fdividef(cross, dot);
-        if (dot > 0.0f && fabsf(a) < 0.1f) {
-            const float a2 = a * a;
-            dphi = a * (1.0f - a2 * (1.0f / 3.0f - a2 * (0.2f - a2 * (1.0f / 7.0f))));
-        } else {
-            dphi = atan2f(cross, dot);
-        }
         const float w = __fdividef(h * (2.0f * b + h * c), rho2);      // rho2_new / rho2 - 1
         const float sa = __fdividef(w, 2.0f + w);
-        float dln;
-        if (fabsf(sa) < 0.1f) {
-            const float s2 = sa * sa;
-            dln = sa * (1.0f + s2 * (1.0f / 3.0f + s2 * (0.2f + s2 * (1.0f / 7.0f))));
-        } else {
-            dln = 0.5f * log1pf(w);
-        }
+        // atan(a) and atanh(sa) by one series in t = (a^2, -sa^2):
+        // x (1 - t/3 + t^2/5 - t^3/7), evaluated for both at once
+        const float2 x2 = make_float2(a, sa);
+        const float2 t = mul2(x2, make_float2(a, -sa));
+        float2 poly = fma2(t, dup2(-1.0f / 7.0f), dup2(0.2f));
+        poly = fma2(t, poly, dup2(-1.0f / 3.0f));
+        poly = fma2(t, poly, dup2(1.0f));
+        const float2 ser = mul2(x2, poly);
+        float dphi = ser.x, dln = ser.y;
+        if (!(dot > 0.0f && fabsf(a) < 0.1f)) dphi = atan2f(cross, dot);
+        if (!(fabsf(sa) < 0.1f)) dln = 0.5f * log1pf(w);
         u = dd_add_f(u, 1.2732395447351628f * (dphi - 4.9151570310712050f * dln));
         rho2 = rho2_new;
         b = b_new;
@@ -710,14 +707,31 @@ template <> struct Model<SYNAX_MODEL_JF12> {
             br += mag * sz * m[mc::J_COSX];
             bz += mag * m[mc::J_SINX];
         }
-        B[0] = br * c - bp * s;
-        B[1] = br * s + bp * c;
+        R ne1, ne2;
+        if constexpr (sizeof(R) == 4) {
+            // (B_x, B_y) = br (c, s) + bp (-s, c); the two n_e exponents as a pair
+            const float2 v = fma2(dup2(bp), make_float2(-s, c), mul2(dup2(br), make_float2(c, s)));
+            B[0] = v.x;
+            B[1] = v.y;
+            const float2 r05 = make_float2((float)0.05, (float)0.25);
+            const float2 r05lo = make_float2((float)(0.05 - (double)(float)0.05), 0.0f);
+            const float2 arg_r = fma2(dup2(rho), r05, mul2(dup2(rho), r05lo));           // mulc
+            const float2 ih = make_float2(m[mc::J_IH1], m[mc::J_IH2]);
+            const float2 ihlo = make_float2(m[mc::J_IH1_LO], m[mc::J_IH2_LO]);
+            const float2 arg_z = fma2(dup2(az), ih, mul2(dup2(az), ihlo));               // mul_hl
+            const float2 a = add2(arg_r, arg_z);
+            ne1 = R(0.025) * F::exp(-a.x);
+            ne2 = R(0.10) * F::exp(-a.y);
+        } else {
+            B[0] = br * c - bp * s;
+            B[1] = br * s + bp * c;
+            ne1 = R(0.025) * F::exp(-(F::mulc(rho, 0.05) + F::mul_hl(az, m[mc::J_IH1], m[mc::J_IH1_LO])));
+            ne2 = R(0.10) * F::exp(-(F::mulc(rho, 0.25) + F::mul_hl(az, m[mc::J_IH2], m[mc::J_IH2_LO])));
+        }
         B[2] = bz;
 
         const R n0u = cr_density<R>(m[mc::J_N0U], rho, az);
         N0 = m[mc::J_N0OBS] * n0u;
-        const R ne1 = R(0.025) * F::exp(-(F::mulc(rho, 0.05) + F::mul_hl(az, m[mc::J_IH1], m[mc::J_IH1_LO])));
-        const R ne2 = R(0.10) * F::exp(-(F::mulc(rho, 0.25) + F::mul_hl(az, m[mc::J_IH2], m[mc::J_IH2_LO])));
         ne = ne1 + ne2;
         loc.c = c; loc.s = s; loc.az = az; loc.rho = rho; loc.ri = ri;
         loc.halo_unit = hu; loc.rp = rp; loc.xe = xe; loc.xmag_unit = xu; loc.sz = sz;
@@ -740,11 +754,26 @@ struct Emit {
     R jI, pc, ps, f;
 };
 
+// (B.n, B.e_b) as one pair of dot products (FP32), or plainly.
+template <typename R>
+__device__ __forceinline__ void dot_n_eb(const R B[3], const Los<R>& L, R& bn, R& bb) {
+    if constexpr (sizeof(R) == 4) {
+        float2 v = mul2(dup2(B[0]), make_float2(L.n[0], L.eb[0]));
+        v = fma2(dup2(B[1]), make_float2(L.n[1], L.eb[1]), v);
+        v = fma2(dup2(B[2]), make_float2(L.n[2], L.eb[2]), v);
+        bn = v.x;
+        bb = v.y;
+    } else {
+        bn = B[0] * L.n[0] + B[1] * L.n[1] + B[2] * L.n[2];
+        bb = B[0] * L.eb[0] + B[1] * L.eb[1] + B[2] * L.eb[2];
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ Emit<R> emit(const R B[3], R N0, R ne, const Los<R>& L, R q) {
-    const R bn = B[0] * L.n[0] + B[1] * L.n[1] + B[2] * L.n[2];
+    R bn, bb;
+    dot_n_eb<R>(B, L, bn, bb);
     const R bl = B[0] * L.el[0] + B[1] * L.el[1];
-    const R bb = B[0] * L.eb[0] + B[1] * L.eb[1] + B[2] * L.eb[2];
     const R bp2 = bl * bl + bb * bb;
     // B_perp below 1e-15 uG radiates nothing measurable; the cut also keeps
     // FP32 denormals away from the flush-to-zero logarithm.
@@ -752,8 +781,14 @@ __device__ __forceinline__ Emit<R> emit(const R B[3], R N0, R ne, const Los<R>& 
     const R nw = N0 * w;
     Emit<R> e;
     e.jI = nw * bp2;
-    e.pc = nw * (bl * bl - bb * bb);
-    e.ps = nw * (R(2) * bl * bb);
+    if constexpr (sizeof(R) == 4) {
+        const float2 v = mul2(dup2(nw), fma2(dup2(bl), make_float2(bl, 2.0f * bb), make_float2(-(bb * bb), 0.0f)));
+        e.pc = v.x;
+        e.ps = v.y;
+    } else {
+        e.pc = nw * (bl * bl - bb * bb);
+        e.ps = nw * (R(2) * bl * bb);
+    }
     e.f = -ne * bn;
     return e;
 }

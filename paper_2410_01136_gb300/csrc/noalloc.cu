@@ -10,7 +10,7 @@
 // from a fixed array compiled into the library instead.
 //
 // The array is a file-scope __device__ object of kNoAllocScratchBytes
-// (4 MiB).  Every GPU that loads the library holds it until the process
+// (8 MiB).  Every GPU that loads the library holds it until the process
 // exits.  Host code must not pass the symbol itself to a kernel (in host code
 // it is only a stand-in): the device address is obtained once per device
 // with cudaGetSymbolAddress, with that device current, on the first call
@@ -28,7 +28,7 @@
 
 namespace synax {
 
-constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
 constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];

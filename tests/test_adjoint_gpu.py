@@ -118,9 +118,13 @@ def test_chi2_jf12(torch, n_steps):
     assert float(chi2.item()) == pytest.approx(chi2_ora, rel=1e-5)
     ref, _ = fd_reference(prob, lambda m: oracle.chi2(m, target, sigma))
     assert_grad(g, ref, what=f"chi2 JF12 N={n_steps}")
-    # maps_out is the forward map (same arithmetic, separately compiled kernel)
+    # maps_out is the map: against the oracle at the stated tolerance, and
+    # against the forward kernel (the same arithmetic, compiled separately
+    # under another register budget, so FMA contraction may differ: I agrees
+    # to rounding; Q+iU, which cancels by up to ~100x at 408 MHz, to 1e-5)
+    assert_parity(maps.cpu().numpy(), ora_maps, what="adjoint maps_out vs oracle")
     fwd = forward(prob).cpu().numpy()
-    assert_parity(maps.cpu().numpy(), fwd, 1e-6, 1e-6, "adjoint maps_out vs forward")
+    assert_parity(maps.cpu().numpy(), fwd, 1e-6, 1e-5, "adjoint maps_out vs forward")
 
 
 @pytest.mark.slow
