@@ -212,11 +212,11 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
             ArmTracker<R> trk;
             if constexpr (MODEL == SYNAX_MODEL_JF12) trk.init(P, nd, n1 - 1, dr, dr_lo);
             const R q = P.q;
-            for (int n = n1 - 1; n >= n0; --n) {
+            R nh = R(n1 - 1) + R(0.5);                  // n + 1/2, exact
+            for (int n = n1 - 1; n >= n0; --n, nh -= R(1)) {
                 if constexpr (MODEL == SYNAX_MODEL_JF12) {
                     if (n < n1 - 1) trk.step(-1);
                 }
-                const R nh = R(n) + R(0.5);
                 const R t = fma(nh, dr, nh * dr_lo);
                 const R x = P.obs[0] + t * L.n[0];
                 const R y = P.obs[1] + t * L.n[1];
@@ -262,24 +262,23 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                     // frequencies in pairs; the pair sums are folded at the end
                     float2 or2 = dup2(0.f), oi2 = dup2(0.f), opr2 = dup2(0.f), opi2 = dup2(0.f);
                     float2 odr2 = dup2(0.f), odi2 = dup2(0.f);
+                    // all NF: beyond n_freq h, c2 and dlnaP_dp are 0, so they add 0
 #pragma unroll
                     for (int k = 0; k < NF; k += 2) {
-                        if (k < P.n_freq) {
-                            float2 sn, cs;
-                            sincos_rev_pair(cd[k], cd[k + 1], s_n, sn, cs);
-                            const float2 h_r = make_float2(hr[k], hr[k + 1]);
-                            const float2 h_i = make_float2(hi[k], hi[k + 1]);
-                            const float2 ur = fma2(h_r, cs, neg2(mul2(h_i, sn)));   // h_f e^{i phi_f}
-                            const float2 ui = fma2(h_r, sn, mul2(h_i, cs));
-                            const float2 dp = make_float2(A.dlnaP_dp[k], A.dlnaP_dp[k + 1]);
-                            const float2 cc = make_float2(c2[k], c2[k + 1]);
-                            or2 = add2(or2, ur);
-                            oi2 = add2(oi2, ui);
-                            opr2 = fma2(dp, ur, opr2);
-                            opi2 = fma2(dp, ui, opi2);
-                            odr2 = fma2(cc, ur, odr2);
-                            odi2 = fma2(cc, ui, odi2);
-                        }
+                        float2 sn, cs;
+                        sincos_rev_pair(cd[k], cd[k + 1], s_n, sn, cs);
+                        const float2 h_r = make_float2(hr[k], hr[k + 1]);
+                        const float2 h_i = make_float2(hi[k], hi[k + 1]);
+                        const float2 ur = fma2(h_r, cs, neg2(mul2(h_i, sn)));   // h_f e^{i phi_f}
+                        const float2 ui = fma2(h_r, sn, mul2(h_i, cs));
+                        const float2 dp = make_float2(A.dlnaP_dp[k], A.dlnaP_dp[k + 1]);
+                        const float2 cc = make_float2(c2[k], c2[k + 1]);
+                        or2 = add2(or2, ur);
+                        oi2 = add2(oi2, ui);
+                        opr2 = fma2(dp, ur, opr2);
+                        opi2 = fma2(dp, ui, opi2);
+                        odr2 = fma2(cc, ur, odr2);
+                        odi2 = fma2(cc, ui, odi2);
                     }
                     Or = or2.x + or2.y;
                     Oi = oi2.x + oi2.y;
@@ -310,22 +309,50 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
 
                 R abar = R(0), bbar = R(0), n0bar = R(0), pbar = R(0);
                 if (lit) {
-                    const R t1 = Or * ba - Oi * bb;             // Omega z
-                    const R t2 = Or * bb + Oi * ba;
-                    const R t3 = t1 * ba - t2 * bb;             // Re(Omega z^2)
-                    const R u1 = Opr * ba - Opi * bb;
-                    const R u2 = Opr * bb + Opi * ba;
-                    const R u3 = u1 * ba - u2 * bb;             // Re(Omega_p z^2)
-                    const R ibp2 = R(1) / bp2;
                     const R half_p1 = R(2) * q + R(2);          // (p + 1)/2
-                    abar = nw * (GI * half_p1 * ba + R(2) * t1 + R(2) * q * ba * t3 * ibp2);
-                    bbar = nw * (GI * half_p1 * bb - R(2) * t2 + R(2) * q * bb * t3 * ibp2);
+                    R t1, t2, t3, u3;
+                    if constexpr (sizeof(R) == 4) {
+                        // (t1, t2) = Omega z, (u1, u2) = Omega_p z, then
+                        // (t3, u3) = Re(Omega z^2), Re(Omega_p z^2)
+                        const float2 t12 = fma2(make_float2(Or, Or), make_float2(ba, bb),
+                                                mul2(make_float2(Oi, Oi), make_float2(-bb, ba)));
+                        const float2 u12 = fma2(make_float2(Opr, Opr), make_float2(ba, bb),
+                                                mul2(make_float2(Opi, Opi), make_float2(-bb, ba)));
+                        const float2 r3 = fma2(make_float2(t12.x, u12.x), dup2(ba),
+                                               mul2(make_float2(t12.y, u12.y), dup2(-bb)));
+                        t1 = t12.x;
+                        t2 = t12.y;
+                        t3 = r3.x;
+                        u3 = r3.y;
+                        const float k = GI * half_p1 + R(2) * q * t3 * F::rcp_nr(bp2);
+                        const float2 ab = mul2(dup2(nw), fma2(make_float2(ba, bb), dup2(k),
+                                                              make_float2(R(2) * t1, -R(2) * t2)));
+                        abar = ab.x;
+                        bbar = ab.y;
+                    } else {
+                        t1 = Or * ba - Oi * bb;                 // Omega z
+                        t2 = Or * bb + Oi * ba;
+                        t3 = t1 * ba - t2 * bb;                 // Re(Omega z^2)
+                        const R u1 = Opr * ba - Opi * bb;
+                        const R u2 = Opr * bb + Opi * ba;
+                        u3 = u1 * ba - u2 * bb;                 // Re(Omega_p z^2)
+                        const R ibp2 = R(1) / bp2;
+                        abar = nw * (GI * half_p1 * ba + R(2) * t1 + R(2) * q * ba * t3 * ibp2);
+                        bbar = nw * (GI * half_p1 * bb - R(2) * t2 + R(2) * q * bb * t3 * ibp2);
+                    }
                     n0bar = w * (GI * bp2 + t3);
                     pbar = nw * ((GI * bp2 + t3) * lg * R(0.25 * kLn2) + GIp * bp2 + u3);
                 }
                 (void)jI;
-                const R bnb = -ne * fbar;                        // d f / d(B.n) = -n_e
-                const R neb = -bn * fbar;                        // d f / d n_e = -B.n
+                R bnb, neb;                                      // d f / d(B.n) = -n_e, d f / d n_e = -B.n
+                if constexpr (sizeof(R) == 4) {
+                    const float2 v = mul2(make_float2(-ne, -bn), dup2(fbar));
+                    bnb = v.x;
+                    neb = v.y;
+                } else {
+                    bnb = -ne * fbar;
+                    neb = -bn * fbar;
+                }
                 R bxb, byb;
                 if constexpr (sizeof(R) == 4) {
                     float2 v = mul2(dup2(abar), make_float2(L.el[0], L.el[1]));

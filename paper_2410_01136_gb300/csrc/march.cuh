@@ -658,6 +658,8 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         using F = M<R>;
         const R rho2 = x * x + y * y;
         const bool has_rho = rho2 > R(0);
+        // correctly rounded rho: it enters the RM through n_e and the field
+        // envelopes, where a rsqrt-based rho measurably biases Q/U at 300 MHz
         const R rho = F::sqrt(rho2);
         const R ri = has_rho ? F::rcp_nr(rho) : R(0);
         const R c = has_rho ? x * ri : R(1);
@@ -821,11 +823,11 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
     if constexpr (MODEL == SYNAX_MODEL_JF12) {
         if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
     }
-    for (int n = n0; n < n1; ++n) {
+    R nh = R(n0) + R(0.5);                              // n + 1/2, exact
+    for (int n = n0; n < n1; ++n, nh += R(1)) {
         if constexpr (MODEL == SYNAX_MODEL_JF12) {
             if (n > n0) trk.step(+1);
         }
-        const R nh = R(n) + R(0.5);
         const R t = fma(nh, dr, nh * dr_lo);            // (n + 1/2) dr, dr as hi + lo
         const R x = P.obs[0] + t * L.n[0];
         const R y = P.obs[1] + t * L.n[1];
@@ -845,18 +847,18 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
             S = Ph::add(S, e.f);
         }
         if constexpr (sizeof(R) == 4 && NF >= 2) {
-            // frequencies in pairs: (pc + i ps) e^{i phi} for two at once
+            // frequencies in pairs: (pc + i ps) e^{i phi} for two at once.
+            // All NF are computed; those beyond n_freq have phase constant 0
+            // and are never stored.
             const float2 pc = dup2(e.pc), ps = dup2(e.ps);
 #pragma unroll
             for (int k = 0; k < NF; k += 2) {
-                if (k < P.n_freq) {
-                    float2 sn, cs;
-                    sincos_rev_pair(cd[k], cd[k + 1], s_n, sn, cs);
-                    const float2 r = fma2(pc, cs, neg2(mul2(ps, sn)));
-                    const float2 i = fma2(pc, sn, mul2(ps, cs));
-                    zr2[k >> 1] = add2(zr2[k >> 1], r);
-                    zi2[k >> 1] = add2(zi2[k >> 1], i);
-                }
+                float2 sn, cs;
+                sincos_rev_pair(cd[k], cd[k + 1], s_n, sn, cs);
+                const float2 r = fma2(pc, cs, neg2(mul2(ps, sn)));
+                const float2 i = fma2(pc, sn, mul2(ps, cs));
+                zr2[k >> 1] = add2(zr2[k >> 1], r);
+                zi2[k >> 1] = add2(zi2[k >> 1], i);
             }
         } else {
 #pragma unroll
