@@ -42,7 +42,7 @@ template <> struct Grad<SYNAX_MODEL_JF12> {
         garm[L.kb * stride] += beta_b * L.wb;
         g[8] += bpb * L.halo_unit;
         g[9] += bpb * m[mc::J_BH_IZH2] * L.halo_unit * L.az;
-        if (L.rp > R(0)) {
+        {   // X field: xe = xmag_unit = 0 where r_p <= 0
             const R proj = brb * L.sz * m[mc::J_COSX] + bzb * m[mc::J_SINX];
             g[10] += L.xmag_unit * proj;
             const R dmag_drp = m[mc::J_BX] * L.xe * L.ri * (R(1) - L.rp * R(1.0 / 4.8));
@@ -223,7 +223,10 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 const R z = P.obs[2] + t * L.n[2];
                 R B[3], N0, ne;
                 ArmCoord<R> ac{0, R(0)};
-                if constexpr (MODEL == SYNAX_MODEL_JF12) ac = trk.coord(x, y, F::sqrt(x * x + y * y));
+                if constexpr (MODEL == SYNAX_MODEL_JF12) {
+                    if constexpr (sizeof(R) == 4) ac = trk.coord(x, y, R(0));   // FP32 tracker: no rho needed
+                    else ac = trk.coord(x, y, F::sqrt(x * x + y * y));
+                }
                 FieldLocal<R> loc;
                 Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
 

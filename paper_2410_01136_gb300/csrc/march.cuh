@@ -668,28 +668,25 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         const R sz = z * F::rsqrt_nr(z * z + R(0.01));                    // smooth sign
         R Lz, omLz;
         logistic_pair<R>(az, 0.4, 0.27, Lz, omLz);
-        R br = R(0), bp = R(0), bz = R(0);
-        loc.disc_unit = R(0); loc.ka = 0; loc.kb = 0; loc.wa = R(0); loc.wb = R(0);
+        R br, bp, bz = R(0);
 
-        // disc: 8 smooth log-spiral arms inside a smooth radial window
+        // disc: 8 smooth log-spiral arms inside a smooth radial window (no
+        // branch: W = 0 outside the window zeroes the field and its gradient)
         const R W = smoothstep01<R>((rho - R(4.75)) * R(2)) * smoothstep01<R>((R(20.25) - rho) * R(2));
-        if (W > R(0)) {
+        {
             const int k = ac.k;
             const R f = ac.f;
             // b_k at the arm centre u = k + 1/2, C^1 smoothstep towards the
             // neighbouring centre on either side
-            int ka, kb;
-            R wgt;
-            if (f < R(0.5)) {
-                ka = (k + 7) & 7; kb = k; wgt = smoothstep01<R>(f + R(0.5));
-            } else {
-                ka = k; kb = (k + 1) & 7; wgt = smoothstep01<R>(f - R(0.5));
-            }
+            const bool lower = f < R(0.5);
+            const int ka = lower ? ((k + 7) & 7) : k;
+            const int kb = lower ? k : ((k + 1) & 7);
+            const R wgt = smoothstep01<R>(lower ? f + R(0.5) : f - R(0.5));
             const R beta = arms[ka] + (arms[kb] - arms[ka]) * wgt;
             const R unit = R(5) * ri * W * omLz;
             const R amp = beta * unit;
-            br += amp * R(kPitchSin);
-            bp += amp * R(kPitchCos);
+            br = amp * R(kPitchSin);
+            bp = amp * R(kPitchCos);
             loc.disc_unit = unit; loc.ka = ka; loc.kb = kb; loc.wa = R(1) - wgt; loc.wb = wgt;
         }
 
@@ -699,12 +696,11 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         const R hu = F::exp(-F::mul_hl(az, m[mc::J_IZH], m[mc::J_IZH_LO])) * Lz * omLr * sz;
         bp += m[mc::J_BH] * hu;
 
-        // X field
+        // X field (no branch: xe = 0 where r_p <= 0 zeroes it and its gradient)
         const R rp = rho - az * m[mc::J_COTX];
-        R xe = R(0), xu = R(0);
-        if (rp > R(0)) {
-            xe = F::exp(-F::mulc(rp, 1.0 / 4.8));
-            xu = xe * rp * ri;
+        const R xe = rp > R(0) ? F::exp(-F::mulc(rp, 1.0 / 4.8)) : R(0);
+        const R xu = xe * rp * ri;
+        {
             const R mag = m[mc::J_BX] * xu;
             br += mag * sz * m[mc::J_COSX];
             bz += mag * m[mc::J_SINX];
@@ -834,7 +830,11 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
         const R z = P.obs[2] + t * L.n[2];
         R B[3], N0, ne;
         ArmCoord<R> ac{0, R(0)};
-        if constexpr (MODEL == SYNAX_MODEL_JF12) ac = trk.coord(x, y, M<R>::sqrt(x * x + y * y));
+        if constexpr (MODEL == SYNAX_MODEL_JF12) {
+            // the FP32 tracker needs no rho; the FP64 path evaluates directly
+            if constexpr (sizeof(R) == 4) ac = trk.coord(x, y, R(0));
+            else ac = trk.coord(x, y, M<R>::sqrt(x * x + y * y));
+        }
         FieldLocal<R> loc;
         Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
         const Emit<R> e = emit<R>(B, N0, ne, L, P.q);
