@@ -311,7 +311,9 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 after += d;
 
                 R abar = R(0), bbar = R(0), n0bar = R(0), pbar = R(0);
-                if (lit) {
+                // FP32: no branch; without emission (w = nw = 0, 1/bp2 -> 0)
+                // every emission adjoint below is 0
+                if (sizeof(R) == 4 || lit) {
                     const R half_p1 = R(2) * q + R(2);          // (p + 1)/2
                     R t1, t2, t3, u3;
                     if constexpr (sizeof(R) == 4) {
@@ -327,7 +329,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                         t2 = t12.y;
                         t3 = r3.x;
                         u3 = r3.y;
-                        const float k = GI * half_p1 + R(2) * q * t3 * F::rcp_nr(bp2);
+                        const float k = GI * half_p1 + R(2) * q * t3 * (lit ? F::rcp_nr(bp2) : 0.0f);
                         const float2 ab = mul2(dup2(nw), fma2(make_float2(ba, bb), dup2(k),
                                                               make_float2(R(2) * t1, -R(2) * t2)));
                         abar = ab.x;

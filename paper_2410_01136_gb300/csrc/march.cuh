@@ -552,8 +552,10 @@ template <> struct ArmTracker<float> {
         poly = fma2(t, poly, dup2(1.0f));
         const float2 ser = mul2(x2, poly);
         float dphi = ser.x, dln = ser.y;
-        if (!(dot > 0.0f && fabsf(a) < 0.1f)) dphi = atan2f(cross, dot);
-        if (!(fabsf(sa) < 0.1f)) dln = 0.5f * log1pf(w);
+        if (!(dot > 0.0f && fabsf(a) < 0.1f && fabsf(sa) < 0.1f)) {   // rare: long steps near the axis
+            dphi = (dot > 0.0f && fabsf(a) < 0.1f) ? dphi : atan2f(cross, dot);
+            dln = fabsf(sa) < 0.1f ? dln : 0.5f * log1pf(w);
+        }
         u = dd_add_f(u, 1.2732395447351628f * (dphi - 4.9151570310712050f * dln));
         rho2 = rho2_new;
         b = b_new;
