@@ -214,9 +214,6 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
             const R q = P.q;
             R nh = R(n1 - 1) + R(0.5);                  // n + 1/2, exact
             for (int n = n1 - 1; n >= n0; --n, nh -= R(1)) {
-                if constexpr (MODEL == SYNAX_MODEL_JF12) {
-                    if (n < n1 - 1) trk.step(-1);
-                }
                 const R t = fma(nh, dr, nh * dr_lo);
                 const R x = P.obs[0] + t * L.n[0];
                 const R y = P.obs[1] + t * L.n[1];
@@ -372,6 +369,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 const R bzb = bbar * L.eb[2] + bnb * L.n[2];
                 g[Grad<MODEL>::P_INDEX] += pbar;
                 Grad<MODEL>::accum(P.m, loc, bxb, byb, bzb, n0bar, neb, g, garm, kAdjThreads);
+                if constexpr (MODEL == SYNAX_MODEL_JF12) trk.step(-1);   // to the previous sample
             }
         }
         if constexpr (NSLOT > 1) {

@@ -822,10 +822,8 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
         if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
     }
     R nh = R(n0) + R(0.5);                              // n + 1/2, exact
+#pragma unroll 2
     for (int n = n0; n < n1; ++n, nh += R(1)) {
-        if constexpr (MODEL == SYNAX_MODEL_JF12) {
-            if (n > n0) trk.step(+1);
-        }
         const R t = fma(nh, dr, nh * dr_lo);            // (n + 1/2) dr, dr as hi + lo
         const R x = P.obs[0] + t * L.n[0];
         const R y = P.obs[1] + t * L.n[1];
@@ -873,6 +871,9 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
                 }
             }
         }
+        // advance the arm tracker to the next sample (one step past the
+        // chunk at the end: harmless, its state is not used again)
+        if constexpr (MODEL == SYNAX_MODEL_JF12) trk.step(+1);
     }
     if constexpr (sizeof(R) == 4 && NF >= 2) {
 #pragma unroll

@@ -56,7 +56,10 @@ def test_batch_matches_single_adjoint(torch):
         gi = gi.cpu().numpy()
         assert np.allclose(g[i], gi, rtol=1e-5, atol=1e-6 * np.abs(gi).max()), i
         assert c[i] == pytest.approx(float(ci.item()), rel=1e-6)
-        assert_parity(maps[i].cpu().numpy(), forward(p).cpu().numpy(), 1e-6, 1e-6, f"set {i} maps")
+        # the same arithmetic compiled into another kernel (another register
+        # budget, so FMA contraction may differ): I to rounding, Q+iU (which
+        # cancels by up to ~100x at 408 MHz) to 1e-5
+        assert_parity(maps[i].cpu().numpy(), forward(p).cpu().numpy(), 1e-6, 1e-5, f"set {i} maps")
         # chi^2 against the oracle's maps
         ora = oracle.chi2(oracle.forward(p), tg[i].cpu().numpy(), 0.5)
         assert c[i] == pytest.approx(ora, rel=1e-5)
