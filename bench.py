@@ -45,7 +45,7 @@ FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 # DRAM bytes (read + write) of one k_adjoint launch of this workload, from the
 # ncu capture summarised in profiles/k_adjoint_jf12_nside64_512steps.md
-ADJ_DRAM_BYTES = 2.432e6
+ADJ_DRAM_BYTES = 2.444e6
 
 
 def parse():
@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the CPU oracle")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the learned surrogate")
     ap.add_argument("--surrogate-steps", type=int, default=20000, help="Adam steps of the surrogate training")
+    ap.add_argument("--surrogate-maps", type=int, default=50000, help="training maps of the surrogate")
+    ap.add_argument("--only-surrogate", action="store_true",
+                    help="run only the surrogate section and print its object (a profiling aid)")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 8, 16, 32],
                     help="lanes per ray for every launch (0: autotune per step-count bin)")
     return ap.parse_args()
@@ -242,7 +245,7 @@ def bench_batch(sx, inputs, torch, dev, n_runs: int = 3, sets=None, name=None) -
     }
 
 
-def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict) -> dict:
+def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict, n_maps: int = 50000) -> dict:
     """The learned surrogate on its workload: 50 000 Nside-64 JF12-type maps at
     408 MHz (parameters uniform in +-20 % of the fiducial scale), an MLP
     16 -> 1024 x 4 -> 3 x 3072, judged by the march on 512 held-out draws."""
@@ -251,7 +254,7 @@ def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict) -> dict:
 
     prob = inputs.config5_problem()
     sur = Surrogate.for_workload(batch=512, total_steps=steps, lr=1e-3, lr_min=1e-5)
-    thetas = inputs.config5_thetas(50000, seed=50)
+    thetas = inputs.config5_thetas(n_maps, seed=50)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sur.dataset(prob, thetas)
@@ -310,7 +313,7 @@ def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict) -> dict:
     ms_march = e0.elapsed_time(e1) / 10
     pass_all = float(np.mean(rms.max(axis=1) <= 1.0))
     out = {
-        "workload": "MLP 16->1024x4 (GELU)->3x3072, Nside 64 maps at 408 MHz, 50000 training maps, "
+        "workload": f"MLP 16->1024x4 (GELU)->3x3072, Nside 64 maps at 408 MHz, {n_maps} training maps, "
                     "+-20% parameter box, 512 held-out draws judged by the march",
         "dataset_s": t_data, "train_steps": steps, "train_s": t_train, "ms_per_train_step": 1e3 * t_train / steps,
         "final_loss": float(np.mean(losses[-200:])), "norm_scale_K": scale,
@@ -348,6 +351,17 @@ def run_synax(args):
     import paper_2410_01136_gb300 as sx
     from paper_2410_01136_gb300 import _native, inputs, tune
     sx.build()
+    if args.only_surrogate:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                peaks = json.load(fh)
+        except (OSError, ValueError):
+            pass
+        if rank == 0:
+            print(json.dumps({"surrogate": bench_surrogate(sx, inputs, torch, dev, args.surrogate_steps, peaks,
+                                                           args.surrogate_maps)}), flush=True)
+        return
     if args.lanes:
         tune.reset()
         _native.check(_native.lib().synax_set_lanes_per_ray(-1, args.lanes), "synax_set_lanes_per_ray")
@@ -499,7 +513,7 @@ def run_synax(args):
                 peaks = json.load(fh)
         except (OSError, ValueError):
             pass
-        out["surrogate"] = bench_surrogate(sx, inputs, torch, dev, args.surrogate_steps, peaks)
+        out["surrogate"] = bench_surrogate(sx, inputs, torch, dev, args.surrogate_steps, peaks, args.surrogate_maps)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             rate, dt, threads, desc = oracle_map_grad_rate(8192)
