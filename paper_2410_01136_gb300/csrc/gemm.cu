@@ -16,8 +16,13 @@
 //                        epilogue ("acc_full");
 //   warps 2-5            epilogue: tcgen05.ld of their 32 TMEM lanes (warp w
 //                        reads lanes 32 (w % 4) .. +31), epilogue arithmetic,
-//                        vectorised row stores (coalesced transposed stores),
-//                        then release the accumulator ("acc_empty").
+//                        then release the accumulator ("acc_empty").  FP32
+//                        outputs go through shared memory: 128 x 32 chunks in
+//                        the 128-byte swizzle (conflict-free writes), stored by
+//                        one thread with TMA (cp.async.bulk.tensor, bounds
+//                        clipped), two staging buffers in flight; other
+//                        outputs are vectorised row stores (coalesced
+//                        transposed stores).
 // With two accumulators the MMAs of tile i+1 run while tile i is stored.
 // Every mbarrier wait gives up after ~1 s of SM clocks and sets *err; each
 // role then stops, the MMA issuer waits (bounded) for its issued MMAs, the
@@ -26,6 +31,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "gemm.cuh"
@@ -45,7 +51,8 @@ struct GemmCfg {
     static constexpr uint32_t A_BYTES = kGemmBM * kGemmBK * 2;
     static constexpr uint32_t B_BYTES = BN * kGemmBK * 2;
     static constexpr uint32_t TMEM_COLS = 2 * BN;                      // two accumulators
-    static constexpr size_t SMEM = 1024 + (size_t)ST * (A_BYTES + B_BYTES) + 256;
+    static constexpr uint32_t STG_BYTES = kGemmBM * 32 * 4;                 // one 128 x 32 FP32 chunk
+    static constexpr size_t SMEM = 1024 + (size_t)ST * (A_BYTES + B_BYTES) + 2 * STG_BYTES + 256;
 };
 
 __device__ __forceinline__ bool mbar_wait_clock(uint64_t* bar, uint32_t parity) {
@@ -141,15 +148,16 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-            int K, GemmEpiParams ep, int* err) {
+k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ CUtensorMap tmC, int M, int N, int K, GemmEpiParams ep, int* err) {
     using C = GemmCfg<BN>;
     constexpr int ST = C::ST;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sB = smem + ST * C::A_BYTES;
-    uint64_t* full = (uint64_t*)(sB + ST * C::B_BYTES);
+    uint8_t* sC = sB + ST * C::B_BYTES;          // two FP32 staging chunks (1024-byte aligned)
+    uint64_t* full = (uint64_t*)(sC + 2 * C::STG_BYTES);
     uint64_t* empty = full + ST;
     uint64_t* acc_full = empty + ST;      // [2]
     uint64_t* acc_empty = acc_full + 2;   // [2]
@@ -248,9 +256,13 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         // epilogue warps 2..5: TMEM lanes 32 (warp % 4) .. +31
         const int q = warp & 3;
         int j = 0;
+        int stg = 0;       // staging chunks used (TMA-store path)
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             const int buf = j & 1;
-            const bool have = __all_sync(0xffffffffu, mbar_wait_clock(&acc_full[buf], (j >> 1) & 1) ? 1 : 0) != 0;
+            // all four epilogue warps agree (they share named barriers below):
+            // every one of them reaches this reduction each tile, waited or not
+            const bool mine = mbar_wait_clock(&acc_full[buf], (j >> 1) & 1);
+            const bool have = tc::named_and(2, 128, mine);
             if (!have) {
                 ok = false;
                 break;
@@ -264,12 +276,51 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 if (row_ok && ep.target_rows) trow = ep.target_rows[row];
             }
             const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
-            for (int c = 0; c < BN; c += 16) {
-                float v[16];
-                tc::tmem_ld16(base + (uint32_t)c, v);
-                if (!row_ok || n0 + c >= N) continue;
-                const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
-                epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq);
+            constexpr bool kF32Out = EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC;
+            if (kF32Out && ep.tma_store) {
+                // 32 columns at a time through a swizzled staging chunk and a TMA store
+                const int r = q * 32 + lane;                      // row within the tile
+                for (int c = 0; c < BN && n0 + c < N; c += 32, ++stg) {
+                    uint8_t* chunk = sC + (stg & 1) * C::STG_BYTES;
+                    if (threadIdx.x == 64) tc::bulk_wait_read<1>();    // this buffer's previous store has read it
+                    tc::named_sync(1, 128);
+                    float v[32];
+                    tc::tmem_ld16(base + (uint32_t)c, v);
+                    tc::tmem_ld16(base + (uint32_t)(c + 16), v + 16);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int col = n0 + c + i < N ? n0 + c + i : N - 1;
+                        float x = v[i];
+                        if constexpr (EPI == EPI_BIAS_F32) x += ep.bias[col];
+                        if constexpr (EPI == EPI_AFFINE) {
+                            if (ep.bias) x += ep.bias[col];
+                            x *= ep.colscale ? ep.colscale[col] : ep.scale;
+                            if (ep.shift) x += ep.shift[col];
+                        }
+                        if constexpr (EPI == EPI_SCALE_ACC) x *= ep.scale;
+                        v[i] = x;
+                    }
+                    // 128-byte swizzle: 16-byte unit j of row r sits at unit j ^ (r % 8)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<float4*>(chunk + r * 128 + ((j ^ (r & 7)) << 4)) =
+                            make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    tc::fence_proxy_async_smem();
+                    tc::named_sync(1, 128);
+                    if (threadIdx.x == 64) {
+                        tc::tma_store_2d(&tmC, chunk, n0 + c, m0);
+                        tc::bulk_commit();
+                    }
+                }
+                // drain the chunk loads above in TMEM order before releasing
+            } else {
+                for (int c = 0; c < BN; c += 16) {
+                    float v[16];
+                    tc::tmem_ld16(base + (uint32_t)c, v);
+                    if (!row_ok || n0 + c >= N) continue;
+                    const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
+                    epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq);
+                }
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -280,6 +331,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (lane == 0) red[warp - 2] = sq;
         }
+        if (threadIdx.x == 64 && stg > 0) tc::bulk_wait_all();   // every TMA store has completed
     }
     if (!ok) atomicExch(err, 1);
     tc::fence_before_sync();
@@ -360,12 +412,35 @@ cudaError_t set_smem_attrs() {
     return e;
 }
 
+// 2-D FP32 tensor map of the output [rows][ld], box 32 x 128, 128-byte swizzle.
+int make_out_map(CUtensorMap* map, const void* base, int rows, int cols, int ld) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return SYNAX_ECUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32u, (cuuint32_t)kGemmBM};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SYNAX_OK : SYNAX_EINVAL;
+}
+
 template <int BN, int EPI>
-int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const GemmEpiParams& ep,
+int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const GemmEpiParams& ep_in,
                   int* err, cudaStream_t st) {
     const int tiles = ((N + BN - 1) / BN) * ((M + kGemmBM - 1) / kGemmBM);
     const int grid = tiles < sm_count() ? tiles : sm_count();
-    k_gemm_bf16<BN, EPI><<<grid, kGemmThreads, GemmCfg<BN>::SMEM, st>>>(ma, mb, M, N, K, ep, err);
+    GemmEpiParams ep = ep_in;
+    CUtensorMap mc;
+    std::memset(&mc, 0, sizeof mc);
+    ep.tma_store = 0;
+    constexpr bool kF32Out = EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC;
+    if (kF32Out && !(EPI == EPI_SCALE_ACC && ep.accumulate) && ep.out_f32 &&
+        ((uintptr_t)ep.out_f32 & 15) == 0 && (ep.ld_f32 & 3) == 0 &&
+        make_out_map(&mc, ep.out_f32, M, N, ep.ld_f32) == SYNAX_OK)
+        ep.tma_store = 1;
+    k_gemm_bf16<BN, EPI><<<grid, kGemmThreads, GemmCfg<BN>::SMEM, st>>>(ma, mb, mc, M, N, K, ep, err);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
 }

@@ -40,6 +40,7 @@ struct GemmEpiParams {
     const float* colscale;       // EPI_AFFINE
     const float* shift;          // EPI_AFFINE
     int accumulate;              // EPI_SCALE_ACC
+    int tma_store;               // set by gemm_bf16: FP32 output written through TMA stores
 };
 
 // Set the kernels' shared-memory attributes (once per process; gemm_bf16

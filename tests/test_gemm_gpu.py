@@ -47,6 +47,15 @@ def test_gemm_matches_fp32_matmul(torch, M, N, K):
     assert err <= 1e-4 * ref.abs().max().item() + 1e-5, err
 
 
+def test_gemm_unaligned_output_pitch(torch):
+    """An output pitch that is not a multiple of 4 floats takes the direct-store epilogue."""
+    A = torch.randn((200, 128), device="cuda").to(torch.bfloat16)
+    B = torch.randn((300, 128), device="cuda").to(torch.bfloat16)
+    C = run_gemm(torch, A, B, ldc=301)
+    ref = A.float() @ B.float().T
+    assert (C - ref).abs().max().item() <= 1e-4 * ref.abs().max().item()
+
+
 def test_gemm_row_pitch_and_validation(torch):
     A = torch.randn((130, 128), device="cuda").to(torch.bfloat16)[:, :64]     # pitch 128, K 64
     B = torch.randn((96, 64), device="cuda").to(torch.bfloat16)
