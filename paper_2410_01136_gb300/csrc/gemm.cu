@@ -72,22 +72,46 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
+// 16 per-column values p[col0 .. col0 + 15] (the last valid column repeated
+// past nv): four 16-byte loads when the run is whole and aligned.
+__device__ __forceinline__ void load16(const float* __restrict__ p, int col0, int nv, float* out) {
+    const float* q = p + col0;
+    if (nv == 16 && (((uintptr_t)q) & 15) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 t = reinterpret_cast<const float4*>(q)[k];
+            out[4 * k] = t.x;
+            out[4 * k + 1] = t.y;
+            out[4 * k + 2] = t.z;
+            out[4 * k + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) out[i] = q[i < nv ? i : nv - 1];
+    }
+}
+
 // Epilogue of 16 consecutive columns col0.. of one row (nv of them valid).
 template <int EPI>
 __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float* v, int row, int col0, int nv,
                                            long long trow, float& sq) {
     if constexpr (EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC) {
         float* o = ep.out_f32 + (long long)row * ep.ld_f32 + col0;
-        float r[16];
+        float r[16], b[16], sc[16], sh[16];
+        if constexpr (EPI == EPI_BIAS_F32) load16(ep.bias, col0, nv, b);
+        if constexpr (EPI == EPI_AFFINE) {
+            if (ep.bias) load16(ep.bias, col0, nv, b);
+            if (ep.colscale) load16(ep.colscale, col0, nv, sc);
+            if (ep.shift) load16(ep.shift, col0, nv, sh);
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const int col = col0 + (i < nv ? i : 0);
             float x = v[i];
-            if constexpr (EPI == EPI_BIAS_F32) x += ep.bias[col];
+            if constexpr (EPI == EPI_BIAS_F32) x += b[i];
             if constexpr (EPI == EPI_AFFINE) {
-                if (ep.bias) x += ep.bias[col];
-                x *= ep.colscale ? ep.colscale[col] : ep.scale;
-                if (ep.shift) x += ep.shift[col];
+                if (ep.bias) x += b[i];
+                x *= ep.colscale ? sc[i] : ep.scale;
+                if (ep.shift) x += sh[i];
             }
             if constexpr (EPI == EPI_SCALE_ACC) x = ep.accumulate ? fmaf(ep.scale, x, o[i < nv ? i : 0]) : ep.scale * x;
             r[i] = x;
@@ -100,24 +124,26 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
             for (int i = 0; i < nv; ++i) o[i] = r[i];
         }
     } else {
-        __nv_bfloat16 r[16];
-        float z16[16];
+        float r[16];               // values to round to BF16 (kept in registers)
+        float z16[16], b[16], a[16], t[16];
+        if constexpr (EPI == EPI_BIAS_GELU || EPI == EPI_MSE) load16(ep.bias, col0, nv, b);
+        if constexpr (EPI == EPI_GELU_BWD) load16(ep.aux + (long long)row * ep.ld_aux, col0, nv, a);
+        if constexpr (EPI == EPI_MSE) load16(ep.target + trow * ep.ld_target, col0, nv, t);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const int col = col0 + (i < nv ? i : 0);
             float x = v[i];
             if constexpr (EPI == EPI_BIAS_GELU) {
-                const float z = x + ep.bias[col];
+                const float z = x + b[i];
                 z16[i] = z;
                 x = gelu_f(z);
             } else if constexpr (EPI == EPI_GELU_BWD) {
-                x *= gelu_grad_f(ep.aux[(long long)row * ep.ld_aux + col]);
+                x *= gelu_grad_f(a[i]);
             } else {   // EPI_MSE
-                const float d = x + ep.bias[col] - ep.target[trow * ep.ld_target + col];
+                const float d = x + b[i] - t[i];
                 if (i < nv) sq = fmaf(d, d, sq);
                 x = ep.coef * d;
             }
-            r[i] = __float2bfloat16_rn(x);
+            r[i] = x;
         }
         if constexpr (EPI == EPI_BIAS_GELU) {
             if (ep.out_z) {
@@ -132,16 +158,26 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
                 }
             }
         }
+        // BF16 rounding once; pairs packed into 32-bit words with bit operations
+        // (no array whose address is taken, so nothing goes to local memory)
+        uint32_t h[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = __bfloat16_as_ushort(__float2bfloat16_rn(r[i]));
         __nv_bfloat16* o = ep.out_bf16 + (long long)row * ep.ld_bf16 + col0;
         if (nv == 16 && (((uintptr_t)o) & 15) == 0) {
-            const uint4* src = reinterpret_cast<const uint4*>(r);
-            reinterpret_cast<uint4*>(o)[0] = src[0];
-            reinterpret_cast<uint4*>(o)[1] = src[1];
+            reinterpret_cast<uint4*>(o)[0] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16),
+                                                        h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+            reinterpret_cast<uint4*>(o)[1] = make_uint4(h[8] | (h[9] << 16), h[10] | (h[11] << 16),
+                                                        h[12] | (h[13] << 16), h[14] | (h[15] << 16));
         } else {
-            for (int i = 0; i < nv; ++i) o[i] = r[i];
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (i < nv) o[i] = __ushort_as_bfloat16((unsigned short)h[i]);
         }
         if (ep.out_bf16_t) {
-            for (int i = 0; i < nv; ++i) ep.out_bf16_t[(long long)(col0 + i) * ep.ld_t + row] = r[i];
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (i < nv) ep.out_bf16_t[(long long)(col0 + i) * ep.ld_t + row] = __ushort_as_bfloat16((unsigned short)h[i]);
         }
     }
 }
@@ -287,18 +323,34 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     float v[32];
                     tc::tmem_ld16(base + (uint32_t)c, v);
                     tc::tmem_ld16(base + (uint32_t)(c + 16), v + 16);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int col = n0 + c + i < N ? n0 + c + i : N - 1;
-                        float x = v[i];
-                        if constexpr (EPI == EPI_BIAS_F32) x += ep.bias[col];
-                        if constexpr (EPI == EPI_AFFINE) {
-                            if (ep.bias) x += ep.bias[col];
-                            x *= ep.colscale ? ep.colscale[col] : ep.scale;
-                            if (ep.shift) x += ep.shift[col];
+                    {
+                        const int nv32 = N - (n0 + c) < 32 ? N - (n0 + c) : 32;
+                        float b[32], sc[32], sh[32];
+                        const int nlo = nv32 < 16 ? nv32 : 16, nhi = nv32 > 16 ? nv32 - 16 : 1;
+                        if (EPI == EPI_BIAS_F32 || (EPI == EPI_AFFINE && ep.bias)) {
+                            load16(ep.bias, n0 + c, nlo, b);
+                            load16(ep.bias, nv32 > 16 ? n0 + c + 16 : n0 + c, nhi, b + 16);
                         }
-                        if constexpr (EPI == EPI_SCALE_ACC) x *= ep.scale;
-                        v[i] = x;
+                        if (EPI == EPI_AFFINE && ep.colscale) {
+                            load16(ep.colscale, n0 + c, nlo, sc);
+                            load16(ep.colscale, nv32 > 16 ? n0 + c + 16 : n0 + c, nhi, sc + 16);
+                        }
+                        if (EPI == EPI_AFFINE && ep.shift) {
+                            load16(ep.shift, n0 + c, nlo, sh);
+                            load16(ep.shift, nv32 > 16 ? n0 + c + 16 : n0 + c, nhi, sh + 16);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            float x = v[i];
+                            if constexpr (EPI == EPI_BIAS_F32) x += b[i];
+                            if constexpr (EPI == EPI_AFFINE) {
+                                if (ep.bias) x += b[i];
+                                x *= ep.colscale ? sc[i] : ep.scale;
+                                if (ep.shift) x += sh[i];
+                            }
+                            if constexpr (EPI == EPI_SCALE_ACC) x *= ep.scale;
+                            v[i] = x;
+                        }
                     }
                     // 128-byte swizzle: 16-byte unit j of row r sits at unit j ^ (r % 8)
 #pragma unroll
@@ -314,12 +366,30 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 }
                 // drain the chunk loads above in TMEM order before releasing
             } else {
-                for (int c = 0; c < BN; c += 16) {
-                    float v[16];
-                    tc::tmem_ld16(base + (uint32_t)c, v);
-                    if (!row_ok || n0 + c >= N) continue;
-                    const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
-                    epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq);
+                // TMEM reads pipelined one 16-column chunk ahead of the epilogue
+                // arithmetic: even chunks in ra, odd chunks in rb (BN is a multiple of 32)
+                uint32_t ra[16], rb[16];
+                tc::tmem_ld16_async(base, ra);
+                tc::tmem_wait_ld();
+                for (int c = 0; c < BN; c += 32) {
+                    tc::tmem_ld16_async(base + (uint32_t)(c + 16), rb);
+                    if (row_ok && n0 + c < N) {
+                        float v[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
+                        const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
+                        epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq);
+                    }
+                    tc::tmem_wait_ld();
+                    if (c + 32 < BN) tc::tmem_ld16_async(base + (uint32_t)(c + 32), ra);
+                    if (row_ok && n0 + c + 16 < N) {
+                        float v[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(rb[i]);
+                        const int nv = N - (n0 + c + 16) < 16 ? N - (n0 + c + 16) : 16;
+                        epilogue16<EPI>(ep, v, row, n0 + c + 16, nv, trow, sq);
+                    }
+                    if (c + 32 < BN) tc::tmem_wait_ld();
                 }
             }
             tc::fence_before_sync();
@@ -349,8 +419,12 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// tile width: 256 for wide outputs, 128 for medium, 64 for narrow ones
-static int gemm_bn_for(int N) { return N >= 2048 ? 256 : (N >= 256 ? 128 : 64); }
+// tile width: 256 for wide outputs, and for medium ones with a long K (the A
+// row block is then re-read by half as many column tiles and each stage
+// feeds twice the MMA work); 128 for medium, 64 for narrow ones
+static int gemm_bn_for(int N, int K) {
+    return (N >= 2048 || (N >= 1024 && K >= 4096)) ? 256 : (N >= 256 ? 128 : 64);
+}
 
 namespace {
 
@@ -449,7 +523,7 @@ template <int EPI>
 int launch_gemm_bn(const CUtensorMap& ma, const void* B, int N, int K, int ldb, int M, const GemmEpiParams& ep,
                    int* err, cudaStream_t st) {
     CUtensorMap mb;
-    const int bn = gemm_bn_for(N);
+    const int bn = gemm_bn_for(N, K);
     if (bn == 256) {
         if (make_map(&mb, B, N, K, ldb, 256) != SYNAX_OK) return SYNAX_EINVAL;
         return launch_gemm_t<256, EPI>(ma, mb, M, N, K, ep, err, st);
@@ -481,8 +555,8 @@ int gemm_init() {
     return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
 }
 
-int gemm_tiles(int M, int N) {
-    const int bn = gemm_bn_for(N);
+int gemm_tiles(int M, int N, int K) {
+    const int bn = gemm_bn_for(N, K);
     const int tiles = ((N + bn - 1) / bn) * ((M + kGemmBM - 1) / kGemmBM);
     return tiles < sm_count() ? tiles : sm_count();
 }

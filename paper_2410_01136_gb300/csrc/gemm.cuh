@@ -47,8 +47,8 @@ struct GemmEpiParams {
 // calls it too).  Call before capturing a stream that will launch GEMMs.
 int gemm_init();
 
-// Number of CTAs of a GEMM with this M and N (one loss partial each).
-int gemm_tiles(int M, int N);
+// Number of CTAs of a GEMM of this shape (one loss partial each).
+int gemm_tiles(int M, int N, int K);
 
 // Enqueue C = A . B^T with epilogue `epi` on `st`.  A [M][lda], B [N][ldb]
 // BF16 row-major, K a multiple of 64, pitches multiples of 8 elements, bases

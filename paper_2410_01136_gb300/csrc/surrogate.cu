@@ -734,7 +734,7 @@ int synax_surrogate_create(const synax_surrogate_cfg* cfg, synax_surrogate_t** o
     const long long dmax = s->n_out > c.width ? s->n_out : c.width;
     SX_ALLOC(s->eD0, (long long)E * dmax) SX_ALLOC(s->eD1, (long long)E * dmax)
     SX_ALLOC(s->rows_dev, B) SX_ALLOC(s->ybuf, (long long)B * s->n_out)
-    s->n_part = gemm_tiles(B, s->n_out);
+    s->n_part = gemm_tiles(B, s->n_out, c.width);
     SX_ALLOC(s->loss_part, s->n_part) SX_ALLOC(s->loss_hist, kLossHist)
     SX_ALLOC(s->t_dev, 1) SX_ALLOC(s->adam_coef, 4) SX_ALLOC(s->err, 1)
     SX_ALLOC(s->sign_dev, npix) SX_ALLOC(s->basis_rows_dev, c.n_basis)
