@@ -1,19 +1,20 @@
 // forward.cuh -- forward ray-march kernel (Sec. 2.3, Eq. 2 and 5-9).
 //
-// Work decomposition: one warp per sightline, 8 sightlines per 256-thread
-// CTA.  The N_int midpoints of a ray are split into 32 contiguous chunks,
-// one per lane.  Each lane marches its chunk once, evaluating the fields and
-// emissivities, and keeps:
+// Work decomposition: LPR lanes of a warp (8, 16 or 32) march one sightline,
+// a 128-thread CTA 128 / LPR of them.  The N_int midpoints of a ray are split
+// into LPR contiguous chunks, one per lane.  Each lane marches its chunk once
+// (the FP32 JF12-type path two samples per iteration, as element pairs),
+// evaluating the fields and emissivities, and keeps:
 //   * sum of j_I over its samples (I does not depend on RM);
 //   * per frequency, sum of j_P e^{2i chi_0} e^{2i lambda^2 RM_local}, where
 //     RM_local is the RM accumulated from the start of the lane's chunk;
 //   * the chunk total S_lane of f = n_e B_par (double-float).
-// A warp exclusive scan of S_lane gives every lane its RM offset O (the RM
-// of all earlier chunks); because e^{i(a + b)} = e^{ia} e^{ib}, rotating the
-// lane's complex partial sums by e^{2i lambda^2 K O} makes the split exact,
-// with no per-step storage.  A butterfly reduction then sums the lanes, and
-// the CTA stages its 8 rays in shared memory so that every (frequency,
-// Stokes) row is written as one contiguous 32-byte run.
+// A segmented exclusive scan of S_lane gives every lane its RM offset O (the
+// RM of all earlier chunks); because e^{i(a + b)} = e^{ia} e^{ib}, rotating
+// the lane's complex partial sums by e^{2i lambda^2 K O} makes the split
+// exact, with no per-step storage.  A segmented butterfly then sums the lanes,
+// and the CTA stages its rays in shared memory so that every (frequency,
+// Stokes) row is written as one contiguous run.
 //
 // The RM sum and the Faraday phases are double-float in the FP32 path: the
 // phase 2 lambda^2 RM reaches ~10^3 rad at 408 MHz, and it must be known to
@@ -27,14 +28,18 @@
 
 namespace synax {
 
-constexpr int kThreads = 256;
+// 128 threads with at most 85 registers each, so that 6 CTAs (24 warps)
+// share an SM (measured: 0.283 ms against 0.304 ms for 256 threads at the
+// natural 96 registers, for the Nside-64, 512-step, 4-frequency map).
+constexpr int kThreads = 128;
+constexpr int kFwdMinBlocks = 6;
 
-// LPR lanes march one ray (32, 16 or 8): a CTA of 256 threads handles
-// 256 / LPR rays.  Fewer lanes per ray amortise the per-ray set-up (LOS
+// LPR lanes march one ray (32, 16 or 8): a CTA of 128 threads handles
+// 128 / LPR rays.  Fewer lanes per ray amortise the per-ray set-up (LOS
 // geometry, arm-tracker anchor, scan, rotation, reductions) over more samples
 // per lane; more lanes give more parallelism for few rays.
 template <int MODEL, int NF, int LPR, typename R>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kFwdMinBlocks)
 k_forward(const MapParams<R> P, R* __restrict__ maps) {
     using Ph = PhaseOps<R>;
     using PT = typename Ph::T;

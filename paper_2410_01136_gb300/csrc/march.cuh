@@ -797,6 +797,189 @@ __device__ __forceinline__ Emit<R> emit(const R B[3], R N0, R ne, const Los<R>& 
 
 namespace synax {
 
+// ---------------------------------------------------------------------------
+// Two samples at a time (FP32, JF12-type): the field model, emission terms,
+// RM sums and phases of samples n and n + 1 as element pairs, so that the
+// FP32 arithmetic issues as FFMA2/FADD2/FMUL2.  exp, the correctly rounded
+// square root, MUFU approximations and the arm-strength lookups stay per
+// element; the arm tracker stays sequential.  Each element follows the
+// single-sample formulas of Model<JF12>::eval and emit.
+// ---------------------------------------------------------------------------
+namespace pair2 {
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+// x * c for a double constant c split into hi + lo (the pair form of mulc)
+__device__ __forceinline__ float2 mulc(float2 x, double c) {
+    const float hi = (float)c;
+    const float lo = (float)(c - (double)hi);
+    return lo == 0.0f ? mul2(x, dup2(hi)) : fma2(x, dup2(hi), mul2(x, dup2(lo)));
+}
+__device__ __forceinline__ float2 expf2(float2 x) { return f2(expf(x.x), expf(x.y)); }
+__device__ __forceinline__ float2 rcp_nr(float2 x) {
+    const float2 y = f2(rcp_approx(x.x), rcp_approx(x.y));
+    return fma2(y, fma2(neg2(x), y, dup2(1.0f)), y);
+}
+__device__ __forceinline__ float2 rsqrt_nr(float2 x) {
+    const float2 y = f2(rsqrt_approx(x.x), rsqrt_approx(x.y));
+    const float2 h = mul2(x, y);
+    return fma2(mul2(dup2(0.5f), y), fma2(neg2(h), y, dup2(1.0f)), y);
+}
+__device__ __forceinline__ float2 smoothstep(float2 t) {
+    t = f2(fminf(fmaxf(t.x, 0.0f), 1.0f), fminf(fmaxf(t.y, 0.0f), 1.0f));
+    return mul2(mul2(t, t), fma2(dup2(-2.0f), t, dup2(3.0f)));
+}
+__device__ __forceinline__ void logistic_pair(float2 x, double h, double w, float2& L, float2& omL) {
+    const float2 e = expf2(mulc(add2(x, dup2(-(float)h)), 2.0 / w));
+    const float2 r = rcp_nr(add2(dup2(1.0f), e));
+    omL = f2(e.x < 1e30f ? r.x : 0.0f, e.y < 1e30f ? r.y : 0.0f);
+    const float2 a = add2(dup2(1.0f), neg2(omL)), b = mul2(e, omL);
+    L = f2(e.x > 1.0f ? a.x : b.x, e.y > 1.0f ? a.y : b.y);
+}
+
+// B (uG), N0 and n_e (cm^-3) of the JF12-type model at two points.
+__device__ __forceinline__ void jf12_eval(const float* m, const float* arms, float2 x, float2 y, float2 z,
+                                          const ArmCoord<float>& aa, const ArmCoord<float>& ab, float2 B[3],
+                                          float2& N0, float2& ne) {
+    const float2 rho2 = fma2(x, x, mul2(y, y));
+    const float2 rho = f2(__fsqrt_rn(rho2.x), __fsqrt_rn(rho2.y));
+    const float2 rr = rcp_nr(rho);
+    const float2 ri = f2(rho2.x > 0.0f ? rr.x : 0.0f, rho2.y > 0.0f ? rr.y : 0.0f);
+    const float2 cq = mul2(x, ri), sq = mul2(y, ri);
+    const float2 c = f2(rho2.x > 0.0f ? cq.x : 1.0f, rho2.y > 0.0f ? cq.y : 1.0f);
+    const float2 s = f2(rho2.x > 0.0f ? sq.x : 0.0f, rho2.y > 0.0f ? sq.y : 0.0f);
+    const float2 az = f2(fabsf(z.x), fabsf(z.y));
+    const float2 sz = mul2(z, rsqrt_nr(fma2(z, z, dup2(0.01f))));
+    float2 Lz, omLz;
+    logistic_pair(az, 0.4, 0.27, Lz, omLz);
+
+    // disc: window and arm interpolation
+    const float2 W = mul2(smoothstep(mul2(add2(rho, dup2(-4.75f)), dup2(2.0f))),
+                          smoothstep(mul2(add2(dup2(20.25f), neg2(rho)), dup2(2.0f))));
+    float2 beta;
+    {
+        const bool la = aa.f < 0.5f, lb = ab.f < 0.5f;
+        const int ka_a = la ? ((aa.k + 7) & 7) : aa.k, kb_a = la ? aa.k : ((aa.k + 1) & 7);
+        const int ka_b = lb ? ((ab.k + 7) & 7) : ab.k, kb_b = lb ? ab.k : ((ab.k + 1) & 7);
+        const float2 wgt = smoothstep(f2(la ? aa.f + 0.5f : aa.f - 0.5f, lb ? ab.f + 0.5f : ab.f - 0.5f));
+        const float2 a0 = f2(arms[ka_a], arms[ka_b]), a1 = f2(arms[kb_a], arms[kb_b]);
+        beta = fma2(add2(a1, neg2(a0)), wgt, a0);
+    }
+    const float2 amp = mul2(beta, mul2(mul2(mul2(dup2(5.0f), ri), W), omLz));
+    float2 br = mul2(amp, dup2((float)kPitchSin));
+    float2 bp = mul2(amp, dup2((float)kPitchCos));
+
+    // toroidal halo
+    float2 Lr, omLr;
+    logistic_pair(rho, 9.22, 0.2, Lr, omLr);
+    const float2 hz = fma2(az, dup2(m[mc::J_IZH]), mul2(az, dup2(m[mc::J_IZH_LO])));
+    const float2 hu = mul2(mul2(mul2(expf2(neg2(hz)), Lz), omLr), sz);
+    bp = fma2(dup2(m[mc::J_BH]), hu, bp);
+
+    // X field
+    const float2 rp = fma2(neg2(az), dup2(m[mc::J_COTX]), rho);
+    const float2 ex = expf2(neg2(mulc(rp, 1.0 / 4.8)));
+    const float2 xe = f2(rp.x > 0.0f ? ex.x : 0.0f, rp.y > 0.0f ? ex.y : 0.0f);
+    const float2 mag = mul2(dup2(m[mc::J_BX]), mul2(mul2(xe, rp), ri));
+    br = fma2(mul2(mag, sz), dup2(m[mc::J_COSX]), br);
+    const float2 bz = mul2(mag, dup2(m[mc::J_SINX]));
+
+    B[0] = fma2(bp, neg2(s), mul2(br, c));
+    B[1] = fma2(bp, c, mul2(br, s));
+    B[2] = bz;
+
+    // n_e: thick and thin discs
+    const float2 a1r = mulc(rho, 0.05), a2r = mulc(rho, 0.25);
+    const float2 a1 = add2(a1r, fma2(az, dup2(m[mc::J_IH1]), mul2(az, dup2(m[mc::J_IH1_LO]))));
+    const float2 a2 = add2(a2r, fma2(az, dup2(m[mc::J_IH2]), mul2(az, dup2(m[mc::J_IH2_LO]))));
+    ne = fma2(dup2(0.025f), expf2(neg2(a1)), mul2(dup2(0.10f), expf2(neg2(a2))));
+
+    // CR density (fast primitives: magnitudes only)
+    const float2 e2a = mul2(dup2((float)(-2.0 * kLog2e)), az);
+    const float2 e2 = f2(ex2_approx(e2a.x), ex2_approx(e2a.y));
+    const float2 onep = add2(dup2(1.0f), e2);
+    const float2 inv1 = f2(rcp_approx(onep.x), rcp_approx(onep.y));
+    const float2 er = mul2(dup2((float)(-0.2 * kLog2e)), rho);
+    const float2 eR = f2(ex2_approx(er.x), ex2_approx(er.y));
+    N0 = mul2(dup2(m[mc::J_N0OBS] * m[mc::J_N0U]), mul2(eR, mul2(mul2(dup2(4.0f), e2), mul2(inv1, inv1))));
+}
+
+}  // namespace pair2
+
+// The FP32 JF12-type lane march, two samples per iteration (see pair2).  Same
+// contract as march_lane.
+template <int NF>
+__device__ __forceinline__ void march_lane_pair_jf12(const MapParams<float>& P, const float* s_arms,
+                                                     const Los<float>& L, const ff* nd, int n0, int n1, float dr,
+                                                     float dr_lo, const ff* cd, float& accI, float* zr, float* zi,
+                                                     ff& S) {
+    float2 zrp[NF], zip[NF];                      // (even samples, odd samples) per frequency
+#pragma unroll
+    for (int k = 0; k < NF; ++k) { zrp[k] = dup2(0.0f); zip[k] = dup2(0.0f); }
+    float2 accI2 = dup2(0.0f);
+    S = ff{0.0f, 0.0f};
+    ArmTracker<float> trk;
+    if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
+    float2 nh = make_float2(float(n0) + 0.5f, float(n0) + 1.5f);     // n + 1/2, exact
+    const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
+    for (int n = n0; n < n1; n += 2, nh = add2(nh, dup2(2.0f))) {
+        // the second sample of an odd tail is a placeholder whose terms are zeroed
+        const float live_b = n + 1 < n1 ? 1.0f : 0.0f;
+        const float2 t = fma2(nh, dup2(dr), mul2(nh, dup2(dr_lo)));
+        const float2 x = fma2(t, dup2(L.n[0]), obs_x);
+        const float2 y = fma2(t, dup2(L.n[1]), obs_y);
+        const float2 z = fma2(t, dup2(L.n[2]), obs_z);
+        const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
+        trk.step(+1);
+        const ArmCoord<float> ab = trk.coord(0.f, 0.f, 0.f);
+        trk.step(+1);
+        float2 B[3], N0, ne;
+        pair2::jf12_eval(P.m, s_arms, x, y, z, aa, ab, B, N0, ne);
+        // emission (Eq. 2, 5, 8) and RM integrand (Eq. 7), element-wise as emit()
+        float2 v = mul2(B[0], dup2(L.n[0]));
+        v = fma2(B[1], dup2(L.n[1]), v);
+        const float2 bn = fma2(B[2], dup2(L.n[2]), v);
+        float2 u = mul2(B[0], dup2(L.eb[0]));
+        u = fma2(B[1], dup2(L.eb[1]), u);
+        const float2 bb = fma2(B[2], dup2(L.eb[2]), u);
+        const float2 bl = fma2(B[0], dup2(L.el[0]), mul2(B[1], dup2(L.el[1])));
+        const float2 bp2 = fma2(bl, bl, mul2(bb, bb));
+        const float2 lg = make_float2(lg2_approx(bp2.x), lg2_approx(bp2.y));
+        const float2 qa = mul2(dup2(P.q), lg);
+        const float2 w = make_float2(bp2.x > 1e-30f ? ex2_approx(qa.x) : 0.0f, bp2.y > 1e-30f ? ex2_approx(qa.y) : 0.0f);
+        const float2 nw = mul2(mul2(N0, w), make_float2(1.0f, live_b));
+        accI2 = fma2(nw, bp2, accI2);
+        const float2 pc = mul2(nw, fma2(bl, bl, neg2(mul2(bb, bb))));
+        const float2 ps = mul2(nw, mul2(dup2(2.0f), mul2(bl, bb)));
+        const float2 f = mul2(neg2(mul2(ne, bn)), make_float2(1.0f, live_b));
+        // RM at the two midpoints: s_a = S + w f_a, S1 = S + f_a; s_b = S1 + w f_b, S2 = S1 + f_b
+        ff s_a, S1, s_b;
+        ff_add_f_pair(S, make_float2(P.w_own * f.x, f.x), s_a, S1);
+        ff_add_f_pair(S1, make_float2(P.w_own * f.y, f.y), s_b, S);
+        const float2 sh = make_float2(s_a.hi, s_b.hi), sl = make_float2(s_a.lo, s_b.lo);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            // frac(c_k s) for both samples (PhaseOps<float>::frac_mul element-wise)
+            const float2 ch = dup2(cd[k].hi), cl = dup2(cd[k].lo);
+            const float2 p = mul2(ch, sh);
+            float2 e = fma2(ch, sh, neg2(p));
+            e = fma2(ch, sl, e);
+            e = fma2(cl, sh, e);
+            const float2 kk = make_float2(rintf(p.x), rintf(p.y));
+            const float2 a = mul2(add2(add2(p, neg2(kk)), e), dup2(6.2831853071795865f));
+            const float2 sn = make_float2(sin_approx(a.x), sin_approx(a.y));
+            const float2 cs = make_float2(cos_approx(a.x), cos_approx(a.y));
+            zrp[k] = fma2(pc, cs, fma2(neg2(ps), sn, zrp[k]));
+            zip[k] = fma2(pc, sn, fma2(ps, cs, zip[k]));
+        }
+    }
+    accI = accI2.x + accI2.y;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        zr[k] = zrp[k].x + zrp[k].y;
+        zi[k] = zip[k].x + zip[k].y;
+    }
+}
+
 // One lane's share of the forward march of one ray (Sec. 2.3, Eq. 2, 5-9):
 // samples [n0, n1) of the ray with LOS triad L (and double-float direction
 // nd for the FP32 arm tracker).  Returns the lane's sum of j_I terms, per
@@ -810,6 +993,10 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
                                            typename PhaseOps<R>::T& S) {
     using Ph = PhaseOps<R>;
     using PT = typename Ph::T;
+    if constexpr (sizeof(R) == 4 && MODEL == SYNAX_MODEL_JF12) {
+        march_lane_pair_jf12<NF>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
+        return;
+    }
     accI = R(0);
 #pragma unroll
     for (int k = 0; k < NF; ++k) { zr[k] = R(0); zi[k] = R(0); }
