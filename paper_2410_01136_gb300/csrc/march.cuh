@@ -561,6 +561,50 @@ template <> struct ArmTracker<float> {
         b = b_new;
         n = nn;
     }
+    // Two steps in direction dir at once: the geometry of both comes from the
+    // anchor in closed form, so the two increments are computed as element
+    // pairs; only their double-float accumulation into u is sequential.
+    // `mid` receives the coordinate after the first step.
+    __device__ __forceinline__ void step_pair(int dir, ArmCoord<float>& mid) {
+        const float h = dir > 0 ? dr : -dr;
+        const int n1 = n + dir, n2 = n + 2 * dir;
+        const float2 dt = make_float2(float(n1 - n_a) * dr, float(n2 - n_a) * dr);
+        // (rho^2, b) after one and after two steps
+        const float2 rho2_12 = fma2(dt, fma2(dt, dup2(c), dup2(2.0f * b_a)), dup2(rho2_a));
+        const float2 b_12 = fma2(dt, dup2(c), dup2(b_a));
+        // increments of steps n -> n1 (from rho2, b) and n1 -> n2 (from the n1 values)
+        const float2 r2 = make_float2(rho2, rho2_12.x), bb = make_float2(b, b_12.x);
+        const float cross = h * lz;
+        const float2 dot = fma2(dup2(h), bb, r2);
+        const float2 a = make_float2(__fdividef(cross, dot.x), __fdividef(cross, dot.y));
+        const float2 wn = mul2(dup2(h), fma2(dup2(h), dup2(c), mul2(dup2(2.0f), bb)));
+        const float2 w = make_float2(__fdividef(wn.x, r2.x), __fdividef(wn.y, r2.y));
+        const float2 den = add2(dup2(2.0f), w);
+        const float2 sa = make_float2(__fdividef(w.x, den.x), __fdividef(w.y, den.y));
+        // atan(a) and atanh(sa) for both steps: x (1 - t/3 + t^2/5 - t^3/7)
+        const float2 ta = mul2(a, a), ts = neg2(mul2(sa, sa));
+        float2 pa = fma2(ta, dup2(-1.0f / 7.0f), dup2(0.2f));
+        float2 ps = fma2(ts, dup2(-1.0f / 7.0f), dup2(0.2f));
+        pa = fma2(ta, pa, dup2(-1.0f / 3.0f));
+        ps = fma2(ts, ps, dup2(-1.0f / 3.0f));
+        pa = fma2(ta, pa, dup2(1.0f));
+        ps = fma2(ts, ps, dup2(1.0f));
+        float2 dphi = mul2(a, pa), dln = mul2(sa, ps);
+        if (!(dot.x > 0.0f && fabsf(a.x) < 0.1f && fabsf(sa.x) < 0.1f && dot.y > 0.0f && fabsf(a.y) < 0.1f &&
+              fabsf(sa.y) < 0.1f)) {   // rare: long steps near the axis
+            if (!(dot.x > 0.0f && fabsf(a.x) < 0.1f)) dphi.x = atan2f(cross, dot.x);
+            if (!(dot.y > 0.0f && fabsf(a.y) < 0.1f)) dphi.y = atan2f(cross, dot.y);
+            if (!(fabsf(sa.x) < 0.1f)) dln.x = 0.5f * log1pf(w.x);
+            if (!(fabsf(sa.y) < 0.1f)) dln.y = 0.5f * log1pf(w.y);
+        }
+        const float2 inc = mul2(dup2(1.2732395447351628f), fma2(dup2(-4.9151570310712050f), dln, dphi));
+        u = dd_add_f(u, inc.x);
+        mid = coord(0.f, 0.f, 0.f);
+        u = dd_add_f(u, inc.y);
+        rho2 = rho2_12.y;
+        b = b_12.y;
+        n = n2;
+    }
     __device__ __forceinline__ ArmCoord<float> coord(float, float, float) const {
         const float v = u.hi - 8.0f * floorf(u.hi * 0.125f);
         float kf = floorf(v);
@@ -929,9 +973,8 @@ __device__ __forceinline__ void march_lane_pair_jf12(const MapParams<float>& P, 
         const float2 y = fma2(t, dup2(L.n[1]), obs_y);
         const float2 z = fma2(t, dup2(L.n[2]), obs_z);
         const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
-        trk.step(+1);
-        const ArmCoord<float> ab = trk.coord(0.f, 0.f, 0.f);
-        trk.step(+1);
+        ArmCoord<float> ab;
+        trk.step_pair(+1, ab);
         float2 B[3], N0, ne;
         pair2::jf12_eval(P.m, s_arms, x, y, z, aa, ab, B, N0, ne);
         // emission (Eq. 2, 5, 8) and RM integrand (Eq. 7), element-wise as emit()
