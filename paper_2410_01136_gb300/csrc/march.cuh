@@ -501,6 +501,9 @@ template <> struct ArmTracker<double> {
     }
 };
 
+// Floor of the tracked rho^2 (kpc^2): a point closer to the axis than 1e-15 kpc.
+constexpr float kMinRho2 = 1e-30f;
+
 template <> struct ArmTracker<float> {
     ff u;
     float rho2_a, b_a, c, lz, dr;
@@ -518,7 +521,7 @@ template <> struct ArmTracker<float> {
         lz = dd_add(dd_mul(ff{P.obs[0], P.obs_lo[0]}, nd[1]), dd_neg(dd_mul(ff{P.obs[1], P.obs_lo[1]}, nd[0]))).hi;
         b_a = px.hi * nd[0].hi + py.hi * nd[1].hi;
         c = nd[0].hi * nd[0].hi + nd[1].hi * nd[1].hi;
-        rho2_a = r2.hi;
+        rho2_a = fmaxf(r2.hi, kMinRho2);
         rho2 = rho2_a;
         b = b_a;
         if (r2.hi > 0.0f) {
@@ -528,6 +531,8 @@ template <> struct ArmTracker<float> {
             const ff d = dd_add(phi, dd_neg(dd_mul(dd_const(kPitchCot), halfln)));
             u = dd_mul(dd_const(4.0 / kPi), d);
         } else {
+            // a chunk starting exactly on the axis (x = y = 0 in FP32): the
+            // azimuth is undefined there and u starts at 0
             u = ff{0.0f, 0.0f};
         }
     }
@@ -536,7 +541,8 @@ template <> struct ArmTracker<float> {
         const float h = dir > 0 ? dr : -dr;
         const int nn = n + dir;
         const float dt = float(nn - n_a) * dr;
-        const float rho2_new = rho2_a + dt * (2.0f * b_a + dt * c);
+        // (rho^2 from the anchor can round to <= 0 where the ray crosses the axis)
+        const float rho2_new = fmaxf(rho2_a + dt * (2.0f * b_a + dt * c), kMinRho2);
         const float b_new = b_a + dt * c;
         const float cross = h * lz;
         const float dot = rho2 + h * b;
@@ -554,7 +560,9 @@ template <> struct ArmTracker<float> {
         float dphi = ser.x, dln = ser.y;
         if (!(dot > 0.0f && fabsf(a) < 0.1f && fabsf(sa) < 0.1f)) {   // rare: long steps near the axis
             dphi = (dot > 0.0f && fabsf(a) < 0.1f) ? dphi : atan2f(cross, dot);
-            dln = fabsf(sa) < 0.1f ? dln : 0.5f * log1pf(w);
+            // from the tracked rho^2 values: these increments telescope, so u is
+            // exact again once the ray has left the axis
+            dln = fabsf(sa) < 0.1f ? dln : 0.5f * (logf(rho2_new) - logf(rho2));
         }
         u = dd_add_f(u, 1.2732395447351628f * (dphi - 4.9151570310712050f * dln));
         rho2 = rho2_new;
@@ -569,8 +577,10 @@ template <> struct ArmTracker<float> {
         const float h = dir > 0 ? dr : -dr;
         const int n1 = n + dir, n2 = n + 2 * dir;
         const float2 dt = make_float2(float(n1 - n_a) * dr, float(n2 - n_a) * dr);
-        // (rho^2, b) after one and after two steps
-        const float2 rho2_12 = fma2(dt, fma2(dt, dup2(c), dup2(2.0f * b_a)), dup2(rho2_a));
+        // (rho^2, b) after one and after two steps (rho^2 floored: it can round
+        // to <= 0 where the ray crosses the axis)
+        float2 rho2_12 = fma2(dt, fma2(dt, dup2(c), dup2(2.0f * b_a)), dup2(rho2_a));
+        rho2_12 = make_float2(fmaxf(rho2_12.x, kMinRho2), fmaxf(rho2_12.y, kMinRho2));
         const float2 b_12 = fma2(dt, dup2(c), dup2(b_a));
         // increments of steps n -> n1 (from rho2, b) and n1 -> n2 (from the n1 values)
         const float2 r2 = make_float2(rho2, rho2_12.x), bb = make_float2(b, b_12.x);
@@ -594,8 +604,9 @@ template <> struct ArmTracker<float> {
               fabsf(sa.y) < 0.1f)) {   // rare: long steps near the axis
             if (!(dot.x > 0.0f && fabsf(a.x) < 0.1f)) dphi.x = atan2f(cross, dot.x);
             if (!(dot.y > 0.0f && fabsf(a.y) < 0.1f)) dphi.y = atan2f(cross, dot.y);
-            if (!(fabsf(sa.x) < 0.1f)) dln.x = 0.5f * log1pf(w.x);
-            if (!(fabsf(sa.y) < 0.1f)) dln.y = 0.5f * log1pf(w.y);
+            // from the tracked rho^2 values (telescoping, exact once off the axis)
+            if (!(fabsf(sa.x) < 0.1f)) dln.x = 0.5f * (logf(rho2_12.x) - logf(rho2));
+            if (!(fabsf(sa.y) < 0.1f)) dln.y = 0.5f * (logf(rho2_12.y) - logf(rho2_12.x));
         }
         const float2 inc = mul2(dup2(1.2732395447351628f), fma2(dup2(-4.9151570310712050f), dln, dphi));
         u = dd_add_f(u, inc.x);
@@ -868,16 +879,22 @@ __device__ __forceinline__ float2 rsqrt_nr(float2 x) {
     const float2 h = mul2(x, y);
     return fma2(mul2(dup2(0.5f), y), fma2(neg2(h), y, dup2(1.0f)), y);
 }
-__device__ __forceinline__ float2 smoothstep(float2 t) {
-    t = f2(fminf(fmaxf(t.x, 0.0f), 1.0f), fminf(fmaxf(t.y, 0.0f), 1.0f));
+// t^2 (3 - 2 t) for t already in [0, 1]
+__device__ __forceinline__ float2 smoothstep_unit(float2 t) {
     return mul2(mul2(t, t), fma2(dup2(-2.0f), t, dup2(3.0f)));
 }
+// smoothstep of a * x + b, the argument clamped to [0, 1] by the saturating FMA
+__device__ __forceinline__ float2 smoothstep_affine(float2 x, float a, float b) {
+    return smoothstep_unit(f2(__saturatef(fmaf(x.x, a, b)), __saturatef(fmaf(x.y, a, b))));
+}
+// L(x; h, w) = 1/(1 + e^{-2(x-h)/w}) and 1 - L, each without cancellation.
+// The exponent is capped at 80 so that e stays finite (1 - L is then below
+// 2e-35, where it no longer matters) and no select is needed.
 __device__ __forceinline__ void logistic_pair(float2 x, double h, double w, float2& L, float2& omL) {
-    const float2 e = expf2(mulc(add2(x, dup2(-(float)h)), 2.0 / w));
-    const float2 r = rcp_nr(add2(dup2(1.0f), e));
-    omL = f2(e.x < 1e30f ? r.x : 0.0f, e.y < 1e30f ? r.y : 0.0f);
-    const float2 a = add2(dup2(1.0f), neg2(omL)), b = mul2(e, omL);
-    L = f2(e.x > 1.0f ? a.x : b.x, e.y > 1.0f ? a.y : b.y);
+    const float2 arg = mulc(add2(x, dup2(-(float)h)), 2.0 / w);
+    const float2 e = expf2(f2(fminf(arg.x, 80.0f), fminf(arg.y, 80.0f)));
+    omL = rcp_nr(add2(dup2(1.0f), e));
+    L = mul2(e, omL);
 }
 
 // B (uG), N0 and n_e (cm^-3) of the JF12-type model at two points.
@@ -897,14 +914,14 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
     logistic_pair(az, 0.4, 0.27, Lz, omLz);
 
     // disc: window and arm interpolation
-    const float2 W = mul2(smoothstep(mul2(add2(rho, dup2(-4.75f)), dup2(2.0f))),
-                          smoothstep(mul2(add2(dup2(20.25f), neg2(rho)), dup2(2.0f))));
+    const float2 W = mul2(smoothstep_affine(rho, 2.0f, -9.5f), smoothstep_affine(rho, -2.0f, 40.5f));
     float2 beta;
     {
         const bool la = aa.f < 0.5f, lb = ab.f < 0.5f;
         const int ka_a = la ? ((aa.k + 7) & 7) : aa.k, kb_a = la ? aa.k : ((aa.k + 1) & 7);
         const int ka_b = lb ? ((ab.k + 7) & 7) : ab.k, kb_b = lb ? ab.k : ((ab.k + 1) & 7);
-        const float2 wgt = smoothstep(f2(la ? aa.f + 0.5f : aa.f - 0.5f, lb ? ab.f + 0.5f : ab.f - 0.5f));
+        // f in [0, 1), so f -/+ 1/2 on the chosen side is already in [0, 1]
+        const float2 wgt = smoothstep_unit(f2(la ? aa.f + 0.5f : aa.f - 0.5f, lb ? ab.f + 0.5f : ab.f - 0.5f));
         const float2 a0 = f2(arms[ka_a], arms[ka_b]), a1 = f2(arms[kb_a], arms[kb_b]);
         beta = fma2(add2(a1, neg2(a0)), wgt, a0);
     }

@@ -148,3 +148,21 @@ def test_streams_and_out_buffer(torch):
         forward(prob, out=out)
     s.synchronize()
     assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_axis_crossing_rays(torch):
+    """Sightlines at phi = 0 cross the Galactic axis.  With 8 lanes per ray and
+    r_max = 120 kpc (64 steps), one lane's 15 kpc chunk holds the crossing at
+    8.5 kpc and the ray's re-entry into the disc beyond 13 kpc, so the arm
+    tracker must come through rho ~ 0 intact."""
+    from paper_2410_01136_gb300 import _native, tune
+    prob = inputs.config2().replace(nside=4, n_steps=64, r_max_kpc=120.0)
+    pix = [p for p in range(prob.npix) if oracle.healpix_centre(prob.nside, p)[1] == 0.0]
+    assert len(pix) >= 4
+    _native.check(_native.lib().synax_set_lanes_per_ray(-1, 8), "synax_set_lanes_per_ray")
+    try:
+        gpu = gpu_map(torch, prob)
+    finally:
+        tune.reset()
+    assert np.all(np.isfinite(gpu))
+    assert_parity(gpu[:, :, pix], oracle.forward(prob, pix=pix), what="axis-crossing rays")
