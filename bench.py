@@ -312,6 +312,31 @@ def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict, n_maps: int
     torch.cuda.synchronize()
     ms_march = e0.elapsed_time(e1) / 10
     pass_all = float(np.mean(rms.max(axis=1) <= 1.0))
+
+    # ensemble gate: a second network from other initial weights; draws where
+    # the two disagree by more than 1 K (in-subspace RMS) go to the march
+    sur_b = Surrogate.for_workload(batch=512, total_steps=steps, lr=1e-3, lr_min=1e-5, init_seed=8)
+    sur_b.dataset(prob, thetas)
+    sur_b.train(steps, seed=2)
+    c_gate, dis = sur.gate(sur_b, torch.tensor(hold, dtype=torch.float32, device=dev))
+    _, rms_g, _ = sur.judge(prob, hold, c_gate, 1.0)
+    dis, rms_g = dis.cpu().numpy().max(axis=1), rms_g.cpu().numpy().max(axis=1)
+    # calibrate the threshold on the first half of the held-out draws (largest
+    # candidate with <= 1 % judged failures among accepted), report on the second
+    cal, tst = slice(0, 256), slice(256, 512)
+    tau = 0.0
+    for cand in (0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.4, 0.5, 0.75, 1.0):
+        acc = dis[cal] <= cand
+        if acc.any() and np.mean(rms_g[cal][acc] > 1.0) <= 0.01:
+            tau = cand
+    accepted = dis[tst] <= tau
+    acc_frac = float(np.mean(accepted))
+    fail_acc = float(np.mean(rms_g[tst][accepted] > 1.0)) if accepted.any() else None
+    # gated cost per set: two surrogate evaluations + gradients, and the march
+    # for the rejected share
+    t_set = 2.0 * ms_call / B
+    t_gated = t_set + (1.0 - acc_frac) * ms_march
+    sur_b.close()
     out = {
         "workload": f"MLP 16->1024x4 (GELU)->3x3072, Nside 64 maps at 408 MHz, {n_maps} training maps, "
                     "+-20% parameter box, 512 held-out draws judged by the march",
@@ -323,6 +348,12 @@ def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict, n_maps: int
                            for k, s in enumerate("IQU")},
         "pass_frac_1K_all_stokes": pass_all, "pass_frac_1K_I": float(np.mean(rms[:, 0] <= 1.0)),
         "fell_back_frac": float(fell.float().mean().item()),
+        "gate": {"threshold_K": tau, "calibration": "largest threshold with <= 1 % judged failures among "
+                 "accepted draws on held-out draws 0-255; figures below on draws 256-511",
+                 "accepted_frac": acc_frac, "judged_fail_frac_among_accepted": fail_acc,
+                 "judged_fail_frac_all_mean_prediction": float(np.mean(rms_g[tst] > 1.0)),
+                 "maps_grad_per_s_gated": 1e3 / t_gated,
+                 "speedup_vs_march_gated": ms_march / t_gated},
         "maps_grad_per_s": B / (ms_call * 1e-3), "batch": B, "ms_per_call": ms_call,
         "march_maps_grad_per_s_same_workload": 1e3 / ms_march,
         "speedup_vs_march": (B / (ms_call * 1e-3)) / (1e3 / ms_march),

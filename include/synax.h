@@ -306,6 +306,18 @@ int synax_surrogate_judge(synax_surrogate_t* s, const synax_problem* fiducial, c
                           float* coeffs_dev, double rms_max_K, float* rms_dev, int* fell_back_dev,
                           void* stream);
 
+/* Ensemble gate (no counterpart in the paper): evaluates two surrogates of
+ * the same basis and input box, trained from different initial weights, on
+ * theta_dev [n][n_theta]; writes their mean coefficients to coeffs_dev
+ * [n][3][n_basis] (scratch_dev, of the same shape, receives b's before the
+ * mean is formed) and disagreement_dev [n][3] = ||c_a - c_b||_2 /
+ * sqrt(12 nside^2) per Stokes parameter.  Where the two networks disagree
+ * the emulator is unreliable: a caller sends those parameter sets to the
+ * march (synax_surrogate_judge with rms_max_K = 0 replaces them by the
+ * march's coefficients). */
+int synax_surrogate_gate(synax_surrogate_t* a, synax_surrogate_t* b, const float* theta_dev, int n,
+                         float* coeffs_dev, float* scratch_dev, float* disagreement_dev, void* stream);
+
 /* Waits for `stream`; SYNAX_ETIMEOUT if a bounded wait of a tensor-core
  * kernel of this surrogate gave up since creation, else SYNAX_OK. */
 int synax_surrogate_status(synax_surrogate_t* s, void* stream);

@@ -113,6 +113,7 @@ SIGNATURES = {
     "synax_surrogate": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "synax_surrogate_judge": (ctypes.c_int, [_VP, ctypes.POINTER(SynaxProblem), _VP, ctypes.c_int, _VP,
                                              ctypes.c_double, _VP, _VP, _VP]),
+    "synax_surrogate_gate": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "synax_surrogate_status": (ctypes.c_int, [_VP, _VP]),
     "synax_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "synax_surrogate_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),

@@ -379,6 +379,35 @@ k_judge(float* __restrict__ c_sur, const float* __restrict__ c_true, int n_basis
         for (int i = threadIdx.x; i < 3 * n_basis; i += blockDim.x) c_sur[base + i] = c_true[base + i];
 }
 
+// Ensemble gate: D[b][s] = ||a_s - b_s||_2 / sqrt(N) per (set, Stokes) and the
+// mean (a + b) / 2 written over a.  Block b handles set b.
+__global__ void __launch_bounds__(256)
+k_disagree(float* __restrict__ ca, const float* __restrict__ cb, int n_basis, float inv_npix,
+           float* __restrict__ d_out) {
+    __shared__ float red[3][8];
+    const int b = blockIdx.x;
+    const long long base = (long long)b * 3 * n_basis;
+    for (int s = 0; s < 3; ++s) {
+        float acc = 0.0f;
+        for (int i = threadIdx.x; i < n_basis; i += blockDim.x) {
+            const long long j = base + (long long)s * n_basis + i;
+            const float x = ca[j], y = cb[j];
+            const float d = x - y;
+            acc = fmaf(d, d, acc);
+            ca[j] = 0.5f * (x + y);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[s][threadIdx.x >> 5] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float acc = 0.0f;
+        for (int w = 0; w < 8; ++w) acc += red[threadIdx.x][w];
+        d_out[b * 3 + threadIdx.x] = sqrtf(acc * inv_npix);
+    }
+}
+
 template <typename T>
 int dalloc(T** p, size_t n) {
     *p = nullptr;
@@ -1095,6 +1124,20 @@ int synax_surrogate_judge(synax_surrogate_t* s, const synax_problem* fiducial, c
         SX_TRY(launch_status());
     }
     return SYNAX_OK;
+}
+
+int synax_surrogate_gate(synax_surrogate_t* a, synax_surrogate_t* b, const float* theta_dev, int n, float* coeffs_dev,
+                         float* scratch_dev, float* disagreement_dev, void* stream) {
+    if (!a || !b || n < 0 || (n > 0 && (!theta_dev || !coeffs_dev || !scratch_dev || !disagreement_dev)))
+        return SYNAX_EINVAL;
+    if (a->cfg.n_theta != b->cfg.n_theta || a->cfg.n_basis != b->cfg.n_basis || a->npix != b->npix)
+        return SYNAX_EINVAL;
+    if (n == 0) return SYNAX_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    SX_TRY(synax_surrogate(a, theta_dev, n, coeffs_dev, nullptr, nullptr, stream));
+    SX_TRY(synax_surrogate(b, theta_dev, n, scratch_dev, nullptr, nullptr, stream));
+    k_disagree<<<n, 256, 0, st>>>(coeffs_dev, scratch_dev, a->cfg.n_basis, (float)(1.0 / a->npix), disagreement_dev);
+    return launch_status();
 }
 
 int synax_surrogate_status(synax_surrogate_t* s, void* stream) {

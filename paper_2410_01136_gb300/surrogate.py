@@ -192,6 +192,19 @@ class Surrogate:
               "synax_surrogate_judge")
         return coeffs, rms, fell
 
+    def gate(self, other: "Surrogate", theta):
+        """Mean coefficients of this surrogate and `other` and their
+        disagreement [n, 3] (in-subspace RMS of the difference, kelvin)."""
+        torch = self._torch
+        th = theta.contiguous().float()
+        n = th.shape[0]
+        c = torch.empty((n, 3, self.n_basis), dtype=torch.float32, device=th.device)
+        scratch = torch.empty_like(c)
+        d = torch.empty((n, 3), dtype=torch.float32, device=th.device)
+        check(lib().synax_surrogate_gate(self._h, other._h, _ptr(th), n, _ptr(c), _ptr(scratch), _ptr(d),
+                                         _stream(torch)), "synax_surrogate_gate")
+        return c, d
+
     def status(self) -> None:
         check(lib().synax_surrogate_status(self._h, _stream(self._torch)), "synax_surrogate_status")
 

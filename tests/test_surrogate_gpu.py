@@ -291,3 +291,23 @@ def test_invalid_configurations_are_rejected(torch):
         Surrogate(3, lo, hi, sign, bad, nside=4)
     with pytest.raises(_native.SynaxError):
         Surrogate(3, hi, lo, sign, rows, nside=4)
+
+
+def test_gate_mean_and_disagreement_match_oracle(torch):
+    a, pa, lo, hi, sign, rows = small(torch, seed=1)
+    b, pb, _, _, _, _ = small(torch, seed=2)
+    mean = np.linspace(-1, 1, a.n_out).astype(np.float32)
+    for s_ in (a, b):
+        s_.set_normalization(mean, 1.5)
+    theta, _ = _batch(torch, a, lo, hi, 15, n=37)
+    c, d = a.gate(b, torch.tensor(theta, device="cuda"))
+    c = c.cpu().numpy().reshape(37, -1)
+    d = d.cpu().numpy()
+    x = so.normalize_theta(theta.astype(np.float64), lo, hi)
+    ca = mean + 1.5 * so.mlp_forward([(W.astype(np.float64), v.astype(np.float64)) for W, v in pa], x)[0][-1]
+    cb = mean + 1.5 * so.mlp_forward([(W.astype(np.float64), v.astype(np.float64)) for W, v in pb], x)[0][-1]
+    assert_close(c - mean, 0.5 * (ca + cb) - mean, "gated mean")
+    ref = so.judge_rms(ca.reshape(37, 3, -1), cb.reshape(37, 3, -1), 4)
+    assert np.allclose(d, ref, rtol=2e-2, atol=1e-3 * ref.max())
+    a.close()
+    b.close()
