@@ -17,7 +17,9 @@ Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (closed forms, textbook forms, invariants, brute force); see the pin list in
 the design notes.  The JF12-type field model is defined by this project, so
 its absolute values are "parity unpinned" beyond the invariants those tests
-check.
+check.  The grid model's interpolation is pinned by exactness on multilinear
+fields, by scipy's linear grid interpolator and by node values
+(``tests/test_oracle_grid.py``).
 """
 from __future__ import annotations
 
@@ -33,8 +35,8 @@ _SRC = os.path.join(_HERE, "synax_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-MODEL_TOY, MODEL_WMAP, MODEL_JF12 = 0, 1, 2
-N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16}
+MODEL_TOY, MODEL_WMAP, MODEL_JF12, MODEL_GRID = 0, 1, 2, 3
+N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16, MODEL_GRID: 3}
 
 
 class _OracleProblem(ctypes.Structure):
@@ -51,6 +53,8 @@ class _OracleProblem(ctypes.Structure):
         ("n_theta", ctypes.c_int32),
         ("theta", ctypes.c_double * 32),
         ("rm_rule", ctypes.c_int32),
+        ("grid", ctypes.POINTER(ctypes.c_double)),
+        ("grid_n", ctypes.c_int32 * 3),
     ]
 
 
@@ -108,6 +112,10 @@ def _load():
             lib.oracle_fields_batch.restype = ctypes.c_int
             lib.oracle_ray_length.argtypes = [ctypes.POINTER(_OracleProblem), ctypes.c_int64]
             lib.oracle_ray_length.restype = ctypes.c_double
+            lib.oracle_grid_interp.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double)]
+            lib.oracle_grid_interp.restype = None
             _lib = lib
     return _lib
 
@@ -137,6 +145,14 @@ def _to_struct(prob) -> _OracleProblem:
     for k, x in enumerate(th):
         s.theta[k] = x
     s.rm_rule = int(getattr(prob, "rm_rule", 0))
+    grid = getattr(prob, "grid", None)
+    if grid is not None:
+        g = np.ascontiguousarray(np.asarray(grid, dtype=np.float64))
+        if g.ndim != 4 or g.shape[3] != 3 or min(g.shape[:3]) < 2:
+            raise ValueError("grid must be [nz][ny][nx][3] with every n >= 2")
+        s._grid_keepalive = g              # the struct points into this array
+        s.grid = g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        s.grid_n[0], s.grid_n[1], s.grid_n[2] = g.shape[2], g.shape[1], g.shape[0]
     return s
 
 
@@ -191,6 +207,17 @@ def los(nside: int, pix: int) -> dict:
 def ray_length(prob, pix: int) -> float:
     s = _to_struct(prob)
     return float(_load().oracle_ray_length(ctypes.byref(s), pix))
+
+
+def grid_interp(grid, box_kpc, r) -> np.ndarray:
+    """Trilinear B (uG) of a cell-centred grid [nz][ny][nx][3] over the box at r (kpc)."""
+    g = np.ascontiguousarray(np.asarray(grid, dtype=np.float64))
+    n = (ctypes.c_int32 * 3)(g.shape[2], g.shape[1], g.shape[0])
+    box = (ctypes.c_double * 3)(*[float(x) for x in box_kpc])
+    rr = (ctypes.c_double * 3)(*[float(x) for x in r])
+    B = (ctypes.c_double * 3)()
+    _load().oracle_grid_interp(g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, box, rr, B)
+    return np.array(B[:])
 
 
 def fields(prob, r, t: float = 0.0):

@@ -16,7 +16,8 @@
  *   2. the ray length L_i (fixed r_max, or exit from the box l_x,l_y,l_z
  *      centred on the Galactic centre, Sec. 2.3) and dr_i = L_i / N_int;
  *   3. midpoints r_{i,n} = r_obs + (n - 1/2) dr_i n_i, n = 1..N_int;
- *   4. B, N0, n_e at each midpoint (field models below);
+ *   4. B, N0, n_e at each midpoint (field models below: analytic, or B
+ *      interpolated trilinearly on a grid over the box);
  *   5. j_I (Eq. 2) and j_P (Eq. 5) literally, in cgs, with B_trans the norm
  *      of the component of B transverse to n_i;
  *   6. chi_0 from Eq. 8 (denominator read as B.e_l, see the design notes);
@@ -55,6 +56,7 @@
 #define OR_MODEL_TOY  0
 #define OR_MODEL_WMAP 1
 #define OR_MODEL_JF12 2
+#define OR_MODEL_GRID 3
 
 #define OR_MAX_FREQ  16
 #define OR_MAX_THETA 32
@@ -72,6 +74,8 @@ typedef struct {
     int32_t n_theta;
     double  theta[OR_MAX_THETA];
     int32_t rm_rule;                /* 0 half-cell, 1 exclusive, 2 inclusive */
+    const double* grid;             /* grid model: B at cell centres, [nz][ny][nx][3] uG */
+    int32_t grid_n[3];              /* (nx, ny, nz), each >= 2 */
 } oracle_problem;
 
 /* ======================================================================
@@ -296,11 +300,58 @@ static void field_jf12(const double* th, const double r[3], const double obs[3],
         + 0.10 * exp(-rho / 4.0) * exp(-fabs(z) / th[15]);
 }
 
+/* Grid model (Sec. 2.3: a field given on a regular 3D grid over the box and
+ * found at the midpoints by 3D linear interpolation; Sec. 3.3 optimises such
+ * a B grid).  The nodes span the box wall to wall: node i of n_x along x sits
+ * at x_i = -l_x/2 + i l_x / (n_x - 1), likewise y and z, so every point of the
+ * box lies inside the node hull.  A point's fractional node coordinate
+ * u = (x + l_x/2) (n_x - 1) / l_x is clamped to [0, n_x - 1] (which only
+ * matters for points on or beyond a wall), and B is the trilinear blend of the
+ * 8 nodes around it.  theta = [N0_obs (cm^-3), p, ne0 (cm^-3)]: CR density as
+ * in the WMAP-type model (cr_density), n_e = ne0 e^{-rho/20} sech^2(z/1). */
+static void grid_axis(double x, double l, int n, int* i0, double* f)
+{
+    double u = (x + 0.5 * l) * (n - 1) / l;
+    if (u < 0.0) u = 0.0;
+    if (u > n - 1) u = n - 1;
+    int i = (int)floor(u);
+    if (i > n - 2) i = n - 2;
+    *i0 = i;
+    *f = u - i;
+}
+
+void oracle_grid_interp(const double* grid, const int32_t n[3], const double box[3], const double r[3],
+                        double B[3])
+{
+    int i0, j0, k0;
+    double fx, fy, fz;
+    grid_axis(r[0], box[0], n[0], &i0, &fx);
+    grid_axis(r[1], box[1], n[1], &j0, &fy);
+    grid_axis(r[2], box[2], n[2], &k0, &fz);
+    for (int c = 0; c < 3; ++c) B[c] = 0.0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                double w = (di ? fx : 1.0 - fx) * (dj ? fy : 1.0 - fy) * (dk ? fz : 1.0 - fz);
+                size_t node = ((size_t)(k0 + dk) * n[1] + (size_t)(j0 + dj)) * n[0] + (size_t)(i0 + di);
+                for (int c = 0; c < 3; ++c) B[c] += w * grid[node * 3 + c];
+            }
+}
+
+static void field_grid(const oracle_problem* P, const double r[3], double B[3], double* N0, double* ne)
+{
+    oracle_grid_interp(P->grid, P->grid_n, P->box_kpc, r, B);
+    double rho = sqrt(r[0] * r[0] + r[1] * r[1]);
+    *N0 = cr_density(r, P->obs_kpc, P->theta[0]);
+    *ne = P->theta[2] * exp(-rho / 20.0) * sech2(r[2] / 1.0);
+}
+
 static double spectral_index(const oracle_problem* P)
 {
     switch (P->model_id) {
     case OR_MODEL_TOY:  return P->theta[5];
     case OR_MODEL_WMAP: return P->theta[6];
+    case OR_MODEL_GRID: return P->theta[1];
     default:            return P->theta[13];
     }
 }
@@ -313,6 +364,10 @@ int oracle_fields(const oracle_problem* P, const double r[3], double t,
     case OR_MODEL_TOY:  field_toy(P->theta, t, B, N0, ne); return 0;
     case OR_MODEL_WMAP: field_wmap(P->theta, r, P->obs_kpc, B, N0, ne); return 0;
     case OR_MODEL_JF12: field_jf12(P->theta, r, P->obs_kpc, B, N0, ne); return 0;
+    case OR_MODEL_GRID:
+        if (!P->grid) return -1;
+        field_grid(P, r, B, N0, ne);
+        return 0;
     default: return -1;
     }
 }
@@ -438,10 +493,16 @@ static int or_validate(const oracle_problem* P)
     if (P->nside < 1 || P->nside > 8192) return -1;
     if (P->n_steps < 1) return -1;
     if (P->n_freq < 1 || P->n_freq > OR_MAX_FREQ) return -1;
-    if (P->model_id < OR_MODEL_TOY || P->model_id > OR_MODEL_JF12) return -1;
-    static const int need[3] = {7, 8, 16};
+    if (P->model_id < OR_MODEL_TOY || P->model_id > OR_MODEL_GRID) return -1;
+    static const int need[4] = {7, 8, 16, 3};
     if (P->n_theta != need[P->model_id]) return -1;
     if (!P->box_clip && !(P->r_max_kpc > 0.0)) return -1;
+    if (P->model_id == OR_MODEL_GRID) {
+        /* the grid spans the box, so rays end at its walls */
+        if (!P->grid || !P->box_clip) return -1;
+        for (int a = 0; a < 3; ++a)
+            if (P->grid_n[a] < 2) return -1;
+    }
     if (P->rm_rule < 0 || P->rm_rule > 2) return -1;
     return 0;
 }

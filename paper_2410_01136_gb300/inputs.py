@@ -18,8 +18,8 @@ import math
 
 import numpy as np
 
-MODEL_TOY, MODEL_WMAP, MODEL_JF12 = 0, 1, 2
-N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16}
+MODEL_TOY, MODEL_WMAP, MODEL_JF12, MODEL_GRID = 0, 1, 2, 3
+N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16, MODEL_GRID: 3}
 
 #: Parameter names of each model, in theta order.
 THETA_NAMES = {
@@ -27,14 +27,16 @@ THETA_NAMES = {
     MODEL_WMAP: ["b0", "psi0", "psi1", "chi0B", "Bux", "N0_obs", "p", "ne0"],
     MODEL_JF12: [f"b{k + 1}" for k in range(8)]
     + ["B_h", "z_h", "B_X", "theta_X", "N0_obs", "p", "h1", "h2"],
+    MODEL_GRID: ["N0_obs", "p", "ne0"],
 }
 
 #: Index of the CR spectral index p in each model's theta.
-P_INDEX = {MODEL_TOY: 5, MODEL_WMAP: 6, MODEL_JF12: 13}
+P_INDEX = {MODEL_TOY: 5, MODEL_WMAP: 6, MODEL_JF12: 13, MODEL_GRID: 1}
 
 OBS_PAPER_KPC = (-8.3, 0.0, 0.006)      # Sec. 2.1
 OBS_CONFIG_KPC = (-8.5, 0.0, 0.015)     # synthetic workloads
 BOX_PAPER_KPC = (40.0, 40.0, 10.0)      # Sec. 2.4
+GRID_PAPER_N = (128, 128, 32)           # B grid nodes (nx, ny, nz), Sec. 3.3
 N0_EARTH = 4.0e-5                       # cm^-3, Sec. 3.1
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -97,7 +99,8 @@ class Problem:
     double maps.  pix_begin / pix_count: a contiguous RING pixel range
     (pix_count 0 = to the end of the map).  rm_rule: how much of a cell's
     own n_e B_LOS dr enters the RM at its midpoint: 0 half (default), 1 none,
-    2 all of it (a plain cumulative sum).
+    2 all of it (a plain cumulative sum).  grid: the grid model's B nodes,
+    [nz][ny][nx][3] in uG, spanning box_kpc wall to wall (grid model only).
     """
 
     nside: int
@@ -113,10 +116,15 @@ class Problem:
     pix_begin: int = 0
     pix_count: int = 0
     rm_rule: int = 0
+    grid: np.ndarray | None = None
 
     def __post_init__(self):
         self.theta = np.asarray(self.theta, dtype=np.float64).copy()
         self.freq_hz = tuple(float(f) for f in self.freq_hz)
+        if self.grid is not None:
+            self.grid = np.asarray(self.grid)
+            if self.grid.ndim != 4 or self.grid.shape[3] != 3 or min(self.grid.shape[:3]) < 2:
+                raise ValueError("grid must be [nz][ny][nx][3] with every n >= 2")
 
     @property
     def npix(self) -> int:
@@ -300,3 +308,42 @@ def mlp_init(widths=SURROGATE_WIDTHS, seed: int = 7) -> list[tuple[np.ndarray, n
         w = uniform(substream(seed, l + 1), fan_out * fan_in, -b, b).reshape(fan_out, fan_in)
         params.append((w.astype(np.float32), np.zeros(fan_out, dtype=np.float32)))
     return params
+
+
+# ---------------------------------------------------------------------------
+# grid model (B on a regular grid over the box, Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def grid_field(n=GRID_PAPER_N, seed: int = 21, n_modes: int = 8, amp_ug: float = 4.0) -> np.ndarray:
+    """A seeded smooth vector field on an (nx, ny, nz) node lattice, returned
+    as [nz][ny][nx][3] float64 (uG): a sum of n_modes plane waves over the node
+    indices, B_c[k, j, i] = sum_m a_mc cos(2 pi (kx_m i / nx + ky_m j / ny +
+    kz_m k / nz) + phi_m), wave numbers integers in [-3, 3], a_mc ~ N(0,
+    amp^2 / n_modes), phi_m ~ U[0, 2 pi)."""
+    nx, ny, nz = (int(v) for v in n)
+    waves = (splitmix64(substream(seed, 1), 3 * n_modes) % np.uint64(7)).astype(np.int64).reshape(n_modes, 3) - 3
+    amps = (amp_ug / math.sqrt(n_modes)) * normal(substream(seed, 2), 3 * n_modes).reshape(n_modes, 3)
+    phases = uniform(substream(seed, 3), n_modes, 0.0, 2.0 * math.pi)
+    i = np.arange(nx, dtype=np.float64)[None, None, :] / nx
+    j = np.arange(ny, dtype=np.float64)[None, :, None] / ny
+    k = np.arange(nz, dtype=np.float64)[:, None, None] / nz
+    out = np.zeros((nz, ny, nx, 3), dtype=np.float64)
+    for m in range(n_modes):
+        wave = np.cos(2.0 * math.pi * (waves[m, 0] * i + waves[m, 1] * j + waves[m, 2] * k) + phases[m])
+        out += wave[..., None] * amps[m][None, None, None, :]
+    return out
+
+
+def grid_theta(N0_obs: float = N0_EARTH, p: float = 3.0, ne0: float = 0.03) -> np.ndarray:
+    """Grid-model parameters [N0_obs (cm^-3), p, ne0 (cm^-3)]."""
+    return np.array([N0_obs, p, ne0], dtype=np.float64)
+
+
+def grid_problem(nside: int = 64, n_steps: int = 512, freq_hz=(2.4e9,), n=GRID_PAPER_N, seed: int = 21,
+                 **kw) -> Problem:
+    """The grid optimisation workload (Sec. 3.3): Nside 64, 512 steps to the
+    walls of the (40, 40, 10) kpc box, Q/U at 2.4 GHz, B on 128 x 128 x 32
+    nodes (grid_field(seed)), analytic CR and thermal electrons."""
+    return Problem(nside=nside, n_steps=n_steps, freq_hz=freq_hz, model_id=MODEL_GRID,
+                   theta=kw.pop("theta", grid_theta()), box_clip=True, grid=kw.pop("grid", grid_field(n, seed)),
+                   **kw)
