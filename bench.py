@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--impl", default="synax", choices=["synax", "reference"])
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-set ensemble measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the CPU oracle")
+    ap.add_argument("--no-grid", action="store_true", help="skip the grid-model (Sec. 3.3) measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the learned surrogate")
     ap.add_argument("--surrogate-steps", type=int, default=20000, help="Adam steps of the surrogate training")
     ap.add_argument("--surrogate-maps", type=int, default=50000, help="training maps of the surrogate")
@@ -242,6 +243,64 @@ def bench_batch(sx, inputs, torch, dev, n_runs: int = 3, sets=None, name=None) -
         "sequential_maps_grad_per_s": len(sets) / (ms_seq * 1e-3),
         "speedup_vs_sequential": ms_seq / ms_batch,
         "plan": info,
+    }
+
+
+def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
+    """The field-level workload (Sec. 3.3): B on 128 x 128 x 32 nodes over the
+    (40, 40, 10) kpc box, Nside 64, 512 steps to the walls, Q/U at 2.4 GHz;
+    one step = synax_adjoint_grid in chi^2 mode (maps, chi^2 against a mock
+    from another seeded grid plus 1 mK noise, theta gradient and the
+    1.57-million-value grid gradient).  L2 flushed between steps."""
+    import numpy as np
+    prob = inputs.grid_problem()
+    grid = torch.tensor(np.asarray(prob.grid), dtype=torch.float32, device=dev)
+    prob = prob.replace(grid=grid)
+    mock = sx.forward(inputs.grid_problem(seed=22).replace(grid=torch.tensor(
+        inputs.grid_field(seed=22), dtype=torch.float32, device=dev)))
+    target = (mock + 1e-3 * torch.tensor(inputs.target_noise(tuple(mock.shape), seed=23, sigma=1.0),
+                                         dtype=torch.float32, device=dev)).contiguous()
+    maps = torch.empty_like(target)
+    gg = torch.empty_like(grid)
+    ws = torch.empty(max(sx.adjoint_workspace_bytes(prob), 1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return sx.adjoint_grid(prob, target=target, sigma=1e-3, maps_out=maps, grid_grad=gg, workspace=ws)
+
+    for _ in range(3):
+        step()
+        sx.forward(prob, out=maps)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_runs)]
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_runs)]
+    for k in range(n_runs):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    for k in range(n_runs):
+        flush.fill_(float(k))
+        fev[k][0].record(stream)
+        sx.forward(prob, out=maps)
+        fev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms_fwd = float(np.mean([a.elapsed_time(b) for a, b in fev]))
+    samples = prob.samples
+    return {
+        "workload": "grid B 128x128x32 over (40, 40, 10) kpc, Nside 64, 512 steps to the box, 2.4 GHz, "
+                    "chi^2 map + theta gradient + grid gradient",
+        "samples_per_step": samples,
+        "grid_values": int(grid.numel()),
+        "ms_per_step": ms,
+        "samples_per_s": samples / (ms * 1e-3),
+        "maps_grad_per_s": 1.0 / (ms * 1e-3),
+        "forward_ms": ms_fwd,
+        "forward_samples_per_s": samples / (ms_fwd * 1e-3),
+        "gpu_launches_per_step": 2,      # k_adjoint + k_reduce_partials (plus a memset of the grid gradient)
+        "l2": "flushed between steps (256 MiB write); the 6.3 MB grid is re-read from HBM",
     }
 
 
@@ -537,6 +596,8 @@ def run_synax(args):
         out["batch_low_res"] = bench_batch(sx, inputs, torch, dev, n_runs=20, sets=chains,
                                            name="256 chains, Nside 16, 256 steps, chi^2 map+gradient")
         out["gpu_launches_batch_per_run"] = 2
+    if rank == 0 and not args.no_grid:
+        out["grid"] = bench_grid(sx, inputs, torch, dev)
     if rank == 0 and not args.no_surrogate:
         peaks = {}
         try:

@@ -57,11 +57,19 @@ extern "C" {
  * SYNAX_MODEL_JF12 (JF12-type: 8 smooth log-spiral arms, toroidal halo, X field)
  *   theta = [b1..b8 (uG), B_h (uG), z_h (kpc), B_X (uG), theta_X (rad),
  *            N0_obs (cm^-3), p, h1 (kpc), h2 (kpc)].
+ * SYNAX_MODEL_GRID (Sec. 2.3 grid field generator; the B grid of Sec. 3.3)
+ *   theta = [N0_obs (cm^-3), p, ne0 (cm^-3)]; B is read from the problem's
+ *   grid (grid_dev, grid_n): nodes spanning the box wall to wall, node
+ *   (i, j, k) at (-l_x/2 + i l_x/(n_x - 1), -l_y/2 + j l_y/(n_y - 1),
+ *   -l_z/2 + k l_z/(n_z - 1)), B at a midpoint the trilinear blend of the 8
+ *   nodes of its cell (fractional node coordinates clamped to the grid);
+ *   N0 and n_e are the WMAP-type model's.  Needs SYNAX_BOX_CLIP.
  * N0_obs is the CR density at the observer; p is the CR spectral index
  * (the paper's alpha). */
 #define SYNAX_MODEL_TOY   0
 #define SYNAX_MODEL_WMAP  1
 #define SYNAX_MODEL_JF12  2
+#define SYNAX_MODEL_GRID  3
 
 #define SYNAX_MAX_FREQ   16
 #define SYNAX_MAX_THETA  32
@@ -87,6 +95,12 @@ typedef struct synax_problem {
                                      0 half (default), 1 none, 2 all */
     int64_t  pix_begin;           /* first RING pixel marched, >= 0 */
     int64_t  pix_count;           /* pixels marched; 0 = to the end of the map */
+    const void* grid_dev;         /* SYNAX_MODEL_GRID only: B at the nodes, device
+                                     memory [n_z][n_y][n_x][3] in uG, float32
+                                     (float64 with SYNAX_F64), read during the
+                                     enqueued work; ignored by the other models */
+    int32_t  grid_n[3];           /* (n_x, n_y, n_z), each >= 2, 3 n_x n_y n_z < 2^31 */
+    int32_t  reserved;            /* must be 0 */
 } synax_problem;
 
 /* Forward march (Sec. 2.3, Eq. 2 and 5-9).
@@ -100,7 +114,8 @@ int synax_adjoint_workspace_bytes(const synax_problem* prob, size_t* bytes);
 /* Adjoint (reverse-mode) march: the gradient of a scalar of the maps with
  * respect to theta, computed by recomputing each ray from theta (no per-step
  * storage) and marching it backwards for the RM adjoint (Eq. 7 is a prefix
- * sum along the ray, so its adjoint is a suffix sum).  Models: WMAP, JF12.
+ * sum along the ray, so its adjoint is a suffix sum).  Models: WMAP, JF12,
+ * GRID (its 3 parameters; synax_adjoint_grid adds the grid gradient).
  *
  * Two modes:
  *  - VJP mode, gmaps_dev != NULL: grad = sum_{f,s,i} gmaps[f][s][i] dM[f][s][i]/dtheta.
@@ -118,6 +133,19 @@ int synax_adjoint_workspace_bytes(const synax_problem* prob, size_t* bytes);
 int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
                   double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
                   void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Adjoint of the grid model (SYNAX_MODEL_GRID, the field-level optimisation
+ * of Sec. 3.3): synax_adjoint (same modes, arguments and workspace) plus the
+ * gradient with respect to every grid value, written to grid_grad_dev, laid
+ * out like the grid ([n_z][n_y][n_x][3], float32, float64 with SYNAX_F64,
+ * overwritten).  Each sample's adjoint of B is scattered into the 8 nodes of
+ * its cell with the trilinear weights; a lane sums consecutive samples of one
+ * cell in registers and adds them with atomic adds when it leaves the cell,
+ * so the grid gradient is not bitwise reproducible (the theta gradient is).
+ * Other models: SYNAX_ENOTSUP. */
+int synax_adjoint_grid(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
+                       double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
+                       void* grid_grad_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* ---- persistent batch: many parameter sets in one launch ----
  * An ensemble of map+gradient evaluations (e.g. the chains of an HMC

@@ -18,7 +18,7 @@ from . import inputs
 from . import _native
 from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
 
-__all__ = ["forward", "adjoint", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
+__all__ = ["forward", "adjoint", "adjoint_grid", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
            "SynaxError"]
 
 
@@ -124,6 +124,50 @@ def adjoint(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=None, wo
     if target is not None:
         return grad, chi2
     return grad
+
+
+def adjoint_grid(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=None, grid_grad=None,
+                 workspace=None, stream=None):
+    """Grid model (Sec. 3.3): the gradient with respect to theta = [N0_obs, p,
+    ne0] and to every grid value.  Modes as in ``adjoint``; returns
+    (grad, grid_grad) in VJP mode and (grad, grid_grad, chi2) in chi^2 mode,
+    grid_grad a CUDA tensor shaped like the grid ([nz, ny, nx, 3]).  The
+    grid gradient is summed with atomic adds (not bitwise reproducible)."""
+    torch = _torch()
+    if (gmaps is None) == (target is None):
+        raise ValueError("give exactly one of gmaps (VJP mode) or target (chi^2 mode)")
+    if getattr(prob, "grid", None) is None:
+        raise ValueError("adjoint_grid needs a grid-model problem")
+    seed = gmaps if gmaps is not None else target
+    _check_map_tensor(torch, seed, prob, "gmaps" if gmaps is not None else "target")
+    if maps_out is not None:
+        _check_map_tensor(torch, maps_out, prob, "maps_out")
+    s = problem_struct(prob)
+    shape = (s.grid_n[2], s.grid_n[1], s.grid_n[0], 3)
+    if grid_grad is None:
+        grid_grad = torch.empty(shape, dtype=_map_dtype(torch, prob), device="cuda")
+    elif (not grid_grad.is_cuda or grid_grad.dtype != _map_dtype(torch, prob)
+          or tuple(grid_grad.shape) != shape or not grid_grad.is_contiguous()):
+        raise ValueError(f"grid_grad must be a contiguous CUDA {_map_dtype(torch, prob)} tensor of shape {shape}")
+    nbytes = adjoint_workspace_bytes(prob)
+    if workspace is None:
+        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    grad = torch.empty(len(prob.theta), dtype=torch.float64, device="cuda")
+    chi2 = torch.empty(1, dtype=torch.float64, device="cuda") if target is not None else None
+    check(lib().synax_adjoint_grid(
+        ctypes.byref(s),
+        ctypes.c_void_p(gmaps.data_ptr() if gmaps is not None else 0),
+        ctypes.c_void_p(target.data_ptr() if target is not None else 0),
+        ctypes.c_double(float(sigma)),
+        ctypes.c_void_p(grad.data_ptr()),
+        ctypes.c_void_p(chi2.data_ptr() if chi2 is not None else 0),
+        ctypes.c_void_p(maps_out.data_ptr() if maps_out is not None else 0),
+        ctypes.c_void_p(grid_grad.data_ptr()),
+        ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+        _stream_handle(torch, stream)), "synax_adjoint_grid")
+    if target is not None:
+        return grad, grid_grad, chi2
+    return grad, grid_grad
 
 
 class BatchPlan:

@@ -52,6 +52,9 @@ class SynaxProblem(ctypes.Structure):
         ("rm_rule", ctypes.c_int32),
         ("pix_begin", ctypes.c_int64),
         ("pix_count", ctypes.c_int64),
+        ("grid_dev", ctypes.c_void_p),
+        ("grid_n", ctypes.c_int32 * 3),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -81,6 +84,10 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                      ctypes.c_void_p]),
+    "synax_adjoint_grid": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.c_void_p]),
     "synax_adjoint_noalloc": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -185,4 +192,30 @@ def problem_struct(prob) -> SynaxProblem:
     s.rm_rule = int(getattr(prob, "rm_rule", 0))
     s.pix_begin = int(getattr(prob, "pix_begin", 0))
     s.pix_count = int(getattr(prob, "pix_count", 0))
+    grid = getattr(prob, "grid", None)
+    if grid is not None:
+        t = grid_device(prob)
+        s.grid_dev = t.data_ptr()
+        s.grid_n[0], s.grid_n[1], s.grid_n[2] = int(t.shape[2]), int(t.shape[1]), int(t.shape[0])
     return s
+
+
+def grid_device(prob):
+    """The grid model's node array on the current CUDA device in the march
+    precision.  A device tensor is used as it is (it must be contiguous, of
+    that dtype, [nz][ny][nx][3]); a host array is copied once and the copy is
+    kept on the problem object (host grids of a Problem are read-only)."""
+    import torch
+    g = prob.grid
+    dt = torch.float64 if getattr(prob, "f64", False) else torch.float32
+    if isinstance(g, torch.Tensor):
+        if not g.is_cuda or g.dtype != dt or not g.is_contiguous() or g.ndim != 4 or g.shape[3] != 3:
+            raise ValueError(f"a device grid must be a contiguous CUDA {dt} tensor of shape [nz, ny, nx, 3]")
+        return g
+    key = (id(g), dt, torch.cuda.current_device())
+    cached = getattr(prob, "_grid_device_copy", None)
+    if cached is None or cached[0] != key:
+        t = torch.as_tensor(g).to(device="cuda", dtype=dt).contiguous()
+        cached = (key, t)
+        object.__setattr__(prob, "_grid_device_copy", cached)
+    return cached[1]

@@ -39,6 +39,7 @@ int model_n_theta(int id) {
     case SYNAX_MODEL_TOY: return 7;
     case SYNAX_MODEL_WMAP: return 8;
     case SYNAX_MODEL_JF12: return 16;
+    case SYNAX_MODEL_GRID: return 3;
     default: return -1;
     }
 }
@@ -47,6 +48,7 @@ int model_p_index(int id) {
     switch (id) {
     case SYNAX_MODEL_TOY: return 5;
     case SYNAX_MODEL_WMAP: return 6;
+    case SYNAX_MODEL_GRID: return 1;
     default: return 13;
     }
 }
@@ -119,6 +121,18 @@ int validate_problem(const synax_problem* P, long long* n_pix) {
         if (!(P->theta[9] > 0.0) || !(P->theta[14] > 0.0) || !(P->theta[15] > 0.0)) return SYNAX_EINVAL;
         if (!(P->theta[11] > 0.0 && P->theta[11] < 0.5 * kPiD)) return SYNAX_EINVAL;
     }
+    if (P->reserved != 0) return SYNAX_EINVAL;
+    if (P->model_id == SYNAX_MODEL_GRID) {
+        // the grid spans the box, so rays must end at its walls
+        if (!(P->flags & SYNAX_BOX_CLIP) || !P->grid_dev) return SYNAX_EINVAL;
+        long long nodes = 1;
+        for (int k = 0; k < 3; ++k) {
+            // node counts stay exact in FP32 (cell indices are formed there)
+            if (P->grid_n[k] < 2 || P->grid_n[k] > (1 << 24)) return SYNAX_EINVAL;
+            nodes *= P->grid_n[k];
+            if (3 * nodes >= (1LL << 31)) return SYNAX_EINVAL;
+        }
+    }
     const long long npix = 12LL * P->nside * P->nside;
     if (P->pix_begin < 0 || P->pix_begin > npix || P->pix_count < 0) return SYNAX_EINVAL;
     const long long count = P->pix_count ? P->pix_count : npix - P->pix_begin;
@@ -175,6 +189,11 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         M.obs[k] = R(P.obs_kpc[k]);
         M.obs_lo[k] = R(P.obs_kpc[k] - (double)R(P.obs_kpc[k]));
         M.box_half[k] = R(0.5 * P.box_kpc[k]);
+        for (int side = 0; side < 2; ++side) {
+            const double d = (side ? -0.5 : 0.5) * P.box_kpc[k] - P.obs_kpc[k];
+            M.box_d[side][k] = R(d);
+            M.box_dlo[side][k] = R(d - (double)R(d));
+        }
     }
     const double dr = P.r_max_kpc / P.n_steps;
     M.r_max = R(P.r_max_kpc);
@@ -234,6 +253,21 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         M.m[mc::J_IH1_SQ] = R(1.0 / (th[14] * th[14]));
         M.m[mc::J_IH2_SQ] = R(1.0 / (th[15] * th[15]));
         break;
+    case SYNAX_MODEL_GRID:
+        M.m[mc::G_N0U] = R(1.0 / cr_profile(P.obs_kpc));
+        M.m[mc::G_N0OBS] = R(th[0]);
+        M.m[mc::G_NE0] = R(th[2]);
+        for (int a = 0; a < 3; ++a) {
+            const double n1 = (double)(P.grid_n[a] - 1);
+            const double sc = n1 / P.box_kpc[a];            // node spacings per kpc
+            M.m[mc::G_S + a] = R(sc);
+            M.m[mc::G_SLO + a] = R(sc - (double)R(sc));      // FP32: the scale as hi + lo
+            M.m[mc::G_O + a] = R(0.5 * n1);
+            M.m[mc::G_UMAX + a] = R(n1);
+            M.grid_n[a] = P.grid_n[a];
+        }
+        M.grid = (const R*)P.grid_dev;
+        break;
     default: break;
     }
 }
@@ -286,36 +320,45 @@ int synax_adjoint_workspace_bytes(const synax_problem* prob, size_t* bytes) {
     return SYNAX_OK;
 }
 
-int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
-                  double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
-                  void* workspace_dev, size_t workspace_bytes, void* stream) {
+// synax_adjoint and synax_adjoint_grid (grid_grad_dev non-null: grid model only).
+static int adjoint_impl(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
+                        double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
+                        void* grid_grad_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
     long long n_pix = 0;
     const int rc = validate_problem(prob, &n_pix);
     if (rc != SYNAX_OK) return rc;
     if (prob->model_id == SYNAX_MODEL_TOY) return SYNAX_ENOTSUP;
     if (!grad_dev) return SYNAX_EINVAL;
-    if (n_pix == 0) {
-        // Empty pixel range: the gradient (and chi^2) are zero whatever the mode.
-        cudaStream_t st = (cudaStream_t)stream;
-        cudaError_t err = cudaMemsetAsync(grad_dev, 0, sizeof(double) * prob->n_theta, st);
-        if (err == cudaSuccess && chi2_dev) err = cudaMemsetAsync(chi2_dev, 0, sizeof(double), st);
-        return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
-    }
     const bool chi2_mode = gmaps_dev == nullptr;
-    if (chi2_mode) {
+    if (n_pix > 0 && chi2_mode) {
         if (!target_dev) return SYNAX_EINVAL;
         if (!is_finite(sigma_K)) return SYNAX_ENONFINITE;
         if (!(sigma_K > 0.0)) return SYNAX_EINVAL;
     }
-    const size_t need = adjoint_workspace_bytes(n_pix, prob->n_theta);
+    const size_t need = n_pix > 0 ? adjoint_workspace_bytes(n_pix, prob->n_theta) : 0;
     if (workspace_bytes < need || (need > 0 && !workspace_dev)) return SYNAX_ESPACE;
-    if (prob->flags & SYNAX_F64) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool f64 = (prob->flags & SYNAX_F64) != 0;
+    if (grid_grad_dev) {
+        // the kernels add into the node gradient: start from zero
+        const size_t nodes = (size_t)prob->grid_n[0] * prob->grid_n[1] * prob->grid_n[2];
+        const cudaError_t err = cudaMemsetAsync(grid_grad_dev, 0, 3 * nodes * (f64 ? 8 : 4), st);
+        if (err != cudaSuccess) return record_cuda_error((int)err);
+    }
+    if (n_pix == 0) {
+        // Empty pixel range: the gradient (and chi^2) are zero whatever the mode.
+        cudaError_t err = cudaMemsetAsync(grad_dev, 0, sizeof(double) * prob->n_theta, st);
+        if (err == cudaSuccess && chi2_dev) err = cudaMemsetAsync(chi2_dev, 0, sizeof(double), st);
+        return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
+    }
+    if (f64) {
         MapParams<double> M;
         AdjParams<double> A;
         fill_params<double>(*prob, n_pix, M);
         fill_adj<double>(*prob, A);
         A.mode_chi2 = chi2_mode ? 1 : 0;
         A.inv_sigma2 = chi2_mode ? 1.0 / (sigma_K * sigma_K) : 0.0;
+        A.grid_grad = (double*)grid_grad_dev;
         return launch_adjoint_f64(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
                                   maps_dev, workspace_dev, stream);
     }
@@ -325,8 +368,29 @@ int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* 
     fill_adj<float>(*prob, A);
     A.mode_chi2 = chi2_mode ? 1 : 0;
     A.inv_sigma2 = chi2_mode ? (float)(1.0 / (sigma_K * sigma_K)) : 0.0f;
+    A.grid_grad = (float*)grid_grad_dev;
     return launch_adjoint_f32(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
                               maps_dev, workspace_dev, stream);
+}
+
+int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
+                  double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
+                  void* workspace_dev, size_t workspace_bytes, void* stream) {
+    return adjoint_impl(prob, gmaps_dev, target_dev, sigma_K, grad_dev, chi2_dev, maps_dev, nullptr,
+                        workspace_dev, workspace_bytes, stream);
+}
+
+int synax_adjoint_grid(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
+                       double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
+                       void* grid_grad_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+    if (!prob) return SYNAX_EINVAL;
+    if (prob->model_id != SYNAX_MODEL_GRID) return SYNAX_ENOTSUP;
+    long long n_pix = 0;
+    const int rc = validate_problem(prob, &n_pix);
+    if (rc != SYNAX_OK) return rc;
+    if (!grid_grad_dev) return SYNAX_EINVAL;
+    return adjoint_impl(prob, gmaps_dev, target_dev, sigma_K, grad_dev, chi2_dev, maps_dev, grid_grad_dev,
+                        workspace_dev, workspace_bytes, stream);
 }
 
 int synax_eval_fields(const synax_problem* prob, const double* pos_dev, const double* t_dev,

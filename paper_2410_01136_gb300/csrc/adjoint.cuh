@@ -14,6 +14,9 @@ namespace synax {
 // share an SM: measured 5 % faster than 256 threads at 2 CTAs per SM.
 constexpr int kAdjThreads = 128;
 constexpr int kAdjMinBlocks = 5;
+// The grid model's reverse march holds its cell's trilinear coefficients and
+// node-gradient sums (48 registers): 4 CTAs per SM leave it 128 registers.
+template <int MODEL> constexpr int adj_min_blocks() { return MODEL == SYNAX_MODEL_GRID ? 4 : kAdjMinBlocks; }
 
 template <int MODEL> struct Grad;
 
@@ -80,6 +83,64 @@ template <> struct Grad<SYNAX_MODEL_WMAP> {
     }
 };
 
+// Grid model: theta = [N0_obs, p, ne0]; the node gradient goes through GridAcc.
+template <> struct Grad<SYNAX_MODEL_GRID> {
+    static constexpr int NT = 3;
+    static constexpr int P_INDEX = 1;
+    static constexpr int N_ARM_SLOTS = 1;
+    template <typename R>
+    static __device__ __forceinline__ void accum(const R* /*m*/, const FieldLocal<R>& L, R /*bxb*/, R /*byb*/,
+                                                 R /*bzb*/, R n0b, R neb, R* g, R* /*garm*/, int /*stride*/) {
+        g[0] += n0b * L.n0_unit;
+        g[2] += neb * L.ne_unit;
+    }
+};
+
+// Gradient of the grid values (grid model).  B at a sample is
+// sum_q w_q B_q over the 8 nodes q = (di, dj, dk) of its cell with the
+// trilinear weights w_q = prod (d ? f : 1 - f), so dL/dB_q += w_q dL/dB.  A
+// lane marches consecutive samples, which mostly share a cell: it sums the
+// cell's 24 node gradients in registers and adds them to the grid with
+// atomic adds when it enters another cell and at the end of its chunk.
+template <typename R>
+struct GridAcc {
+    int base;                 // node index of the cell's lower corner; -1: empty
+    R w[8][3];
+
+    __device__ __forceinline__ void flush(const MapParams<R>& P, R* gg) {
+        if (base < 0) return;
+        const long long sy = 3LL * P.grid_n[0], sz = sy * P.grid_n[1];
+        R* p = gg + 3LL * base;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const long long off = ((q & 1) ? 3 : 0) + ((q & 2) ? sy : 0) + ((q & 4) ? sz : 0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(p + off + c, w[q][c]);
+        }
+        base = -1;
+    }
+
+    __device__ __forceinline__ void add(const MapParams<R>& P, R* gg, const FieldLocal<R>& L, R bxb, R byb,
+                                        R bzb) {
+        if (L.gbase != base) {
+            flush(P, gg);
+            base = L.gbase;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w[q][0] = w[q][1] = w[q][2] = R(0);
+        }
+        const R gx[2] = {R(1) - L.gfx, L.gfx};
+        const R gy[2] = {R(1) - L.gfy, L.gfy};
+        const R gz[2] = {R(1) - L.gfz, L.gfz};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const R wq = gx[q & 1] * gy[(q >> 1) & 1] * gz[(q >> 2) & 1];
+            w[q][0] = fma(wq, bxb, w[q][0]);
+            w[q][1] = fma(wq, byb, w[q][1]);
+            w[q][2] = fma(wq, bzb, w[q][2]);
+        }
+    }
+};
+
 // Shared-memory scratch of one adjoint CTA.
 template <int MODEL, int NF, int LPR, typename R>
 struct AdjSmem {
@@ -132,7 +193,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
         ray_setup<R>(P, r_eff, L, nd, dr, dr_lo);
         PT cd[NF];
 #pragma unroll
-        for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale(P.crev[k], dr) : P.cdr[k];
+        for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale2(P.crev[k], dr, dr_lo) : P.cdr[k];
         const int N = P.n_steps;
         const int n0 = (int)(((long long)sub * N) / LPR);
         const int n1 = (int)(((long long)(sub + 1) * N) / LPR);
@@ -211,13 +272,19 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
             PT Q = Ph::add(O, S);                       // O + sum of f before sample n (after the update)
             ArmTracker<R> trk;
             if constexpr (MODEL == SYNAX_MODEL_JF12) trk.init(P, nd, n1 - 1, dr, dr_lo);
+            GridCell<R> gc;
+            GridAcc<R> gacc;
+            GridRay<R> gr;
+            gc.base = -1;
+            gacc.base = -1;
+            if constexpr (MODEL == SYNAX_MODEL_GRID) grid_ray_init<R>(P, L, nd, n0, dr, dr_lo, gr);
+            R* const gg = live ? A.grid_grad : nullptr;  // idle segments scatter nothing
             const R q = P.q;
             R nh = R(n1 - 1) + R(0.5);                  // n + 1/2, exact
             for (int n = n1 - 1; n >= n0; --n, nh -= R(1)) {
                 const R t = fma(nh, dr, nh * dr_lo);
-                const R x = P.obs[0] + t * L.n[0];
-                const R y = P.obs[1] + t * L.n[1];
-                const R z = P.obs[2] + t * L.n[2];
+                R x, y, z;
+                sample_pos<MODEL, R>(P, L, nd, t, x, y, z);
                 R B[3], N0, ne;
                 ArmCoord<R> ac{0, R(0)};
                 if constexpr (MODEL == SYNAX_MODEL_JF12) {
@@ -225,7 +292,13 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                     else ac = trk.coord(x, y, F::sqrt(x * x + y * y));
                 }
                 FieldLocal<R> loc;
-                Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
+                if constexpr (MODEL == SYNAX_MODEL_GRID) {
+                    R fx, fy, fz;
+                    const int base = grid_locate_ray<R>(P, gr, n, fx, fy, fz);
+                    grid_eval<R>(P, gc, base, fx, fy, fz, x, y, z, B, N0, ne, loc);
+                } else {
+                    Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
+                }
 
                 R bn, bb;
                 dot_n_eb<R>(B, L, bn, bb);
@@ -246,7 +319,9 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                     pc = nw * (ba * ba - bb * bb);
                     ps = nw * (R(2) * ba * bb);
                 }
-                const R f = -ne * bn;
+                R f = -ne * bn;
+                // as in the forward march (same operations, same rounding)
+                if constexpr (MODEL == SYNAX_MODEL_GRID && sizeof(R) == 4) f -= ne * bpar_lo(B, nd);
 
                 // Q <- Q - f (the RM before sample n) and s_n = that + w f,
                 // formed from the same Q as Q + (w - 1) f (exact factor)
@@ -369,7 +444,13 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 const R bzb = bbar * L.eb[2] + bnb * L.n[2];
                 g[Grad<MODEL>::P_INDEX] += pbar;
                 Grad<MODEL>::accum(P.m, loc, bxb, byb, bzb, n0bar, neb, g, garm, kAdjThreads);
+                if constexpr (MODEL == SYNAX_MODEL_GRID) {
+                    if (gg) gacc.add(P, gg, loc, bxb, byb, bzb);
+                }
                 if constexpr (MODEL == SYNAX_MODEL_JF12) trk.step(-1);   // to the previous sample
+            }
+            if constexpr (MODEL == SYNAX_MODEL_GRID) {
+                if (gg) gacc.flush(P, gg);
             }
         }
         if constexpr (NSLOT > 1) {
@@ -411,7 +492,7 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, long long 
                                   int n_theta, double* __restrict__ grad, double* __restrict__ chi2);
 
 template <int MODEL, int NF, int LPR, typename R>
-__global__ void __launch_bounds__(kAdjThreads, kAdjMinBlocks)
+__global__ void __launch_bounds__(kAdjThreads, adj_min_blocks<MODEL>())
 k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmaps,
           const R* __restrict__ target, R* __restrict__ maps_out, double* __restrict__ partial) {
     __shared__ AdjSmem<MODEL, NF, LPR, R> sm;

@@ -21,7 +21,15 @@ k_eval_fields(const MapParams<R> P, const double* __restrict__ pos, const double
     const R x = R(pos[3 * i]), y = R(pos[3 * i + 1]), z = R(pos[3 * i + 2]);
     const ArmCoord<R> ac = arm_coord_direct<R>(x, y, M<R>::sqrt(x * x + y * y));
     FieldLocal<R> loc;
-    Model<MODEL>::eval(P.m, s_arms, R(tdist[i]), x, y, z, ac, B, N0, ne, loc);
+    if constexpr (MODEL == SYNAX_MODEL_GRID) {
+        GridCell<R> gc;
+        gc.base = -1;
+        R fx, fy, fz;
+        const int base = grid_locate<R>(P, x, y, z, fx, fy, fz);
+        grid_eval<R>(P, gc, base, fx, fy, fz, x, y, z, B, N0, ne, loc);
+    } else {
+        Model<MODEL>::eval(P.m, s_arms, R(tdist[i]), x, y, z, ac, B, N0, ne, loc);
+    }
     out[5 * i + 0] = (double)B[0];
     out[5 * i + 1] = (double)B[1];
     out[5 * i + 2] = (double)B[2];
@@ -37,6 +45,7 @@ static int launch_eval_t(const MapParams<R>& P, const double* pos, const double*
     case SYNAX_MODEL_TOY: k_eval_fields<SYNAX_MODEL_TOY, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out); break;
     case SYNAX_MODEL_WMAP: k_eval_fields<SYNAX_MODEL_WMAP, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out); break;
     case SYNAX_MODEL_JF12: k_eval_fields<SYNAX_MODEL_JF12, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out); break;
+    case SYNAX_MODEL_GRID: k_eval_fields<SYNAX_MODEL_GRID, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out); break;
     default: return SYNAX_EINVAL;
     }
     const cudaError_t err = cudaGetLastError();

@@ -66,7 +66,7 @@ k_forward(const MapParams<R> P, R* __restrict__ maps) {
         ray_setup<R>(P, r_eff, L, nd, dr, dr_lo);
         PT cd[NF];
 #pragma unroll
-        for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale(P.crev[k], dr) : P.cdr[k];
+        for (int k = 0; k < NF; ++k) cd[k] = P.box_clip ? Ph::scale2(P.crev[k], dr, dr_lo) : P.cdr[k];
 
         const int N = P.n_steps;
         const int n0 = (int)(((long long)sub * N) / LPR);

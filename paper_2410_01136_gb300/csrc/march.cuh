@@ -6,7 +6,7 @@
 //   * double-float arithmetic (Dekker/Knuth TwoSum, FMA-based products) for
 //     the running RM sum and the Faraday phase, PhaseOps<R>;
 //   * HEALPix RING pixel centres (Gorski et al. 2005) -> LOS triad n, e_l, e_b;
-//   * the three field models (toy, WMAP-type, JF12-type);
+//   * the field models (toy, WMAP-type, JF12-type, trilinear grid);
 //   * the per-sample emissivity terms of Eq. 2, 5, 8 and the RM integrand of Eq. 7.
 // The FP32 path folds all physical constants into host-computed per-frequency
 // prefactors so that every transcendental argument is O(1): B in uG,
@@ -175,6 +175,14 @@ template <> struct PhaseOps<float> {
         e = fmaf(c.lo, d, e);
         return fast_two_sum(p, e);
     }
+    // c (d + d_lo) for a double-float d
+    static __device__ __forceinline__ T scale2(T c, float d, float d_lo) {
+        float p = c.hi * d;
+        float e = fmaf(c.hi, d, -p);
+        e = fmaf(c.lo, d, e);
+        e = fmaf(c.hi, d_lo, e);
+        return fast_two_sum(p, e);
+    }
     // Fractional part of c*s (revolutions), in [-1/2, 1/2] up to rounding.
     // The product is formed exactly to ~2^-46 relative (TwoProd), the
     // integer part is removed exactly (|hi| < 2^22), then the low parts added.
@@ -238,6 +246,7 @@ template <> struct PhaseOps<double> {
     static __device__ __forceinline__ T zero() { return 0.0; }
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
     static __device__ __forceinline__ T scale(T c, double d) { return c * d; }
+    static __device__ __forceinline__ T scale2(T c, double d, double d_lo) { return c * (d + d_lo); }
     static __device__ __forceinline__ double frac_mul(T c, T s) {
         double x = c * s;
         return x - rint(x);
@@ -416,6 +425,29 @@ __device__ __forceinline__ R box_exit(const R o[3], const R h[3], const R n[3]) 
         else if (n[k] < R(0)) t = M<R>::min(t, (-h[k] - o[k]) / n[k]);
     }
     return t;
+}
+
+// The same distance as a double-float for the FP32 march: per axis the FP32
+// quotient of the exit numerator (+h - o or -h - o, double-float from the
+// host) by the double-float direction, refined by one correction step (the
+// residual d - q n_hi of a rounded quotient is exact with an FMA), then the
+// smallest.  Without it the FP32 rounding of the ray length (up to 6e-8)
+// would scale every position and Faraday phase of the ray by the same factor.
+__device__ __forceinline__ ff box_exit_dd(const MapParams<float>& P, const ff nd[3]) {
+    ff best{1e30f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float nh = nd[k].hi;
+        if (nh != 0.0f) {
+            const int side = nh > 0.0f ? 0 : 1;
+            const float d = P.box_d[side][k], dlo = P.box_dlo[side][k];
+            const float q = __fdiv_rn(d, nh);
+            const float r = fmaf(-q, nd[k].lo, fmaf(-q, nh, d) + dlo);
+            const ff t = fast_two_sum(q, __fdiv_rn(r, nh));
+            if (t.hi < best.hi) best = t;
+        }
+    }
+    return best;
 }
 
 // ---------------------------------------------------------------------------
@@ -644,7 +676,10 @@ struct FieldLocal {
     R ne1, ne2;          // thick and thin n_e discs
     // both
     R n0_unit;           // N0 / N0_obs
-    R ne_unit;           // WMAP: n_e / ne0
+    R ne_unit;           // WMAP, grid: n_e / ne0
+    // grid
+    int gbase;           // node index of the cell's lower corner
+    R gfx, gfy, gfz;     // fractional position in the cell
 };
 
 template <int MODEL> struct Model;
@@ -793,6 +828,181 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         loc.ne1 = ne1; loc.ne2 = ne2; loc.n0_unit = n0u;
     }
 };
+
+// ---------------------------------------------------------------------------
+// Grid model (Sec. 2.3: a field given on a regular 3D grid over the box and
+// found at the midpoints by 3D linear interpolation; Sec. 3.3 optimises such
+// a B grid).  Nodes span the box wall to wall: node i of n along an axis of
+// length l sits at -l/2 + i l / (n - 1).  A point's fractional node
+// coordinate u = x (n - 1)/l + (n - 1)/2 is clamped to [0, n - 1]; its cell
+// is i0 = min(floor(u), n - 2) with f = u - i0 in [0, 1].
+//
+// Consecutive samples of a lane mostly share a cell (a 0.31 kpc cell holds
+// ~8 samples of a 512-step ray), so a lane caches its current cell as the
+// coefficients of the trilinear form
+//   B = a + b fx + c fy + d fz + e fx fy + f fx fz + g fy fz + h fx fy fz
+// (24 registers) and reloads the 8 nodes only when it enters a new cell.
+// N0 and n_e are the WMAP-type model's.
+template <typename R>
+struct GridCell {
+    int base;                 // node index of corner (i0, j0, k0); -1: none cached
+    R a[3], b[3], c[3], d[3], e[3], f[3], g[3], h[3];
+};
+
+// Cell and in-cell fraction of one axis from a cell-coordinate split into a
+// whole part cf (an integer-valued R) and a fraction f = v - floor(v):
+// clamping u = cf + f to [0, umax] and taking i0 = min(floor(u), umax - 1)
+// gives i0 = clamp(cf) with f = 0 below the grid and f = 1 at or above its
+// last node.  Every step stays in R and the index is converted only after
+// clamping, so it is in range whatever the inputs (NaN included).
+template <typename R>
+__device__ __forceinline__ int grid_axis_split(R cf, R f, R umax, R& fout) {
+    f = cf < R(0) ? R(0) : f;
+    f = cf > umax - R(1) ? R(1) : f;
+    fout = f;
+    return (int)M<R>::min(M<R>::max(cf, R(0)), umax - R(1));
+}
+
+// Direct form for an arbitrary point: u = x (n - 1)/l + (n - 1)/2.
+template <typename R>
+__device__ __forceinline__ int grid_axis(R x, R s, R slo, R o, R umax, R& f) {
+    const R u = fma(x, s, fma(x, slo, o));
+    const R fl = M<R>::floor(u);
+    return grid_axis_split<R>(fl, u - fl, umax, f);
+}
+
+template <typename R>
+__device__ __forceinline__ int grid_locate(const MapParams<R>& P, R x, R y, R z, R& fx, R& fy, R& fz) {
+    const int i = grid_axis<R>(x, P.m[mc::G_S + 0], P.m[mc::G_SLO + 0], P.m[mc::G_O + 0], P.m[mc::G_UMAX + 0], fx);
+    const int j = grid_axis<R>(y, P.m[mc::G_S + 1], P.m[mc::G_SLO + 1], P.m[mc::G_O + 1], P.m[mc::G_UMAX + 1], fy);
+    const int k = grid_axis<R>(z, P.m[mc::G_S + 2], P.m[mc::G_SLO + 2], P.m[mc::G_O + 2], P.m[mc::G_UMAX + 2], fz);
+    return (k * P.grid_n[1] + j) * P.grid_n[0] + i;
+}
+
+// Cell coordinates along one lane's chunk of a ray.  Sample n sits at
+// u = u_a + (n - n_a) du per axis: u_a, the coordinate of the lane's first
+// sample n_a, is split into a whole part ia and a remainder a, and du (the
+// coordinate step s n dr) is kept as hi + lo.  Both are formed from the
+// double-float direction, step and observer, so the remainder plus the steps
+// taken, a number of at most a chunk's length in cells, is the only rounded
+// quantity: its error is ~ulp of a few cells instead of ulp(n - 1) plus the
+// FP32 rounding of the position.  Below 1 GHz the Faraday phase reaches
+// 10^3 rad, and a coordinate error of 1e-6 cell moves it by ~1e-4 rad on
+// grids whose nodes differ by a few uG.
+template <typename R>
+struct GridRay {
+    R ia[3], a[3], du[3], dulo[3];
+    int na;
+};
+
+template <typename R>
+__device__ __forceinline__ void grid_ray_init(const MapParams<R>& P, const Los<R>& L, const ff* nd, int na, R dr,
+                                              R dr_lo, GridRay<R>& g) {
+    g.na = na;
+    if constexpr (sizeof(R) == 4) {
+        const ff drd{dr, dr_lo};
+        const ff t = dd_mul_f(drd, (float)na + 0.5f);              // exact factor
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const ff sc{P.m[mc::G_S + k], P.m[mc::G_SLO + k]};
+            const ff pos = dd_add(ff{P.obs[k], P.obs_lo[k]}, dd_mul(t, nd[k]));
+            const ff u = dd_add_f(dd_mul(sc, pos), P.m[mc::G_O + k]);
+            const float fl = floorf(u.hi);
+            g.ia[k] = fl;
+            g.a[k] = (u.hi - fl) + u.lo;
+            const ff d = dd_mul(dd_mul(sc, nd[k]), drd);
+            g.du[k] = d.hi;
+            g.dulo[k] = d.lo;
+        }
+    } else {
+        const R t = (R(na) + R(0.5)) * dr;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const R u = fma(P.obs[k] + t * L.n[k], P.m[mc::G_S + k], P.m[mc::G_O + k]);
+            const R fl = M<R>::floor(u);
+            g.ia[k] = fl;
+            g.a[k] = u - fl;
+            g.du[k] = P.m[mc::G_S + k] * L.n[k] * dr;
+            g.dulo[k] = R(0);
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ int grid_locate_ray(const MapParams<R>& P, const GridRay<R>& g, int n, R& fx, R& fy,
+                                               R& fz) {
+    const R kf = R(n - g.na);
+    R fr[3];
+    int c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const R v = fma(kf, g.du[k], fma(kf, g.dulo[k], g.a[k]));
+        const R fl = M<R>::floor(v);
+        c[k] = grid_axis_split<R>(g.ia[k] + fl, v - fl, P.m[mc::G_UMAX + k], fr[k]);
+    }
+    fx = fr[0];
+    fy = fr[1];
+    fz = fr[2];
+    return (c[2] * P.grid_n[1] + c[1]) * P.grid_n[0] + c[0];
+}
+
+template <typename R>
+__device__ __forceinline__ void grid_load(const MapParams<R>& P, int base, GridCell<R>& gc) {
+    const long long sy = 3LL * P.grid_n[0], sz = sy * P.grid_n[1];
+    const R* p = P.grid + 3LL * base;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R v000 = __ldg(p + c), v100 = __ldg(p + 3 + c);
+        const R v010 = __ldg(p + sy + c), v110 = __ldg(p + sy + 3 + c);
+        const R v001 = __ldg(p + sz + c), v101 = __ldg(p + sz + 3 + c);
+        const R v011 = __ldg(p + sz + sy + c), v111 = __ldg(p + sz + sy + 3 + c);
+        const R bx0 = v100 - v000, bx1 = v110 - v010, bx2 = v101 - v001, bx3 = v111 - v011;
+        gc.a[c] = v000;
+        gc.b[c] = bx0;
+        gc.c[c] = v010 - v000;
+        gc.d[c] = v001 - v000;
+        gc.e[c] = bx1 - bx0;
+        gc.f[c] = bx2 - bx0;
+        gc.g[c] = (v011 - v001) - (v010 - v000);
+        gc.h[c] = (bx3 - bx2) - (bx1 - bx0);
+    }
+    gc.base = base;
+}
+
+// Trilinear blend at (fx, fy, fz) of the cached cell.
+template <typename R>
+__device__ __forceinline__ void grid_blend(const GridCell<R>& gc, R fx, R fy, R fz, R B[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R t3 = fma(fy, fma(fz, gc.h[c], gc.e[c]), fma(fz, gc.f[c], gc.b[c]));
+        const R t6 = fma(fy, fma(fz, gc.g[c], gc.c[c]), fma(fz, gc.d[c], gc.a[c]));
+        B[c] = fma(fx, t3, t6);
+    }
+}
+
+// Fields of the grid model at a sample in cell `base` with fractions
+// (fx, fy, fz) and position (x, y, z) (for N0 and n_e).
+template <typename R>
+__device__ __forceinline__ void grid_eval(const MapParams<R>& P, GridCell<R>& gc, int base, R fx, R fy, R fz,
+                                          R x, R y, R z, R B[3], R& N0, R& ne, FieldLocal<R>& loc) {
+    using F = M<R>;
+    if (base != gc.base) grid_load<R>(P, base, gc);
+    grid_blend<R>(gc, fx, fy, fz, B);
+    const R rho = F::sqrt(x * x + y * y);
+    const R az = F::abs(z);
+    const R e2 = F::exp(R(-2) * az);                          // e^{-2|z|}
+    const R inv1 = F::div(R(1), R(1) + e2);
+    const R n0u = cr_density<R>(P.m[mc::G_N0U], rho, az);
+    N0 = P.m[mc::G_N0OBS] * n0u;
+    const R neu = F::exp(-F::mulc(rho, 0.05)) * (R(4) * e2 * inv1 * inv1);
+    ne = P.m[mc::G_NE0] * neu;
+    loc.n0_unit = n0u;
+    loc.ne_unit = neu;
+    loc.gbase = base;
+    loc.gfx = fx;
+    loc.gfy = fy;
+    loc.gfz = fz;
+}
 
 // ---------------------------------------------------------------------------
 // Per-sample emission terms.  With a = B.e_l, b = B.e_b, B_perp^2 = a^2 + b^2
@@ -1040,6 +1250,35 @@ __device__ __forceinline__ void march_lane_pair_jf12(const MapParams<float>& P, 
     }
 }
 
+// Midpoint position at distance t.  The grid model (FP32) adds the low parts
+// of the double-float direction and observer: its trilinear field turns a
+// position error into a field error in proportion to the field's gradient,
+// and the FP32 rounding of the direction alone shifts the far end of a ray
+// by ~1e-6 kpc in one direction, a bias of the RM (Eq. 7) that is visible in
+// the Faraday rotation below 1 GHz.
+template <int MODEL, typename R>
+__device__ __forceinline__ void sample_pos(const MapParams<R>& P, const Los<R>& L, const ff* nd, R t, R& x, R& y,
+                                           R& z) {
+    if constexpr (MODEL == SYNAX_MODEL_GRID && sizeof(R) == 4) {
+        x = fmaf(t, L.n[0], P.obs[0]) + fmaf(t, nd[0].lo, P.obs_lo[0]);
+        y = fmaf(t, L.n[1], P.obs[1]) + fmaf(t, nd[1].lo, P.obs_lo[1]);
+        z = fmaf(t, L.n[2], P.obs[2]) + fmaf(t, nd[2].lo, P.obs_lo[2]);
+    } else {
+        x = P.obs[0] + t * L.n[0];
+        y = P.obs[1] + t * L.n[1];
+        z = P.obs[2] + t * L.n[2];
+    }
+}
+
+// B . n_lo, the part of B_LOS that the FP32 rounding of the direction drops.
+// The grid model adds it to the RM integrand: the rounding is the same for
+// every sample of a ray, so its RM error does not average out, and a field
+// that is strong out to the walls of the box carries it into the Faraday
+// phase below 1 GHz.
+__device__ __forceinline__ float bpar_lo(const float B[3], const ff* nd) {
+    return fmaf(B[0], nd[0].lo, fmaf(B[1], nd[1].lo, B[2] * nd[2].lo));
+}
+
 // One lane's share of the forward march of one ray (Sec. 2.3, Eq. 2, 5-9):
 // samples [n0, n1) of the ray with LOS triad L (and double-float direction
 // nd for the FP32 arm tracker).  Returns the lane's sum of j_I terms, per
@@ -1068,13 +1307,18 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
     if constexpr (MODEL == SYNAX_MODEL_JF12) {
         if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
     }
+    GridCell<R> gc;
+    GridRay<R> gr;
+    gc.base = -1;
+    if constexpr (MODEL == SYNAX_MODEL_GRID) {
+        if (n0 < n1) grid_ray_init<R>(P, L, nd, n0, dr, dr_lo, gr);
+    }
     R nh = R(n0) + R(0.5);                              // n + 1/2, exact
 #pragma unroll 2
     for (int n = n0; n < n1; ++n, nh += R(1)) {
         const R t = fma(nh, dr, nh * dr_lo);            // (n + 1/2) dr, dr as hi + lo
-        const R x = P.obs[0] + t * L.n[0];
-        const R y = P.obs[1] + t * L.n[1];
-        const R z = P.obs[2] + t * L.n[2];
+        R x, y, z;
+        sample_pos<MODEL, R>(P, L, nd, t, x, y, z);
         R B[3], N0, ne;
         ArmCoord<R> ac{0, R(0)};
         if constexpr (MODEL == SYNAX_MODEL_JF12) {
@@ -1083,8 +1327,15 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
             else ac = trk.coord(x, y, M<R>::sqrt(x * x + y * y));
         }
         FieldLocal<R> loc;
-        Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
-        const Emit<R> e = emit<R>(B, N0, ne, L, P.q);
+        if constexpr (MODEL == SYNAX_MODEL_GRID) {
+            R fx, fy, fz;
+            const int base = grid_locate_ray<R>(P, gr, n, fx, fy, fz);
+            grid_eval<R>(P, gc, base, fx, fy, fz, x, y, z, B, N0, ne, loc);
+        } else {
+            Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
+        }
+        Emit<R> e = emit<R>(B, N0, ne, L, P.q);
+        if constexpr (MODEL == SYNAX_MODEL_GRID && sizeof(R) == 4) e.f -= ne * bpar_lo(B, nd);
         accI += e.jI;
         PT s_n;                                        // RM at the midpoint (Eq. 7)
         if constexpr (sizeof(R) == 4) {
@@ -1137,10 +1388,24 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
 template <typename R>
 __device__ __forceinline__ void ray_setup(const MapParams<R>& P, long long ray, Los<R>& L, ff* nd, R& dr,
                                           R& dr_lo) {
-    if constexpr (sizeof(R) == 4) healpix_los_dd(P.nside, P.pix_begin + ray, L, nd);
-    else healpix_los<R>(P.nside, P.pix_begin + ray, L);
-    dr = P.box_clip ? box_exit<R>(P.obs, P.box_half, L.n) / R(P.n_steps) : P.dr;
-    dr_lo = P.box_clip ? R(0) : P.dr_lo;
+    if constexpr (sizeof(R) == 4) {
+        healpix_los_dd(P.nside, P.pix_begin + ray, L, nd);
+        if (P.box_clip) {
+            // dr = L / N as a double-float: the residual of the rounded
+            // quotient is exact with an FMA (N <= 65536 is exact in FP32)
+            const ff len = box_exit_dd(P, nd);
+            const float n = (float)P.n_steps;
+            dr = __fdiv_rn(len.hi, n);
+            dr_lo = __fdiv_rn(fmaf(-dr, n, len.hi) + len.lo, n);
+        } else {
+            dr = P.dr;
+            dr_lo = P.dr_lo;
+        }
+    } else {
+        healpix_los<R>(P.nside, P.pix_begin + ray, L);
+        dr = P.box_clip ? box_exit<R>(P.obs, P.box_half, L.n) / R(P.n_steps) : P.dr;
+        dr_lo = P.box_clip ? R(0) : P.dr_lo;
+    }
 }
 
 }  // namespace synax

@@ -39,6 +39,9 @@ constexpr int J_BH = 8, J_IZH = 9, J_BX = 10, J_COSX = 11, J_SINX = 12, J_COTX =
               J_N0N = 14, J_IH1 = 15, J_IH2 = 16, J_ZH = 17, J_THX = 18, J_H1 = 19, J_H2 = 20,
               J_N0OBS = 21, J_SIN2X = 22, J_N0U = 23, J_IZH_LO = 24, J_IH1_LO = 25, J_IH2_LO = 26,
               J_BH_IZH2 = 27, J_IH1_SQ = 28, J_IH2_SQ = 29;   // B_h / z_h^2, 1 / h1^2, 1 / h2^2 (gradients)
+// grid model: N0 normalisation, N0_obs, ne0; per axis (n - 1) / l (as hi + lo),
+// (n - 1) / 2 and n - 1
+constexpr int G_N0U = 0, G_N0OBS = 1, G_NE0 = 2, G_S = 3, G_O = 6, G_UMAX = 9, G_SLO = 12;
 }  // namespace mc
 
 template <typename R>
@@ -55,6 +58,8 @@ struct MapParams {
     R obs[3];
     R obs_lo[3];              // obs - (R)obs (FP32: observer as hi + lo)
     R box_half[3];
+    R box_d[2][3];            // +h - obs and -h - obs per axis (exit numerators), FP32: hi
+    R box_dlo[2][3];          // and lo parts
     R r_max;
     R dr;                     // r_max / n_steps (r_max mode), rounded
     R dr_lo;                  // r_max / n_steps - dr (FP32: keeps positions unbiased)
@@ -64,6 +69,8 @@ struct MapParams {
     Phase crev[SYNAX_MAX_FREQ];   // Faraday phase, revolutions per (cm^-3 uG kpc)
     Phase cdr[SYNAX_MAX_FREQ];    // crev * dr (r_max mode)
     R m[kModelConsts];
+    const R* grid;            // grid model: B nodes [nz][ny][nx][3] (uG), else null
+    int grid_n[3];            // (nx, ny, nz)
 };
 
 // Gradient-side constants (adjoint): d ln aI / dp and d ln aP / dp per
@@ -75,6 +82,7 @@ struct AdjParams {
     int n_theta;
     int mode_chi2;            // 1: seed = 2 (M - target) / sigma^2
     R inv_sigma2;
+    R* grid_grad;             // grid model: gradient of every node value (zeroed by the host), or null
 };
 
 // Host-side problem handling (abi.cu).

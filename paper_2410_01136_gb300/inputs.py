@@ -100,7 +100,9 @@ class Problem:
     (pix_count 0 = to the end of the map).  rm_rule: how much of a cell's
     own n_e B_LOS dr enters the RM at its midpoint: 0 half (default), 1 none,
     2 all of it (a plain cumulative sum).  grid: the grid model's B nodes,
-    [nz][ny][nx][3] in uG, spanning box_kpc wall to wall (grid model only).
+    [nz][ny][nx][3] in uG, spanning box_kpc wall to wall (grid model only):
+    a host array (kept as a read-only float64 copy) or a device tensor of the
+    march precision, used in place.
     """
 
     nside: int
@@ -122,8 +124,11 @@ class Problem:
         self.theta = np.asarray(self.theta, dtype=np.float64).copy()
         self.freq_hz = tuple(float(f) for f in self.freq_hz)
         if self.grid is not None:
-            self.grid = np.asarray(self.grid)
-            if self.grid.ndim != 4 or self.grid.shape[3] != 3 or min(self.grid.shape[:3]) < 2:
+            if not hasattr(self.grid, "data_ptr"):       # host array: a private, read-only copy
+                self.grid = np.array(self.grid, dtype=np.float64)
+                self.grid.setflags(write=False)
+            shape = tuple(self.grid.shape)
+            if len(shape) != 4 or shape[3] != 3 or min(shape[:3]) < 2:
                 raise ValueError("grid must be [nz][ny][nx][3] with every n >= 2")
 
     @property

@@ -139,6 +139,51 @@ def test_adjoint_validation(L):
                            1 << 30, None) == _native.SYNAX_ENOTSUP
 
 
+def _grid_struct():
+    """A grid-model problem struct with a dummy (never dereferenced) grid pointer."""
+    s = _native.problem_struct(inputs.config2().replace(nside=4, n_steps=64, box_clip=True))
+    s.model_id = inputs.MODEL_GRID
+    s.n_theta = 3
+    for k, v in enumerate(inputs.grid_theta()):
+        s.theta[k] = v
+    s.grid_dev = 16
+    s.grid_n[0], s.grid_n[1], s.grid_n[2] = 4, 4, 2
+    return s
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda s: setattr(s, "flags", 0),                          # the grid needs rays that end at the box
+    lambda s: setattr(s, "grid_dev", None),
+    lambda s: s.grid_n.__setitem__(0, 1),
+    lambda s: s.grid_n.__setitem__(2, 0),
+    lambda s: (s.grid_n.__setitem__(0, 2048), s.grid_n.__setitem__(1, 2048), s.grid_n.__setitem__(2, 256)),
+    lambda s: setattr(s, "reserved", 1),
+    lambda s: setattr(s, "n_theta", 8),
+    lambda s: s.theta.__setitem__(1, 0.2),                     # p
+])
+def test_grid_validation_rejects(L, mutate):
+    s = _grid_struct()
+    s.pix_begin = 192                                          # valid problems do nothing
+    assert L.synax_forward(ctypes.byref(s), None, None) == _native.SYNAX_OK
+    mutate(s)
+    assert L.synax_forward(ctypes.byref(s), ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
+
+
+def test_adjoint_grid_validation(L):
+    dummy = ctypes.c_void_p(16)
+    s = _native.problem_struct(good())
+    assert L.synax_adjoint_grid(ctypes.byref(s), dummy, None, 1.0, dummy, None, None, dummy, dummy,
+                                1 << 30, None) == _native.SYNAX_ENOTSUP
+    g = _grid_struct()
+    assert L.synax_adjoint_grid(ctypes.byref(g), dummy, None, 1.0, dummy, None, None, None, dummy,
+                                1 << 30, None) == _native.SYNAX_EINVAL
+    g.reserved = 2
+    assert L.synax_adjoint_grid(ctypes.byref(g), dummy, None, 1.0, dummy, None, None, dummy, dummy,
+                                1 << 30, None) == _native.SYNAX_EINVAL
+    assert L.synax_adjoint_grid(None, dummy, None, 1.0, dummy, None, None, dummy, dummy,
+                                1 << 30, None) == _native.SYNAX_EINVAL
+
+
 def test_version_and_strerror(L):
     assert L.synax_version() >= 100
     for code in range(-7, 1):

@@ -1,0 +1,226 @@
+"""The grid model on the GPU (B on a regular grid over the box, trilinear at
+the midpoints; Sec. 2.3, Sec. 3.3) against the FP64 oracle, through the C ABI.
+
+Maps: element-wise parity (I to 1e-5, P = Q + iU to 1e-4 relative) on seeded
+smooth grids, at small sizes with ragged pixel ranges and step counts, and on
+sampled pixels of the full Nside-64, 512-step, 128 x 128 x 32 workload.
+
+Below 1 GHz, FP32 holds P to 5e-4 on these grids: their field is strong out
+to the walls of the box, the Faraday phase reaches ~1.6e3 rad at 408 MHz and
+the most rotated pixels keep only ~0.3 % of their unrotated polarised
+intensity P0.  An FP32 march is accurate to ~1e-6 P0 there (phase errors of
+~1e-6 rad from the per-sample rounding of n_e B_par, coherent over a ray),
+which is ~3e-4 of such a pixel's |P|.  FP64 is held to 1e-9 at every
+frequency, and FP32 to 1e-4 at and above 1 GHz (the grid workload of Sec. 3.3
+is at 2.4 GHz).
+theta gradient: Richardson-extrapolated central differences of the oracle.
+Grid gradient (synax_adjoint_grid): directional derivatives <G, V> along
+seeded random directions V and single-node derivatives, both against
+Richardson-extrapolated central differences of the oracle's loss at
+grid +/- eps V.  Tolerance |d - d_FD| <= 1e-3 |d_FD| + 1e-4 sum_i |G_i V_i|
+(FP32 march), 1e-7 relative for FP64.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_01136_gb300 import adjoint, adjoint_grid, eval_fields, forward, inputs
+
+from .parity import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    assert _t.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2410_01136_gb300 import build
+    build()
+    oracle.build()
+    return _t
+
+
+P_TOL_BELOW_1GHZ = 5e-4
+
+
+def small(nside=8, n_steps=100, n=(12, 10, 6), seed=21, freqs=(408e6, 2.4e9), **kw):
+    return inputs.grid_problem(nside=nside, n_steps=n_steps, freq_hz=freqs, n=n, seed=seed, **kw)
+
+
+def check_maps(m, ref, prob, what):
+    """Parity per frequency: FP64 to 1e-9; FP32 I to 1e-5, P to 1e-4 at and
+    above 1 GHz and to P_TOL_BELOW_1GHZ below."""
+    for f, nu in enumerate(prob.freq_hz):
+        if prob.f64:
+            assert_parity(m[f:f + 1], ref[f:f + 1], 1e-9, 1e-9, f"{what} FP64 {nu:.3g} Hz")
+        else:
+            tol_p = 1e-4 if nu >= 1e9 else P_TOL_BELOW_1GHZ
+            assert_parity(m[f:f + 1], ref[f:f + 1], 1e-5, tol_p, f"{what} FP32 {nu:.3g} Hz")
+
+
+def seeds(prob, seed=9):
+    n = prob.n_pix_out
+    return inputs.normal(inputs.substream(seed, n), prob.n_freq * 3 * n).reshape(prob.n_freq, 3, n)
+
+
+def dev(torch, a, prob):
+    return torch.tensor(a, dtype=torch.float64 if prob.f64 else torch.float32, device="cuda")
+
+
+def richardson(L, eps):
+    d1 = (L(eps) - L(-eps)) / (2 * eps)
+    d2 = (L(eps / 2) - L(-eps / 2)) / eps
+    return (4 * d2 - d1) / 3
+
+
+@pytest.mark.parametrize("f64", [False, True])
+@pytest.mark.parametrize("shape", [dict(n=(64, 56, 16)),
+                                   dict(pix_begin=37, pix_count=611, n_steps=77, n=(9, 7, 3), freqs=(1.4e9, 2.4e9))])
+def test_forward_parity_small(torch, f64, shape):
+    prob = small(f64=f64, **shape)
+    m = forward(prob).cpu().numpy()
+    ref = oracle.forward(prob, pix=np.arange(prob.pix_begin, prob.pix_begin + prob.n_pix_out))
+    check_maps(m, ref, prob, "grid")
+
+
+@pytest.mark.parametrize("f64", [False, True])
+@pytest.mark.parametrize("n", [(12, 10, 6), (64, 56, 16)])
+def test_low_frequency(torch, f64, n):
+    """408 MHz alone on a coarse (cells of 2-4 kpc) and a fine grid."""
+    prob = small(n=n, freqs=(408e6,), f64=f64)
+    check_maps(forward(prob).cpu().numpy(), oracle.forward(prob), prob, f"grid {n}")
+
+
+def test_forward_full_size_sampled(torch):
+    prob = inputs.grid_problem()                     # Nside 64, 512 steps, 128 x 128 x 32, 2.4 GHz
+    m = forward(prob).cpu().numpy()
+    pix = inputs.sample_pixels(prob.npix, 96, seed=12)
+    assert_parity(m[:, :, pix], oracle.forward(prob, pix=pix), what="grid full size")
+
+
+def test_uniform_grid_equals_wmap_model(torch):
+    """A uniform grid marches like the WMAP-type model with b0 = 0 and the same x field."""
+    bux = 2.5
+    grid = np.zeros((3, 4, 5, 3))
+    grid[..., 0] = bux
+    pg = small(nside=8, n_steps=64).replace(grid=grid)
+    wm = np.array([0.0, 0.3, 0.0, 0.0, bux, *pg.theta])
+    pw = inputs.Problem(nside=8, n_steps=64, freq_hz=pg.freq_hz, model_id=inputs.MODEL_WMAP, theta=wm,
+                        box_clip=True)
+    assert_parity(forward(pg).cpu().numpy(), forward(pw).cpu().numpy(), what="uniform grid vs WMAP")
+
+
+@pytest.mark.parametrize("f64", [False, True])
+def test_eval_fields_grid(torch, f64):
+    prob = small(f64=f64)
+    u = inputs.uniform(inputs.substream(40, 1), 3 * 500, -0.55, 0.55).reshape(500, 3)
+    pos = u * np.asarray(prob.box_kpc)                  # 10 % beyond the walls: the clamp
+    out = eval_fields(prob, pos, np.zeros(500)).cpu().numpy()
+    ref = np.array([oracle.grid_interp(prob.grid, prob.box_kpc, r) for r in pos])
+    np.testing.assert_allclose(out[:, :3], ref, rtol=0, atol=1e-12 if f64 else 2e-5)
+    for i in range(0, 500, 50):
+        _, n0, ne = oracle.fields(prob, pos[i])
+        np.testing.assert_allclose(out[i, 3:], [n0, ne], rtol=1e-12 if f64 else 1e-5)
+
+
+@pytest.mark.parametrize("f64", [False, True])
+def test_theta_gradient(torch, f64):
+    prob = small(f64=f64, nside=4, n_steps=64)
+    gm = seeds(prob)
+    g, _ = adjoint_grid(prob, gmaps=dev(torch, gm, prob))
+    g2 = adjoint(prob, gmaps=dev(torch, gm, prob))
+    assert np.array_equal(g.cpu().numpy(), g2.cpu().numpy())      # same kernels, same order
+    th = prob.theta
+    ref = np.array([richardson(lambda e, j=j: float(np.sum(gm * oracle.forward(
+        prob.with_theta(th + e * np.eye(3)[j] * abs(th[j]))))) / abs(th[j]), 1e-4) for j in range(3)])
+    rel, floor = (1e-7, 1e-9) if f64 else (1e-3, 1e-4)
+    tol = rel * np.abs(ref) + floor * np.max(np.abs(ref))
+    assert np.all(np.abs(g.cpu().numpy() - ref) <= tol), (g.cpu().numpy(), ref)
+
+
+def _directional(prob, loss, V, eps):
+    base = np.asarray(prob.grid)
+
+    def L(e):
+        return loss(oracle.forward(prob.replace(grid=base + e * V)))
+    return richardson(L, eps)
+
+
+@pytest.mark.parametrize("f64", [False, True])
+def test_grid_gradient_directional_vjp(torch, f64):
+    prob = small(f64=f64, nside=4, n_steps=64, n=(8, 7, 4))
+    gm = seeds(prob, seed=10)
+    _, G = adjoint_grid(prob, gmaps=dev(torch, gm, prob))
+    G = G.cpu().numpy().astype(np.float64)
+    assert G.shape == np.asarray(prob.grid).shape
+    for k in range(3):
+        V = inputs.normal(inputs.substream(41, k), G.size).reshape(G.shape)
+        d = float(np.sum(G * V))
+        # FP64 is compared at 1e-7: a smaller step keeps the extrapolated
+        # difference's truncation error (~eps^4) below that
+        ref = _directional(prob, lambda m: float(np.sum(gm * m)), V, 1e-4 if f64 else 1e-3)
+        scale = float(np.sum(np.abs(G * V)))
+        tol = 1e-7 * abs(ref) + 1e-9 * scale if f64 else 1e-3 * abs(ref) + 1e-4 * scale
+        assert abs(d - ref) <= tol, (k, d, ref, scale)
+
+
+def test_grid_gradient_single_nodes_chi2(torch):
+    prob = small(nside=4, n_steps=64, n=(8, 7, 4))
+    target = oracle.forward(prob.replace(grid=np.asarray(prob.grid) * 0.9))
+    target = target + inputs.target_noise(target.shape, seed=3, sigma=0.05)
+    maps = torch.empty((prob.n_freq, 3, prob.npix), device="cuda")
+    grad, G, chi2 = adjoint_grid(prob, target=dev(torch, target, prob), sigma=0.05, maps_out=maps)
+    ref_maps = oracle.forward(prob)
+    check_maps(maps.cpu().numpy(), ref_maps, prob, "adjoint_grid maps_out")
+    assert float(chi2.item()) == pytest.approx(oracle.chi2(ref_maps, target, 0.05), rel=1e-5)
+    G = G.cpu().numpy().astype(np.float64)
+    flat = np.argsort(-np.abs(G).ravel())[:4]           # the nodes the loss depends on most
+    for idx in flat:
+        V = np.zeros(G.size)
+        V[idx] = 1.0
+        V = V.reshape(G.shape)
+        ref = _directional(prob, lambda m: oracle.chi2(m, target, 0.05), V, 1e-3)
+        assert abs(G.ravel()[idx] - ref) <= 1e-3 * abs(ref) + 1e-5 * np.abs(G).max(), (idx, G.ravel()[idx], ref)
+    assert np.all(np.isfinite(G)) and np.count_nonzero(G) > 0
+
+
+def test_grid_gradient_full_size_sampled(torch):
+    """Full workload, the bench's launch: seeds on 24 sampled pixels only, so the
+    oracle marches just those rays for the directional derivatives."""
+    prob = inputs.grid_problem()
+    pix = inputs.sample_pixels(prob.npix, 24, seed=13)
+    gm = np.zeros((prob.n_freq, 3, prob.npix))
+    gm[:, :, pix] = seeds(prob, seed=11)[:, :, pix]
+    grad, G = adjoint_grid(prob, gmaps=dev(torch, gm, prob))
+    G = G.cpu().numpy().astype(np.float64)
+    base = np.asarray(prob.grid)
+    for k in range(2):
+        V = inputs.normal(inputs.substream(42, k), G.size).reshape(G.shape)
+
+        def L(e):
+            return float(np.sum(gm[:, :, pix] * oracle.forward(prob.replace(grid=base + e * V), pix=pix)))
+        ref = richardson(L, 1e-3)
+        d = float(np.sum(G * V))
+        scale = float(np.sum(np.abs(G * V)))
+        assert abs(d - ref) <= 1e-3 * abs(ref) + 1e-4 * scale, (k, d, ref, scale)
+
+
+def test_empty_range_zeroes_grid_gradient(torch):
+    prob = small(nside=4, n_steps=16)
+    prob = prob.replace(pix_begin=prob.npix, pix_count=0)
+    G = torch.full(np.asarray(prob.grid).shape, 7.0, device="cuda")
+    grad, G = adjoint_grid(prob, gmaps=torch.empty((prob.n_freq, 3, 0), device="cuda"), grid_grad=G)
+    assert float(G.abs().max()) == 0.0 and float(grad.abs().max()) == 0.0
+
+
+def test_device_grid_tensor_in_place(torch):
+    """A device grid is used in place: updating it changes the next march."""
+    prob = small(nside=4, n_steps=32)
+    g_dev = torch.tensor(np.asarray(prob.grid), dtype=torch.float32, device="cuda")
+    pd = prob.replace(grid=g_dev)
+    m1 = forward(pd).clone()
+    assert_parity(m1.cpu().numpy(), forward(prob).cpu().numpy(), 0, 0, "device vs host grid")
+    g_dev.mul_(1.1)
+    m2 = forward(pd).cpu().numpy()
+    check_maps(m2, oracle.forward(prob.replace(grid=np.asarray(prob.grid) * 1.1)), prob, "scaled grid")
