@@ -262,7 +262,7 @@ def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
                                          dtype=torch.float32, device=dev)).contiguous()
     maps = torch.empty_like(target)
     gg = torch.empty_like(grid)
-    ws = torch.empty(max(sx.adjoint_workspace_bytes(prob), 1), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(sx.adjoint_grid_workspace_bytes(prob), 1), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -299,7 +299,7 @@ def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
         "maps_grad_per_s": 1.0 / (ms * 1e-3),
         "forward_ms": ms_fwd,
         "forward_samples_per_s": samples / (ms_fwd * 1e-3),
-        "gpu_launches_per_step": 2,      # k_adjoint + k_reduce_partials (plus a memset of the grid gradient)
+        "gpu_launches_per_step": 3,      # k_adjoint, k_reduce_partials, k_grid_unpad (plus a memset)
         "l2": "flushed between steps (256 MiB write); the 6.3 MB grid is re-read from HBM",
     }
 

@@ -135,14 +135,17 @@ int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* 
                   void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* Adjoint of the grid model (SYNAX_MODEL_GRID, the field-level optimisation
- * of Sec. 3.3): synax_adjoint (same modes, arguments and workspace) plus the
- * gradient with respect to every grid value, written to grid_grad_dev, laid
- * out like the grid ([n_z][n_y][n_x][3], float32, float64 with SYNAX_F64,
- * overwritten).  Each sample's adjoint of B is scattered into the 8 nodes of
- * its cell with the trilinear weights; a lane sums consecutive samples of one
- * cell in registers and adds them with atomic adds when it leaves the cell,
- * so the grid gradient is not bitwise reproducible (the theta gradient is).
+ * of Sec. 3.3): synax_adjoint (same modes and arguments) plus the gradient
+ * with respect to every grid value, written to grid_grad_dev, laid out like
+ * the grid ([n_z][n_y][n_x][3], float32, float64 with SYNAX_F64,
+ * overwritten).  workspace_dev: at least synax_adjoint_grid_workspace_bytes
+ * bytes (the FP32 path keeps a 16-byte-per-node accumulator there).  Each
+ * sample's adjoint of B is scattered into the 8 nodes of its cell with the
+ * trilinear weights; a lane sums consecutive samples of one cell in
+ * registers and adds them with atomic adds when it leaves the cell, so the
+ * grid gradient is not bitwise reproducible (the theta gradient is).
  * Other models: SYNAX_ENOTSUP. */
+int synax_adjoint_grid_workspace_bytes(const synax_problem* prob, size_t* bytes);
 int synax_adjoint_grid(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
                        double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
                        void* grid_grad_dev, void* workspace_dev, size_t workspace_bytes, void* stream);

@@ -18,7 +18,7 @@ from . import inputs
 from . import _native
 from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
 
-__all__ = ["forward", "adjoint", "adjoint_grid", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
+__all__ = ["forward", "adjoint", "adjoint_grid", "adjoint_grid_workspace_bytes", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
            "SynaxError"]
 
 
@@ -126,6 +126,14 @@ def adjoint(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=None, wo
     return grad
 
 
+def adjoint_grid_workspace_bytes(prob) -> int:
+    s = problem_struct(prob)
+    n = ctypes.c_size_t(0)
+    check(lib().synax_adjoint_grid_workspace_bytes(ctypes.byref(s), ctypes.byref(n)),
+          "synax_adjoint_grid_workspace_bytes")
+    return int(n.value)
+
+
 def adjoint_grid(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=None, grid_grad=None,
                  workspace=None, stream=None):
     """Grid model (Sec. 3.3): the gradient with respect to theta = [N0_obs, p,
@@ -149,9 +157,11 @@ def adjoint_grid(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=Non
     elif (not grid_grad.is_cuda or grid_grad.dtype != _map_dtype(torch, prob)
           or tuple(grid_grad.shape) != shape or not grid_grad.is_contiguous()):
         raise ValueError(f"grid_grad must be a contiguous CUDA {_map_dtype(torch, prob)} tensor of shape {shape}")
-    nbytes = adjoint_workspace_bytes(prob)
+    nbytes = ctypes.c_size_t(0)
+    check(lib().synax_adjoint_grid_workspace_bytes(ctypes.byref(s), ctypes.byref(nbytes)),
+          "synax_adjoint_grid_workspace_bytes")
     if workspace is None:
-        workspace = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+        workspace = torch.empty(max(nbytes.value, 1), dtype=torch.uint8, device="cuda")
     grad = torch.empty(len(prob.theta), dtype=torch.float64, device="cuda")
     chi2 = torch.empty(1, dtype=torch.float64, device="cuda") if target is not None else None
     check(lib().synax_adjoint_grid(

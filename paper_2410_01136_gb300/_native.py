@@ -84,6 +84,8 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                      ctypes.c_void_p]),
+    "synax_adjoint_grid_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(SynaxProblem),
+                                                          ctypes.POINTER(ctypes.c_size_t)]),
     "synax_adjoint_grid": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

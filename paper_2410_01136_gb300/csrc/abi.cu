@@ -320,6 +320,17 @@ int synax_adjoint_workspace_bytes(const synax_problem* prob, size_t* bytes) {
     return SYNAX_OK;
 }
 
+// Workspace of synax_adjoint_grid: the partials of synax_adjoint, then (FP32)
+// the padded node-gradient accumulator, 16 bytes per node, 256-byte aligned.
+static size_t round_up_256(size_t v) { return (v + 255) & ~size_t(255); }
+static size_t grid_nodes(const synax_problem* p) {
+    return (size_t)p->grid_n[0] * (size_t)p->grid_n[1] * (size_t)p->grid_n[2];
+}
+static size_t adjoint_grid_ws(const synax_problem* p, long long n_pix) {
+    const size_t part = n_pix > 0 ? adjoint_workspace_bytes(n_pix, p->n_theta) : 0;
+    return (p->flags & SYNAX_F64) ? part : round_up_256(part) + 16 * grid_nodes(p);
+}
+
 // synax_adjoint and synax_adjoint_grid (grid_grad_dev non-null: grid model only).
 static int adjoint_impl(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
                         double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
@@ -335,14 +346,22 @@ static int adjoint_impl(const synax_problem* prob, const void* gmaps_dev, const 
         if (!is_finite(sigma_K)) return SYNAX_ENONFINITE;
         if (!(sigma_K > 0.0)) return SYNAX_EINVAL;
     }
-    const size_t need = n_pix > 0 ? adjoint_workspace_bytes(n_pix, prob->n_theta) : 0;
+    const size_t need = grid_grad_dev ? adjoint_grid_ws(prob, n_pix)
+                                      : (n_pix > 0 ? adjoint_workspace_bytes(n_pix, prob->n_theta) : 0);
     if (workspace_bytes < need || (need > 0 && !workspace_dev)) return SYNAX_ESPACE;
     cudaStream_t st = (cudaStream_t)stream;
     const bool f64 = (prob->flags & SYNAX_F64) != 0;
+    const size_t nodes = grid_grad_dev ? grid_nodes(prob) : 0;
+    float4* grid_acc = nullptr;
     if (grid_grad_dev) {
         // the kernels add into the node gradient: start from zero
-        const size_t nodes = (size_t)prob->grid_n[0] * prob->grid_n[1] * prob->grid_n[2];
-        const cudaError_t err = cudaMemsetAsync(grid_grad_dev, 0, 3 * nodes * (f64 ? 8 : 4), st);
+        cudaError_t err;
+        if (f64 || n_pix == 0) {
+            err = cudaMemsetAsync(grid_grad_dev, 0, 3 * nodes * (f64 ? 8 : 4), st);
+        } else {
+            grid_acc = (float4*)((char*)workspace_dev + round_up_256(adjoint_workspace_bytes(n_pix, prob->n_theta)));
+            err = cudaMemsetAsync(grid_acc, 0, 16 * nodes, st);
+        }
         if (err != cudaSuccess) return record_cuda_error((int)err);
     }
     if (n_pix == 0) {
@@ -368,9 +387,11 @@ static int adjoint_impl(const synax_problem* prob, const void* gmaps_dev, const 
     fill_adj<float>(*prob, A);
     A.mode_chi2 = chi2_mode ? 1 : 0;
     A.inv_sigma2 = chi2_mode ? (float)(1.0 / (sigma_K * sigma_K)) : 0.0f;
-    A.grid_grad = (float*)grid_grad_dev;
-    return launch_adjoint_f32(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
-                              maps_dev, workspace_dev, stream);
+    A.grid_acc = grid_acc;
+    const int rc2 = launch_adjoint_f32(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
+                                       maps_dev, workspace_dev, stream);
+    if (rc2 != SYNAX_OK || !grid_acc) return rc2;
+    return launch_grid_unpad(grid_acc, (float*)grid_grad_dev, (long long)nodes, stream);
 }
 
 int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
@@ -378,6 +399,17 @@ int synax_adjoint(const synax_problem* prob, const void* gmaps_dev, const void* 
                   void* workspace_dev, size_t workspace_bytes, void* stream) {
     return adjoint_impl(prob, gmaps_dev, target_dev, sigma_K, grad_dev, chi2_dev, maps_dev, nullptr,
                         workspace_dev, workspace_bytes, stream);
+}
+
+int synax_adjoint_grid_workspace_bytes(const synax_problem* prob, size_t* bytes) {
+    if (!prob) return SYNAX_EINVAL;
+    if (prob->model_id != SYNAX_MODEL_GRID) return SYNAX_ENOTSUP;
+    long long n_pix = 0;
+    const int rc = validate_problem(prob, &n_pix);
+    if (rc != SYNAX_OK) return rc;
+    if (!bytes) return SYNAX_EINVAL;
+    *bytes = adjoint_grid_ws(prob, n_pix);
+    return SYNAX_OK;
 }
 
 int synax_adjoint_grid(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,

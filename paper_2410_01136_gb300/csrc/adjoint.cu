@@ -60,6 +60,26 @@ k_reduce_partials(const double* __restrict__ partial, long long n_blocks, int n_
     }
 }
 
+// [nodes] float4 accumulator -> [nodes][3] (coalesced: a warp reads 512
+// contiguous bytes and writes 384).
+__global__ void __launch_bounds__(256)
+k_grid_unpad(const float4* __restrict__ acc, float* __restrict__ out, long long nodes) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nodes) return;
+    const float4 v = acc[i];
+    out[3 * i + 0] = v.x;
+    out[3 * i + 1] = v.y;
+    out[3 * i + 2] = v.z;
+}
+
+int launch_grid_unpad(const float4* acc, float* out, long long nodes, void* stream) {
+    if (nodes <= 0) return SYNAX_OK;
+    const long long blocks = (nodes + 255) / 256;
+    k_grid_unpad<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(acc, out, nodes);
+    const cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
+}
+
 // Sized for the largest grid (32 lanes per ray), whatever the tuning picks.
 size_t adjoint_workspace_bytes(long long n_pix, int n_theta) {
     return (size_t)adj_blocks(n_pix, 32) * (size_t)(n_theta + 1) * sizeof(double);

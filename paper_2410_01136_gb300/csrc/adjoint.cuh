@@ -102,26 +102,49 @@ template <> struct Grad<SYNAX_MODEL_GRID> {
 // lane marches consecutive samples, which mostly share a cell: it sums the
 // cell's 24 node gradients in registers and adds them to the grid with
 // atomic adds when it enters another cell and at the end of its chunk.
+// FP32 adds into a [nodes] float4 accumulator, one 16-byte vector atomic per
+// node (8 per cell instead of 24 scalar ones: the scalar form kept the
+// load/store queue full); FP64 adds the 3 components into [nodes][3].
+template <typename R> struct GridGradPtr;
+template <> struct GridGradPtr<float> {
+    using T = float4;
+    static __device__ __forceinline__ T* get(const AdjParams<float>& A) { return A.grid_acc; }
+};
+template <> struct GridGradPtr<double> {
+    using T = double;
+    static __device__ __forceinline__ T* get(const AdjParams<double>& A) { return A.grid_grad; }
+};
+
 template <typename R>
 struct GridAcc {
     int base;                 // node index of the cell's lower corner; -1: empty
     R w[8][3];
 
-    __device__ __forceinline__ void flush(const MapParams<R>& P, R* gg) {
+    __device__ __forceinline__ void flush(const MapParams<R>& P, typename GridGradPtr<R>::T* gg) {
         if (base < 0) return;
-        const long long sy = 3LL * P.grid_n[0], sz = sy * P.grid_n[1];
-        R* p = gg + 3LL * base;
+        if constexpr (sizeof(R) == 4) {
+            const long long sy = P.grid_n[0], sz = sy * P.grid_n[1];
+            float4* p = gg + base;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const long long off = ((q & 1) ? 3 : 0) + ((q & 2) ? sy : 0) + ((q & 4) ? sz : 0);
+            for (int q = 0; q < 8; ++q) {
+                const long long off = ((q & 1) ? 1 : 0) + ((q & 2) ? sy : 0) + ((q & 4) ? sz : 0);
+                atomicAdd(p + off, make_float4(w[q][0], w[q][1], w[q][2], 0.0f));
+            }
+        } else {
+            const long long sy = 3LL * P.grid_n[0], sz = sy * P.grid_n[1];
+            double* p = gg + 3LL * base;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(p + off + c, w[q][c]);
+            for (int q = 0; q < 8; ++q) {
+                const long long off = ((q & 1) ? 3 : 0) + ((q & 2) ? sy : 0) + ((q & 4) ? sz : 0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(p + off + c, w[q][c]);
+            }
         }
         base = -1;
     }
 
-    __device__ __forceinline__ void add(const MapParams<R>& P, R* gg, const FieldLocal<R>& L, R bxb, R byb,
-                                        R bzb) {
+    __device__ __forceinline__ void add(const MapParams<R>& P, typename GridGradPtr<R>::T* gg,
+                                        const FieldLocal<R>& L, R bxb, R byb, R bzb) {
         if (L.gbase != base) {
             flush(P, gg);
             base = L.gbase;
@@ -278,7 +301,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
             gc.base = -1;
             gacc.base = -1;
             if constexpr (MODEL == SYNAX_MODEL_GRID) grid_ray_init<R>(P, L, nd, n0, dr, dr_lo, gr);
-            R* const gg = live ? A.grid_grad : nullptr;  // idle segments scatter nothing
+            auto* const gg = live ? GridGradPtr<R>::get(A) : nullptr;   // idle segments scatter nothing
             const R q = P.q;
             R nh = R(n1 - 1) + R(0.5);                  // n + 1/2, exact
             for (int n = n1 - 1; n >= n0; --n, nh -= R(1)) {

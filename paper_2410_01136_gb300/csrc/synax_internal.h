@@ -82,7 +82,8 @@ struct AdjParams {
     int n_theta;
     int mode_chi2;            // 1: seed = 2 (M - target) / sigma^2
     R inv_sigma2;
-    R* grid_grad;             // grid model: gradient of every node value (zeroed by the host), or null
+    R* grid_grad;             // grid model, FP64: gradient of every node value (zeroed by the host), or null
+    float4* grid_acc;         // grid model, FP32: the same as [nodes] float4 (x, y, z, unused), zeroed
 };
 
 // Host-side problem handling (abi.cu).
@@ -99,6 +100,8 @@ int launch_forward_f32(const MapParams<float>& P, void* maps, void* stream);
 int launch_forward_f64(const MapParams<double>& P, void* maps, void* stream);
 
 size_t adjoint_workspace_bytes(long long n_pix, int n_theta);
+// FP32 grid gradient: padded accumulator -> [nodes][3] output (adjoint.cu).
+int launch_grid_unpad(const float4* acc, float* out, long long nodes, void* stream);
 int launch_adjoint_f32(const MapParams<float>& P, const AdjParams<float>& A, const void* gmaps,
                        const void* target, double* grad, double* chi2, void* maps,
                        void* workspace, void* stream);

@@ -169,6 +169,23 @@ def test_grid_validation_rejects(L, mutate):
     assert L.synax_forward(ctypes.byref(s), ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
 
 
+def test_adjoint_grid_workspace_query(L):
+    g = _grid_struct()
+    n = ctypes.c_size_t(0)
+    assert L.synax_adjoint_grid_workspace_bytes(ctypes.byref(g), ctypes.byref(n)) == _native.SYNAX_OK
+    theta_only = ctypes.c_size_t(0)
+    assert L.synax_adjoint_workspace_bytes(ctypes.byref(g), ctypes.byref(theta_only)) == _native.SYNAX_OK
+    assert n.value >= theta_only.value + 16 * 4 * 4 * 2          # FP32: a float4 per node
+    s = _native.problem_struct(good())
+    assert L.synax_adjoint_grid_workspace_bytes(ctypes.byref(s), ctypes.byref(n)) == _native.SYNAX_ENOTSUP
+    dummy = ctypes.c_void_p(16)
+    g.pix_begin = 0
+    need = ctypes.c_size_t(0)
+    L.synax_adjoint_grid_workspace_bytes(ctypes.byref(g), ctypes.byref(need))
+    assert L.synax_adjoint_grid(ctypes.byref(g), dummy, None, 1.0, dummy, None, None, dummy, dummy,
+                                need.value - 1, None) == _native.SYNAX_ESPACE
+
+
 def test_adjoint_grid_validation(L):
     dummy = ctypes.c_void_p(16)
     s = _native.problem_struct(good())
