@@ -288,6 +288,18 @@ def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     ms_fwd = float(np.mean([a.elapsed_time(b) for a, b in fev]))
+    # the field-level fit of Sec. 3.3: chi^2 + grid gradient + Adam per step
+    fit = sx.GridFit(prob, target, sigma=1e-3, lr=0.05)
+    fit.run(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_fit = 50
+    e0.record(stream)
+    chi2 = fit.run(n_fit)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fit = e0.elapsed_time(e1) / n_fit
+    chi2 = chi2.cpu().numpy()
     samples = prob.samples
     return {
         "workload": "grid B 128x128x32 over (40, 40, 10) kpc, Nside 64, 512 steps to the box, 2.4 GHz, "
@@ -300,8 +312,39 @@ def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
         "forward_ms": ms_fwd,
         "forward_samples_per_s": samples / (ms_fwd * 1e-3),
         "gpu_launches_per_step": 3,      # k_adjoint, k_reduce_partials, k_grid_unpad (plus a memset)
+        "fit_ms_per_step": ms_fit,
+        "fit_200_steps_s": 200 * ms_fit * 1e-3,
+        "fit_chi2_step4_step53": [float(chi2[0]), float(chi2[-1])],
+        "fit_note": "Adam, lr 0.05 uG, on the grid (synax_adam), back to back without L2 flushes",
         "l2": "flushed between steps (256 MiB write); the 6.3 MB grid is re-read from HBM",
     }
+
+
+def interp_study(sx, inputs, torch) -> dict:
+    """Sec. 5's interpolation study, re-run: the WMAP-type field with the
+    parameters of Sec. 3.1 (b0 = 1.2 uG, psi0 = 0.4712, psi1 = 0.0157,
+    chi0B = 0.4363 rad; no x field; analytic n_e) sampled on (N, N, N/4)
+    grids over the (40, 40, 10) kpc box and marched as a grid model, against
+    the analytic march: std over pixels of the I, Q, U residual (K) at
+    2.4 GHz, Nside 64, 512 steps, FP64.  Reported, not timed."""
+    import numpy as np
+    th = np.array([1.2, 0.4712, 0.0157, 0.4363, 0.0, inputs.N0_EARTH, 3.0, 0.03])
+    ana = inputs.Problem(nside=64, n_steps=512, freq_hz=(2.4e9,), model_id=inputs.MODEL_WMAP, theta=th,
+                         box_clip=True, obs_kpc=inputs.OBS_PAPER_KPC, f64=True)
+    m_ana = sx.forward(ana)
+    out = {"workload": "WMAP-type (Sec. 3.1 values) on (N, N, N/4) grids vs analytic, Nside 64, 512 steps, "
+                       "2.4 GHz, FP64", "std_IQU_K": {}, "map_rms_IQU_K": [float(x) for x in
+                                                     m_ana[0].pow(2).mean(dim=-1).sqrt().tolist()]}
+    for n_x in (64, 128, 256, 512):
+        grid = sx.grid_sample(ana, (n_x, n_x, n_x // 4))
+        pg = inputs.Problem(nside=64, n_steps=512, freq_hz=(2.4e9,), model_id=inputs.MODEL_GRID,
+                            theta=np.array([th[5], th[6], th[7]]), box_clip=True, obs_kpc=inputs.OBS_PAPER_KPC,
+                            f64=True, grid=grid)
+        r = (sx.forward(pg) - m_ana)[0]
+        out["std_IQU_K"][str(n_x)] = [float(x) for x in r.std(dim=-1).tolist()]
+        del grid, pg, r
+    torch.cuda.empty_cache()
+    return out
 
 
 def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict, n_maps: int = 50000) -> dict:
@@ -598,6 +641,7 @@ def run_synax(args):
         out["gpu_launches_batch_per_run"] = 2
     if rank == 0 and not args.no_grid:
         out["grid"] = bench_grid(sx, inputs, torch, dev)
+        out["interp_study"] = interp_study(sx, inputs, torch)
     if rank == 0 and not args.no_surrogate:
         peaks = {}
         try:

@@ -219,6 +219,27 @@ int synax_adjoint_noalloc(const synax_problem* prob, const void* gmaps_dev, cons
                           double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
                           void* stream);
 
+/* Samples B of an analytic model (toy, WMAP or JF12; SYNAX_ENOTSUP for the
+ * grid model) at the nodes of an (n_x, n_y, n_z) grid spanning the problem's
+ * box wall to wall, in the layout of the grid model: grid_dev
+ * [n_z][n_y][n_x][3] in uG, float32 (float64 with SYNAX_F64), written
+ * completely.  Node (i, j, k) is at (-l_x/2 + i l_x/(n_x - 1), ...), as in
+ * SYNAX_MODEL_GRID.  Uses: the interpolation-error study of Sec. 5 (an
+ * analytic B on grids of growing size), or a parametric start for the
+ * field-level fit of Sec. 3.3.  Needs SYNAX_BOX_CLIP (the box); grid_n as
+ * for the grid model. */
+int synax_grid_sample(const synax_problem* prob, const int32_t* grid_n, void* grid_dev, void* stream);
+
+/* One Adam step (Kingma & Ba 2015; the optimiser of the field-level fit of
+ * Sec. 3.3) on n float32 values in place:
+ *   m <- beta1 m + (1 - beta1) g,  v <- beta2 v + (1 - beta2) g^2,
+ *   p <- p - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ * t >= 1 is the step number (1 for the first step, with m = v = 0).  All
+ * four arrays are device float32 of n values; grads_dev is read only.
+ * SYNAX_EINVAL for t < 1, beta outside [0, 1) or eps < 0. */
+int synax_adam(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev, int64_t n, double lr,
+               double beta1, double beta2, double eps, int64_t t, void* stream);
+
 /* Field models evaluated at arbitrary points (diagnostics and unit tests of
  * the device field code, which is the code the march runs).
  * pos_dev: [n][3] doubles (kpc, galactocentric); t_dev: [n] doubles, the

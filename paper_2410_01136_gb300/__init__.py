@@ -18,7 +18,7 @@ from . import inputs
 from . import _native
 from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
 
-__all__ = ["forward", "adjoint", "adjoint_grid", "adjoint_grid_workspace_bytes", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
+__all__ = ["forward", "adjoint", "adjoint_grid", "adjoint_grid_workspace_bytes", "grid_sample", "adam_step", "GridFit", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
            "SynaxError"]
 
 
@@ -178,6 +178,80 @@ def adjoint_grid(prob, gmaps=None, target=None, sigma: float = 1.0, maps_out=Non
     if target is not None:
         return grad, grid_grad, chi2
     return grad, grid_grad
+
+
+def grid_sample(prob, n, stream=None):
+    """B of prob's analytic model at the nodes of an n = (n_x, n_y, n_z) grid
+    spanning prob's box (synax_grid_sample); returns a [n_z, n_y, n_x, 3] CUDA
+    tensor in the march precision, ready to be a grid model's ``grid``."""
+    torch = _torch()
+    nx, ny, nz = (int(v) for v in n)
+    out = torch.empty((nz, ny, nx, 3), dtype=_map_dtype(torch, prob), device="cuda")
+    gn = (ctypes.c_int32 * 3)(nx, ny, nz)
+    s = problem_struct(prob)
+    check(lib().synax_grid_sample(ctypes.byref(s), gn, ctypes.c_void_p(out.data_ptr()),
+                                  _stream_handle(torch, stream)), "synax_grid_sample")
+    return out
+
+
+def adam_step(params, grads, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8, stream=None):
+    """One in-place Adam step on contiguous float32 CUDA tensors (synax_adam)."""
+    torch = _torch()
+    for name, x in (("params", params), ("grads", grads), ("m", m), ("v", v)):
+        if not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous() or x.numel() != params.numel():
+            raise ValueError(f"{name} must be a contiguous CUDA float32 tensor of {params.numel()} values")
+    check(lib().synax_adam(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(grads.data_ptr()),
+                           ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()), params.numel(),
+                           float(lr), float(beta1), float(beta2), float(eps), int(t),
+                           _stream_handle(torch, stream)), "synax_adam")
+
+
+class GridFit:
+    """Field-level fit of a grid model to a target map (Sec. 3.3): every step
+    is synax_adjoint_grid in chi^2 mode (maps, chi^2, grid gradient) followed
+    by synax_adam on the grid, all enqueued on one stream; buffers are
+    allocated once.
+
+        fit = GridFit(prob, target, sigma, lr=0.05)   # prob.grid: the start
+        chi2 = fit.run(200)                           # chi^2 before each step
+        fit.grid                                      # the fitted grid (CUDA tensor)
+    """
+
+    def __init__(self, prob, target, sigma: float, lr: float = 0.05, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8):
+        torch = _torch()
+        if getattr(prob, "f64", False):
+            raise ValueError("GridFit runs the FP32 march (synax_adam is float32)")
+        from ._native import grid_device
+        self.grid = grid_device(prob).clone()
+        self.prob = prob.replace(grid=self.grid)
+        _check_map_tensor(torch, target, self.prob, "target")
+        self.target, self.sigma = target, float(sigma)
+        self.lr, self.beta1, self.beta2, self.eps = lr, beta1, beta2, eps
+        self.m = torch.zeros_like(self.grid)
+        self.v = torch.zeros_like(self.grid)
+        self.g = torch.empty_like(self.grid)
+        self.maps = torch.empty_like(target)
+        self.workspace = torch.empty(max(adjoint_grid_workspace_bytes(self.prob), 1), dtype=torch.uint8,
+                                     device="cuda")
+        self.t = 0
+
+    def step(self):
+        """One chi^2 + gradient evaluation and Adam update; returns chi^2 (a
+        device scalar) of the grid before the update."""
+        _, _, chi2 = adjoint_grid(self.prob, target=self.target, sigma=self.sigma, maps_out=self.maps,
+                                  grid_grad=self.g, workspace=self.workspace)
+        self.t += 1
+        adam_step(self.grid, self.g, self.m, self.v, self.t, self.lr, self.beta1, self.beta2, self.eps)
+        return chi2
+
+    def run(self, n_steps: int):
+        torch = _torch()
+        out = torch.empty(n_steps, dtype=torch.float64, device="cuda")
+        for k in range(n_steps):
+            out[k:k + 1].copy_(self.step())
+        return out
 
 
 class BatchPlan:

@@ -84,6 +84,11 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                      ctypes.c_void_p]),
+    "synax_grid_sample": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "synax_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int64, ctypes.c_void_p]),
     "synax_adjoint_grid_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(SynaxProblem),
                                                           ctypes.POINTER(ctypes.c_size_t)]),
     "synax_adjoint_grid": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.c_void_p, ctypes.c_void_p,

@@ -224,3 +224,105 @@ def test_device_grid_tensor_in_place(torch):
     g_dev.mul_(1.1)
     m2 = forward(pd).cpu().numpy()
     check_maps(m2, oracle.forward(prob.replace(grid=np.asarray(prob.grid) * 1.1)), prob, "scaled grid")
+
+
+# ---------------------------------------------------------------------------
+# sampling analytic models onto grids, the interpolation study, Adam, the fit
+# ---------------------------------------------------------------------------
+
+def _nodes(n, box):
+    x, y, z = (np.linspace(-0.5 * box[a], 0.5 * box[a], n[a]) for a in range(3))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return np.stack([X, Y, Z], axis=-1).reshape(-1, 3)
+
+
+def _wmap_box(f64=True, nside=8, n_steps=128, freqs=(2.4e9,)):
+    th = inputs.wmap_theta()
+    th[2], th[3] = 0.05, 0.3
+    return inputs.Problem(nside=nside, n_steps=n_steps, freq_hz=freqs, model_id=inputs.MODEL_WMAP, theta=th,
+                          box_clip=True, f64=f64)
+
+
+@pytest.mark.parametrize("model,f64", [("wmap", True), ("wmap", False), ("jf12", True), ("jf12", False),
+                                       ("toy", True)])
+def test_grid_sample_matches_oracle_fields(torch, model, f64):
+    if model == "wmap":
+        prob = _wmap_box(f64)
+    elif model == "jf12":
+        prob = inputs.config2().replace(nside=4, n_steps=16, box_clip=True, f64=f64)
+    else:
+        prob = inputs.toy_problem(nside=4, n_steps=16).replace(f64=f64)
+    # even node counts along x and y: no node on the z axis, where the
+    # cylindrical unit vectors (and so the WMAP-type field) are undefined
+    n = (8, 6, 5)
+    g = sx_grid_sample(prob, n).cpu().numpy().reshape(-1, 3)
+    pos = _nodes(n, prob.box_kpc)
+    obs = np.asarray(prob.obs_kpc)
+    ref = np.array([oracle.fields(prob, r, float(np.linalg.norm(r - obs)))[0] for r in pos])
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(g, ref, rtol=0, atol=(1e-12 if f64 else 2e-6) * scale)
+
+
+def sx_grid_sample(prob, n):
+    from paper_2410_01136_gb300 import grid_sample
+    return grid_sample(prob, n)
+
+
+def test_interpolation_converges_second_order(torch):
+    """The grid model reproduces an analytic field with the error of
+    trilinear interpolation, O(h^2) where the field is smooth (Sec. 5 studies
+    the resulting map error against grid size).  The WMAP-type field is
+    sampled on (N, N, N/4) grids and B of the grid model is compared with the
+    analytic B at seeded points more than a cell away from the model's
+    non-smooth places (pitch switched on at rho = 3 and off at 20 kpc, |z|
+    kinked at z = 0, the z axis): the largest error falls by >= 3x per
+    doubling of N (4x in the limit), FP64."""
+    ana = _wmap_box(True)
+    th = ana.theta
+    u = inputs.uniform(inputs.substream(51, 1), 3 * 4000, 0.0, 1.0).reshape(4000, 3)
+    rho = 5.0 + 12.0 * u[:, 0]
+    phi = 2 * np.pi * u[:, 1]
+    z = np.where(u[:, 2] < 0.5, -1.0, 1.0) * (1.5 + 3.0 * (2 * u[:, 2] % 1.0))
+    pts = np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+    b_ana = eval_fields(ana, pts, np.zeros(len(pts))).cpu().numpy()[:, :3]
+    errs = []
+    for n_x in (32, 64, 128):
+        grid = sx_grid_sample(ana, (n_x, n_x, n_x // 4))
+        pg = inputs.Problem(nside=1, n_steps=1, freq_hz=ana.freq_hz, model_id=inputs.MODEL_GRID,
+                            theta=np.array([th[5], th[6], th[7]]), box_clip=True, f64=True, grid=grid)
+        b_grid = eval_fields(pg, pts, np.zeros(len(pts))).cpu().numpy()[:, :3]
+        errs.append(np.abs(b_grid - b_ana).max())
+    errs = np.array(errs)
+    assert np.all(errs[1:] * 3.0 < errs[:-1]), errs
+
+
+def test_adam_matches_oracle(torch):
+    from oracle import surrogate as osur
+    from paper_2410_01136_gb300 import adam_step
+    n = 1003
+    rng = [inputs.normal(inputs.substream(50, k), n) for k in range(4)]
+    p, g, m, v = rng[0], rng[1], 0.1 * rng[2], np.abs(rng[3]) * 0.01
+    dp, dg, dm, dv = (torch.tensor(a, dtype=torch.float32, device="cuda") for a in (p, g, m, v))
+    for t in (1, 7):
+        adam_step(dp, dg, dm, dv, t, lr=0.01)
+        p, m, v = osur.adam_step(p, g, m, v, t, 0.01)
+        np.testing.assert_allclose(dm.cpu().numpy(), m, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(dv.cpu().numpy(), v, rtol=1e-5, atol=1e-9)
+        np.testing.assert_allclose(dp.cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+
+
+def test_grid_fit_reduces_chi2(torch):
+    from oracle import surrogate as osur
+    from paper_2410_01136_gb300 import GridFit
+    prob = small(nside=8, n_steps=64, n=(16, 16, 6), freqs=(1.4e9, 2.4e9))
+    truth = prob.replace(grid=inputs.grid_field(n=(16, 16, 6), seed=22))
+    target = torch.tensor(oracle.forward(truth), dtype=torch.float32, device="cuda")
+    fit = GridFit(prob, target, sigma=0.01, lr=0.05)
+    g0 = fit.grid.clone()
+    chi2 = fit.run(1)
+    # the first update is the oracle's Adam step on the gradient the fit used
+    want, _, _ = osur.adam_step(g0.cpu().numpy(), fit.g.cpu().numpy(), 0.0, 0.0, 1, 0.05)
+    np.testing.assert_allclose(fit.grid.cpu().numpy(), want, rtol=1e-5, atol=1e-6)
+    chi2 = torch.cat([chi2, fit.run(40)]).cpu().numpy()
+    assert chi2[0] == pytest.approx(oracle.chi2(oracle.forward(prob), target.cpu().numpy(), 0.01), rel=1e-4)
+    assert chi2[-1] < 0.5 * chi2[0], chi2[::8]
