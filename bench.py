@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-set ensemble measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the CPU oracle")
     ap.add_argument("--no-grid", action="store_true", help="skip the grid-model (Sec. 3.3) measurement")
+    ap.add_argument("--only-grid", action="store_true",
+                    help="run only the grid-model measurement (no interpolation study) and print its JSON")
+    ap.add_argument("--grid-runs", type=int, default=10, help="timed steps of the grid-model measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the learned surrogate")
     ap.add_argument("--surrogate-steps", type=int, default=20000, help="Adam steps of the surrogate training")
     ap.add_argument("--surrogate-maps", type=int, default=50000, help="training maps of the surrogate")
@@ -246,7 +249,7 @@ def bench_batch(sx, inputs, torch, dev, n_runs: int = 3, sets=None, name=None) -
     }
 
 
-def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
+def bench_grid(sx, inputs, torch, dev, n_runs: int = 10, n_fit: int = 50) -> dict:
     """The field-level workload (Sec. 3.3): B on 128 x 128 x 32 nodes over the
     (40, 40, 10) kpc box, Nside 64, 512 steps to the walls, Q/U at 2.4 GHz;
     one step = synax_adjoint_grid in chi^2 mode (maps, chi^2 against a mock
@@ -293,7 +296,6 @@ def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
     fit.run(3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_fit = 50
     e0.record(stream)
     chi2 = fit.run(n_fit)
     e1.record(stream)
@@ -314,7 +316,8 @@ def bench_grid(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
         "gpu_launches_per_step": 3,      # k_adjoint, k_reduce_partials, k_grid_unpad (plus a memset)
         "fit_ms_per_step": ms_fit,
         "fit_200_steps_s": 200 * ms_fit * 1e-3,
-        "fit_chi2_step4_step53": [float(chi2[0]), float(chi2[-1])],
+        "fit_chi2_first_last": [float(chi2[0]), float(chi2[-1])],
+        "fit_steps_timed": n_fit,
         "fit_note": "Adam, lr 0.05 uG, on the grid (synax_adam), back to back without L2 flushes",
         "l2": "flushed between steps (256 MiB write); the 6.3 MB grid is re-read from HBM",
     }
@@ -484,6 +487,11 @@ def run_synax(args):
     import paper_2410_01136_gb300 as sx
     from paper_2410_01136_gb300 import _native, inputs, tune
     sx.build()
+    if args.only_grid:
+        if rank == 0:
+            print(json.dumps({"grid": bench_grid(sx, inputs, torch, dev, max(args.grid_runs, 1),
+                                                 max(args.grid_runs, 1))}), flush=True)
+        return
     if args.only_surrogate:
         peaks = {}
         try:
