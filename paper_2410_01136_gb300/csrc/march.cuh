@@ -103,6 +103,12 @@ template <> struct M<float> {
     // 7.4e-5); the two n_e exponentials, which multiply the RM integrand
     // directly, keep expf (with ex2.approx there the 300 MHz error rose to 9.5e-5).
     static __device__ __forceinline__ float exp_shape(float x) { return ex2_approx(x * 1.4426950408889634f); }
+    // the same class for the other shape-factor operations: the PTX
+    // reciprocal and reciprocal square root without a Newton step, and a
+    // constant multiply without the lo part of the constant
+    static __device__ __forceinline__ float rcp_shape(float x) { return rcp_approx(x); }
+    static __device__ __forceinline__ float rsqrt_shape(float x) { return rsqrt_approx(x); }
+    static __device__ __forceinline__ float mul_shape(float x, double c) { return x * (float)c; }
     static __device__ __forceinline__ float rcp_fast(float x) { return rcp_approx(x); }
     static __device__ __forceinline__ float rsqrt_fast(float x) { return rsqrt_approx(x); }
     static __device__ __forceinline__ float atan2(float y, float x) { return atan2f(y, x); }
@@ -131,6 +137,9 @@ template <> struct M<double> {
     static __device__ __forceinline__ double mul_hl(double x, double hi, double lo) { return x * (hi + lo); }
     static __device__ __forceinline__ double exp2_fast(double x) { return ::exp2(x); }
     static __device__ __forceinline__ double exp_shape(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double rcp_shape(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double rsqrt_shape(double x) { return 1.0 / ::sqrt(x); }
+    static __device__ __forceinline__ double mul_shape(double x, double c) { return x * c; }
     static __device__ __forceinline__ double log2_fast(double x) { return ::log2(x); }
     static __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double rsqrt_fast(double x) { return ::rsqrt(x); }
@@ -480,8 +489,8 @@ constexpr double kArmDelta = 0.5;
 template <typename R>
 __device__ __forceinline__ void logistic_pair(R x, double h, double w, R& L, R& omL) {
     using F = M<R>;
-    const R e = F::exp_shape(F::mulc(x - R(h), 2.0 / w));    // e^{2(x-h)/w}, may be +inf
-    omL = e < R(1e30) ? F::rcp_nr(R(1) + e) : R(0);
+    const R e = F::exp_shape(F::mul_shape(x - R(h), 2.0 / w));    // e^{2(x-h)/w}, may be +inf
+    omL = e < R(1e30) ? F::rcp_shape(R(1) + e) : R(0);
     L = e > R(1) ? R(1) - omL : e * omL;
 }
 
@@ -765,7 +774,7 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         const R c = has_rho ? x * ri : R(1);
         const R s = has_rho ? y * ri : R(0);
         const R az = F::abs(z);
-        const R sz = z * F::rsqrt_nr(z * z + R(0.01));                    // smooth sign
+        const R sz = z * F::rsqrt_shape(z * z + R(0.01));                 // smooth sign
         R Lz, omLz;
         logistic_pair<R>(az, 0.4, 0.27, Lz, omLz);
         R br, bp, bz = R(0);
@@ -793,12 +802,12 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         // toroidal halo: (1 - L(rho; 9.22, 0.2)) is the second member of the pair
         R Lr, omLr;
         logistic_pair<R>(rho, 9.22, 0.2, Lr, omLr);
-        const R hu = F::exp_shape(-F::mul_hl(az, m[mc::J_IZH], m[mc::J_IZH_LO])) * Lz * omLr * sz;
+        const R hu = F::exp_shape(-(az * m[mc::J_IZH])) * Lz * omLr * sz;
         bp += m[mc::J_BH] * hu;
 
         // X field (no branch: xe = 0 where r_p <= 0 zeroes it and its gradient)
         const R rp = rho - az * m[mc::J_COTX];
-        const R xe = rp > R(0) ? F::exp_shape(-F::mulc(rp, 1.0 / 4.8)) : R(0);
+        const R xe = rp > R(0) ? F::exp_shape(-F::mul_shape(rp, 1.0 / 4.8)) : R(0);
         const R xu = xe * rp * ri;
         {
             const R mag = m[mc::J_BX] * xu;
@@ -1110,13 +1119,15 @@ __device__ __forceinline__ float2 smoothstep_unit(float2 t) {
 __device__ __forceinline__ float2 smoothstep_affine(float2 x, float a, float b) {
     return smoothstep_unit(f2(__saturatef(fmaf(x.x, a, b)), __saturatef(fmaf(x.y, a, b))));
 }
-// L(x; h, w) = 1/(1 + e^{-2(x-h)/w}) and 1 - L, each without cancellation.
-// The exponent is capped at 80 so that e stays finite (1 - L is then below
-// 2e-35, where it no longer matters) and no select is needed.
+// L(x; h, w) = 1/(1 + e^{-2(x-h)/w}) and 1 - L, each without cancellation,
+// with the shape-factor operations of M<float> (exp_shape, rcp_shape,
+// mul_shape).  The exponent is capped at 80 so that e stays finite (1 - L is
+// then below 2e-35, where it no longer matters) and no select is needed.
 __device__ __forceinline__ void logistic_pair(float2 x, double h, double w, float2& L, float2& omL) {
-    const float2 arg = mulc(add2(x, dup2(-(float)h)), 2.0 / w);
+    const float2 arg = mul2(add2(x, dup2(-(float)h)), dup2((float)(2.0 / w)));
     const float2 e = exp_shape2(f2(fminf(arg.x, 80.0f), fminf(arg.y, 80.0f)));
-    omL = rcp_nr(add2(dup2(1.0f), e));
+    const float2 ope = add2(dup2(1.0f), e);
+    omL = f2(rcp_approx(ope.x), rcp_approx(ope.y));
     L = mul2(e, omL);
 }
 
@@ -1132,7 +1143,8 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
     const float2 c = f2(rho2.x > 0.0f ? cq.x : 1.0f, rho2.y > 0.0f ? cq.y : 1.0f);
     const float2 s = f2(rho2.x > 0.0f ? sq.x : 0.0f, rho2.y > 0.0f ? sq.y : 0.0f);
     const float2 az = f2(fabsf(z.x), fabsf(z.y));
-    const float2 sz = mul2(z, rsqrt_nr(fma2(z, z, dup2(0.01f))));
+    const float2 szq = fma2(z, z, dup2(0.01f));
+    const float2 sz = mul2(z, f2(rsqrt_approx(szq.x), rsqrt_approx(szq.y)));
     float2 Lz, omLz;
     logistic_pair(az, 0.4, 0.27, Lz, omLz);
 
@@ -1155,13 +1167,13 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
     // toroidal halo
     float2 Lr, omLr;
     logistic_pair(rho, 9.22, 0.2, Lr, omLr);
-    const float2 hz = fma2(az, dup2(m[mc::J_IZH]), mul2(az, dup2(m[mc::J_IZH_LO])));
+    const float2 hz = mul2(az, dup2(m[mc::J_IZH]));
     const float2 hu = mul2(mul2(mul2(exp_shape2(neg2(hz)), Lz), omLr), sz);
     bp = fma2(dup2(m[mc::J_BH]), hu, bp);
 
     // X field
     const float2 rp = fma2(neg2(az), dup2(m[mc::J_COTX]), rho);
-    const float2 ex = exp_shape2(neg2(mulc(rp, 1.0 / 4.8)));
+    const float2 ex = exp_shape2(neg2(mul2(rp, dup2((float)(1.0 / 4.8)))));
     const float2 xe = f2(rp.x > 0.0f ? ex.x : 0.0f, rp.y > 0.0f ? ex.y : 0.0f);
     const float2 mag = mul2(dup2(m[mc::J_BX]), mul2(mul2(xe, rp), ri));
     br = fma2(mul2(mag, sz), dup2(m[mc::J_COSX]), br);
