@@ -45,7 +45,7 @@ FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 # DRAM bytes (read + write) of one k_adjoint launch of this workload, from the
 # ncu capture summarised in profiles/k_adjoint_jf12_nside64_512steps.md
-ADJ_DRAM_BYTES = 2.435e6
+ADJ_DRAM_BYTES = 2.439e6
 
 
 def parse():
