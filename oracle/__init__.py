@@ -19,7 +19,9 @@ the design notes.  The JF12-type field model is defined by this project, so
 its absolute values are "parity unpinned" beyond the invariants those tests
 check.  The grid model's interpolation is pinned by exactness on multilinear
 fields, by scipy's linear grid interpolator and by node values
-(``tests/test_oracle_grid.py``).
+(``tests/test_oracle_grid.py``); the stacked WMAP model of Sec. 4.3 by the
+magnitude, pitch and elevation of each of its Eq. 13 components and its
+stacking (``tests/test_oracle_wmap_stack.py``).
 """
 from __future__ import annotations
 
@@ -35,8 +37,8 @@ _SRC = os.path.join(_HERE, "synax_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-MODEL_TOY, MODEL_WMAP, MODEL_JF12, MODEL_GRID = 0, 1, 2, 3
-N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16, MODEL_GRID: 3}
+MODEL_TOY, MODEL_WMAP, MODEL_JF12, MODEL_GRID, MODEL_WMAP_STACK = 0, 1, 2, 3, 4
+N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16, MODEL_GRID: 3, MODEL_WMAP_STACK: 19}
 
 
 class _OracleProblem(ctypes.Structure):

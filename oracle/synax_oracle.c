@@ -57,6 +57,7 @@
 #define OR_MODEL_WMAP 1
 #define OR_MODEL_JF12 2
 #define OR_MODEL_GRID 3
+#define OR_MODEL_WMAP_STACK 4
 
 #define OR_MAX_FREQ  16
 #define OR_MAX_THETA 32
@@ -346,12 +347,55 @@ static void field_grid(const oracle_problem* P, const double r[3], double B[3], 
     *ne = P->theta[2] * exp(-rho / 20.0) * sech2(r[2] / 1.0);
 }
 
+/* Stacked WMAP model (Sec. 4.3, Eq. 16): four fields of the WMAP form of
+ * Eq. 13, each B_k = b0_k [cos psi_k cos chi_k rho^ + sin psi_k cos chi_k
+ * phi^ + sin chi_k z^] with psi_k = psi0_k + psi1_k ln(rho / 8 kpc) and
+ * chi_k = chi0B_k tanh(z / 1 kpc) for 3 <= rho <= 20 kpc (both zero
+ * otherwise; no envelope: |B_k| = b0_k), stacked with the weights and the
+ * component permutations of Eq. 16:
+ *   B_x = 0.6 B1_x + 0.3 B2_x + 0.1 B3_z + 0.3 B4_y
+ *   B_y = 0.6 B1_y + 0.3 B2_z + 0.1 B3_y + 0.3 B4_x
+ *   B_z = 0.6 B1_z + 0.3 B2_y + 0.1 B3_x + 0.3 B4_z
+ * theta = [b0, psi0, psi1, chi0B for k = 1..4 (uG, rad), N0_obs (cm^-3), p,
+ * ne0 (cm^-3)]; N0 and n_e as in the WMAP-type model. */
+static void wmap_component(const double* th4, double rho, const double rh[3], const double ph[3], double z,
+                           double Bk[3])
+{
+    double psi = 0.0, chi = 0.0;
+    if (rho >= 3.0 && rho <= 20.0) {
+        psi = th4[1] + th4[2] * log(rho / 8.0);
+        chi = th4[3] * tanh(z / 1.0);
+    }
+    for (int k = 0; k < 3; ++k) {
+        double zk = (k == 2) ? 1.0 : 0.0;
+        Bk[k] = th4[0] * (cos(psi) * cos(chi) * rh[k] + sin(psi) * cos(chi) * ph[k] + sin(chi) * zk);
+    }
+}
+
+static void field_wmap_stack(const double* th, const double r[3], const double obs[3],
+                             double B[3], double* N0, double* ne)
+{
+    double rho, rh[3], ph[3];
+    cyl_basis(r, &rho, rh, ph);
+    double B1[3], B2[3], B3[3], B4[3];
+    wmap_component(th + 0, rho, rh, ph, r[2], B1);
+    wmap_component(th + 4, rho, rh, ph, r[2], B2);
+    wmap_component(th + 8, rho, rh, ph, r[2], B3);
+    wmap_component(th + 12, rho, rh, ph, r[2], B4);
+    B[0] = 0.6 * B1[0] + 0.3 * B2[0] + 0.1 * B3[2] + 0.3 * B4[1];
+    B[1] = 0.6 * B1[1] + 0.3 * B2[2] + 0.1 * B3[1] + 0.3 * B4[0];
+    B[2] = 0.6 * B1[2] + 0.3 * B2[1] + 0.1 * B3[0] + 0.3 * B4[2];
+    *N0 = cr_density(r, obs, th[16]);
+    *ne = th[18] * exp(-rho / 20.0) * sech2(r[2] / 1.0);
+}
+
 static double spectral_index(const oracle_problem* P)
 {
     switch (P->model_id) {
     case OR_MODEL_TOY:  return P->theta[5];
     case OR_MODEL_WMAP: return P->theta[6];
     case OR_MODEL_GRID: return P->theta[1];
+    case OR_MODEL_WMAP_STACK: return P->theta[17];
     default:            return P->theta[13];
     }
 }
@@ -364,6 +408,7 @@ int oracle_fields(const oracle_problem* P, const double r[3], double t,
     case OR_MODEL_TOY:  field_toy(P->theta, t, B, N0, ne); return 0;
     case OR_MODEL_WMAP: field_wmap(P->theta, r, P->obs_kpc, B, N0, ne); return 0;
     case OR_MODEL_JF12: field_jf12(P->theta, r, P->obs_kpc, B, N0, ne); return 0;
+    case OR_MODEL_WMAP_STACK: field_wmap_stack(P->theta, r, P->obs_kpc, B, N0, ne); return 0;
     case OR_MODEL_GRID:
         if (!P->grid) return -1;
         field_grid(P, r, B, N0, ne);
@@ -493,8 +538,8 @@ static int or_validate(const oracle_problem* P)
     if (P->nside < 1 || P->nside > 8192) return -1;
     if (P->n_steps < 1) return -1;
     if (P->n_freq < 1 || P->n_freq > OR_MAX_FREQ) return -1;
-    if (P->model_id < OR_MODEL_TOY || P->model_id > OR_MODEL_GRID) return -1;
-    static const int need[4] = {7, 8, 16, 3};
+    if (P->model_id < OR_MODEL_TOY || P->model_id > OR_MODEL_WMAP_STACK) return -1;
+    static const int need[5] = {7, 8, 16, 3, 19};
     if (P->n_theta != need[P->model_id]) return -1;
     if (!P->box_clip && !(P->r_max_kpc > 0.0)) return -1;
     if (P->model_id == OR_MODEL_GRID) {

@@ -18,8 +18,8 @@ import math
 
 import numpy as np
 
-MODEL_TOY, MODEL_WMAP, MODEL_JF12, MODEL_GRID = 0, 1, 2, 3
-N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16, MODEL_GRID: 3}
+MODEL_TOY, MODEL_WMAP, MODEL_JF12, MODEL_GRID, MODEL_WMAP_STACK = 0, 1, 2, 3, 4
+N_THETA = {MODEL_TOY: 7, MODEL_WMAP: 8, MODEL_JF12: 16, MODEL_GRID: 3, MODEL_WMAP_STACK: 19}
 
 #: Parameter names of each model, in theta order.
 THETA_NAMES = {
@@ -28,10 +28,12 @@ THETA_NAMES = {
     MODEL_JF12: [f"b{k + 1}" for k in range(8)]
     + ["B_h", "z_h", "B_X", "theta_X", "N0_obs", "p", "h1", "h2"],
     MODEL_GRID: ["N0_obs", "p", "ne0"],
+    MODEL_WMAP_STACK: [f"{n}_{k}" for k in range(1, 5) for n in ("b0", "psi0", "psi1", "chi0B")]
+    + ["N0_obs", "p", "ne0"],
 }
 
 #: Index of the CR spectral index p in each model's theta.
-P_INDEX = {MODEL_TOY: 5, MODEL_WMAP: 6, MODEL_JF12: 13, MODEL_GRID: 1}
+P_INDEX = {MODEL_TOY: 5, MODEL_WMAP: 6, MODEL_JF12: 13, MODEL_GRID: 1, MODEL_WMAP_STACK: 17}
 
 OBS_PAPER_KPC = (-8.3, 0.0, 0.006)      # Sec. 2.1
 OBS_CONFIG_KPC = (-8.5, 0.0, 0.015)     # synthetic workloads
@@ -352,3 +354,27 @@ def grid_problem(nside: int = 64, n_steps: int = 512, freq_hz=(2.4e9,), n=GRID_P
     return Problem(nside=nside, n_steps=n_steps, freq_hz=freq_hz, model_id=MODEL_GRID,
                    theta=kw.pop("theta", grid_theta()), box_clip=True, grid=kw.pop("grid", grid_field(n, seed)),
                    **kw)
+
+
+# ---------------------------------------------------------------------------
+# stacked WMAP model (Sec. 4.3, Eq. 16)
+# ---------------------------------------------------------------------------
+
+#: b0 (uG), psi0, psi1, chi0B (rad) of the four WMAP fields (Sec. 4.3, table of model parameters).
+WMAP_STACK_TABLE = ((1.20, 0.4712, 0.0157, 0.4363),
+                    (3.50, 0.6457, 0.5393, 0.6108),
+                    (7.70, 1.1693, 1.0629, 1.1344),
+                    (5.70, 1.6930, 1.5865, 1.6580))
+
+
+def wmap_stack_theta(N0_obs: float = N0_EARTH, p: float = 3.0, ne0: float = 0.03) -> np.ndarray:
+    """The 16 field parameters of Sec. 4.3's table, then N0_obs, p, ne0."""
+    return np.array([v for row in WMAP_STACK_TABLE for v in row] + [N0_obs, p, ne0], dtype=np.float64)
+
+
+def wmap_stack_problem(nside: int = 64, n_steps: int = 512, freq_hz=(2.4e9,), **kw) -> Problem:
+    """Sec. 4.3's workload: the stacked model in the (40, 40, 10) kpc box,
+    Nside 64, 512 steps, Q/U at 2.4 GHz, observer as in Sec. 2.1."""
+    return Problem(nside=nside, n_steps=n_steps, freq_hz=freq_hz, model_id=MODEL_WMAP_STACK,
+                   theta=kw.pop("theta", wmap_stack_theta()), box_clip=kw.pop("box_clip", True),
+                   obs_kpc=kw.pop("obs_kpc", OBS_PAPER_KPC), **kw)
