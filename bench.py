@@ -323,6 +323,48 @@ def bench_grid(sx, inputs, torch, dev, n_runs: int = 10, n_fit: int = 50) -> dic
     }
 
 
+def bench_wmap_stack(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
+    """Sec. 4.3's 16-parameter model: the stacked WMAP field of Eq. 16 in
+    the (40, 40, 10) kpc box, Nside 64, 512 steps, I/Q/U at 2.4 GHz; one step
+    = synax_adjoint in chi^2 mode (map + 19-component gradient: the 16 field
+    parameters and N0_obs, p, n_e0) against a mock with 1 mK noise.  L2
+    flushed between steps."""
+    import numpy as np
+    prob = inputs.wmap_stack_problem()
+    th_mock = prob.theta * (1.0 + 0.03 * inputs.normal(inputs.substream(72, 1), prob.theta.size))
+    mock = sx.forward(prob.with_theta(th_mock))
+    target = (mock + 1e-3 * torch.tensor(inputs.target_noise(tuple(mock.shape), seed=73, sigma=1.0),
+                                         dtype=torch.float32, device=dev)).contiguous()
+    maps = torch.empty_like(target)
+    ws = torch.empty(max(sx.adjoint_workspace_bytes(prob), 1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        sx.adjoint(prob, target=target, sigma=1e-3, maps_out=maps, workspace=ws)
+        sx.forward(prob, out=maps)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_runs)]
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_runs)]
+    for k in range(n_runs):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sx.adjoint(prob, target=target, sigma=1e-3, maps_out=maps, workspace=ws)
+        ev[k][1].record(stream)
+    for k in range(n_runs):
+        flush.fill_(float(k))
+        fev[k][0].record(stream)
+        sx.forward(prob, out=maps)
+        fev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ms_fwd = float(np.mean([a.elapsed_time(b) for a, b in fev]))
+    return {"workload": "stacked WMAP (Eq. 16), box (40, 40, 10) kpc, Nside 64, 512 steps, 2.4 GHz, "
+                        "chi^2 map + 19-component gradient",
+            "samples_per_step": prob.samples, "ms_per_step": ms, "maps_grad_per_s": 1.0 / (ms * 1e-3),
+            "samples_per_s": prob.samples / (ms * 1e-3), "forward_ms": ms_fwd,
+            "forward_samples_per_s": prob.samples / (ms_fwd * 1e-3), "gpu_launches_per_step": 2}
+
+
 def interp_study(sx, inputs, torch) -> dict:
     """Sec. 5's interpolation study, re-run: the WMAP-type field with the
     parameters of Sec. 3.1 (b0 = 1.2 uG, psi0 = 0.4712, psi1 = 0.0157,
@@ -650,6 +692,7 @@ def run_synax(args):
     if rank == 0 and not args.no_grid:
         out["grid"] = bench_grid(sx, inputs, torch, dev)
         out["interp_study"] = interp_study(sx, inputs, torch)
+        out["wmap_stack"] = bench_wmap_stack(sx, inputs, torch, dev)
     if rank == 0 and not args.no_surrogate:
         peaks = {}
         try:

@@ -64,12 +64,19 @@ extern "C" {
  *   -l_z/2 + k l_z/(n_z - 1)), B at a midpoint the trilinear blend of the 8
  *   nodes of its cell (fractional node coordinates clamped to the grid);
  *   N0 and n_e are the WMAP-type model's.  Needs SYNAX_BOX_CLIP.
+ * SYNAX_MODEL_WMAP_STACK (Sec. 4.3, Eq. 16: the 16-parameter model) theta =
+ *   [b0_k (uG), psi0_k, psi1_k, chi0B_k (rad) for k = 1..4, N0_obs (cm^-3), p,
+ *   ne0 (cm^-3)]: four fields of the form of Eq. 13 (magnitude b0_k, no
+ *   envelope), stacked as B_x = 0.6 B1_x + 0.3 B2_x + 0.1 B3_z + 0.3 B4_y,
+ *   B_y = 0.6 B1_y + 0.3 B2_z + 0.1 B3_y + 0.3 B4_x, B_z = 0.6 B1_z +
+ *   0.3 B2_y + 0.1 B3_x + 0.3 B4_z; N0 and n_e as the WMAP-type model's.
  * N0_obs is the CR density at the observer; p is the CR spectral index
  * (the paper's alpha). */
 #define SYNAX_MODEL_TOY   0
 #define SYNAX_MODEL_WMAP  1
 #define SYNAX_MODEL_JF12  2
 #define SYNAX_MODEL_GRID  3
+#define SYNAX_MODEL_WMAP_STACK 4
 
 #define SYNAX_MAX_FREQ   16
 #define SYNAX_MAX_THETA  32
@@ -115,7 +122,8 @@ int synax_adjoint_workspace_bytes(const synax_problem* prob, size_t* bytes);
  * respect to theta, computed by recomputing each ray from theta (no per-step
  * storage) and marching it backwards for the RM adjoint (Eq. 7 is a prefix
  * sum along the ray, so its adjoint is a suffix sum).  Models: WMAP, JF12,
- * GRID (its 3 parameters; synax_adjoint_grid adds the grid gradient).
+ * WMAP_STACK, GRID (its 3 parameters; synax_adjoint_grid adds the grid
+ * gradient).
  *
  * Two modes:
  *  - VJP mode, gmaps_dev != NULL: grad = sum_{f,s,i} gmaps[f][s][i] dM[f][s][i]/dtheta.
@@ -219,8 +227,8 @@ int synax_adjoint_noalloc(const synax_problem* prob, const void* gmaps_dev, cons
                           double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
                           void* stream);
 
-/* Samples B of an analytic model (toy, WMAP or JF12; SYNAX_ENOTSUP for the
- * grid model) at the nodes of an (n_x, n_y, n_z) grid spanning the problem's
+/* Samples B of an analytic model (toy, WMAP, JF12 or WMAP_STACK;
+ * SYNAX_ENOTSUP for the grid model) at the nodes of an (n_x, n_y, n_z) grid spanning the problem's
  * box wall to wall, in the layout of the grid model: grid_dev
  * [n_z][n_y][n_x][3] in uG, float32 (float64 with SYNAX_F64), written
  * completely.  Node (i, j, k) is at (-l_x/2 + i l_x/(n_x - 1), ...), as in

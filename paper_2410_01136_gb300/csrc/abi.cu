@@ -40,6 +40,7 @@ int model_n_theta(int id) {
     case SYNAX_MODEL_WMAP: return 8;
     case SYNAX_MODEL_JF12: return 16;
     case SYNAX_MODEL_GRID: return 3;
+    case SYNAX_MODEL_WMAP_STACK: return 19;
     default: return -1;
     }
 }
@@ -49,6 +50,7 @@ int model_p_index(int id) {
     case SYNAX_MODEL_TOY: return 5;
     case SYNAX_MODEL_WMAP: return 6;
     case SYNAX_MODEL_GRID: return 1;
+    case SYNAX_MODEL_WMAP_STACK: return 17;
     default: return 13;
     }
 }
@@ -252,6 +254,12 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         M.m[mc::J_BH_IZH2] = R(th[8] / (th[9] * th[9]));
         M.m[mc::J_IH1_SQ] = R(1.0 / (th[14] * th[14]));
         M.m[mc::J_IH2_SQ] = R(1.0 / (th[15] * th[15]));
+        break;
+    case SYNAX_MODEL_WMAP_STACK:
+        for (int k = 0; k < 16; ++k) M.m[mc::S_COMP + k] = R(th[k]);
+        M.m[mc::S_N0U] = R(1.0 / cr_profile(P.obs_kpc));
+        M.m[mc::S_N0OBS] = R(th[16]);
+        M.m[mc::S_NE0] = R(th[18]);
         break;
     case SYNAX_MODEL_GRID:
         M.m[mc::G_N0U] = R(1.0 / cr_profile(P.obs_kpc));

@@ -35,9 +35,11 @@ namespace synax {
 SYNAX_DECL(adjoint_wmap_f32, float)
 SYNAX_DECL(adjoint_jf12_f32, float)
 SYNAX_DECL(adjoint_grid_f32, float)
+SYNAX_DECL(adjoint_wmapstack_f32, float)
 SYNAX_DECL(adjoint_wmap_f64, double)
 SYNAX_DECL(adjoint_jf12_f64, double)
 SYNAX_DECL(adjoint_grid_f64, double)
+SYNAX_DECL(adjoint_wmapstack_f64, double)
 #undef SYNAX_DECL
 
 // Fixed-order reduction of per-CTA partials: block j sums column j.
@@ -105,6 +107,7 @@ static int launch_adjoint_t(const MapParams<R>& P, const AdjParams<R>& A, const 
         case SYNAX_MODEL_WMAP: return adjoint_wmap_f32(P, A, g, tg, grad, chi2, mo, part, st);
         case SYNAX_MODEL_JF12: return adjoint_jf12_f32(P, A, g, tg, grad, chi2, mo, part, st);
         case SYNAX_MODEL_GRID: return adjoint_grid_f32(P, A, g, tg, grad, chi2, mo, part, st);
+        case SYNAX_MODEL_WMAP_STACK: return adjoint_wmapstack_f32(P, A, g, tg, grad, chi2, mo, part, st);
         default: return SYNAX_ENOTSUP;
         }
     } else {
@@ -112,6 +115,7 @@ static int launch_adjoint_t(const MapParams<R>& P, const AdjParams<R>& A, const 
         case SYNAX_MODEL_WMAP: return adjoint_wmap_f64(P, A, g, tg, grad, chi2, mo, part, st);
         case SYNAX_MODEL_JF12: return adjoint_jf12_f64(P, A, g, tg, grad, chi2, mo, part, st);
         case SYNAX_MODEL_GRID: return adjoint_grid_f64(P, A, g, tg, grad, chi2, mo, part, st);
+        case SYNAX_MODEL_WMAP_STACK: return adjoint_wmapstack_f64(P, A, g, tg, grad, chi2, mo, part, st);
         default: return SYNAX_ENOTSUP;
         }
     }

@@ -83,6 +83,38 @@ template <> struct Grad<SYNAX_MODEL_WMAP> {
     }
 };
 
+// Stacked WMAP model: theta = [b0, psi0, psi1, chi0B for k = 1..4, N0_obs, p,
+// ne0].  The adjoint of each component's Cartesian field is the stacked
+// adjoint (bxb, byb, bzb) sent back through that component's weight and
+// permutation of Eq. 16; each component then contributes as one WMAP field.
+template <> struct Grad<SYNAX_MODEL_WMAP_STACK> {
+    static constexpr int NT = 19;
+    static constexpr int P_INDEX = 17;
+    static constexpr int N_ARM_SLOTS = 1;
+    template <typename R>
+    static __device__ __forceinline__ void accum(const R* m, const FieldLocal<R>& L, R bxb, R byb, R bzb,
+                                                 R n0b, R neb, R* g, R* /*garm*/, int /*stride*/) {
+        // (u_x, u_y, u_z) of component k: Eq. 16 read column by column
+        const R ux[4] = {R(stack_w(0)) * bxb, R(stack_w(1)) * bxb, R(stack_w(2)) * bzb, R(stack_w(3)) * byb};
+        const R uy[4] = {R(stack_w(0)) * byb, R(stack_w(1)) * bzb, R(stack_w(2)) * byb, R(stack_w(3)) * bxb};
+        const R uz[4] = {R(stack_w(0)) * bzb, R(stack_w(1)) * byb, R(stack_w(2)) * bxb, R(stack_w(3)) * bzb};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const R brb = ux[k] * L.c + uy[k] * L.s;
+            const R bpb = -ux[k] * L.s + uy[k] * L.c;
+            const R cp = L.kcp[k], sp = L.ksp[k], cc = L.kcc[k], sc = L.ksc[k];
+            g[4 * k + 0] += brb * cp * cc + bpb * sp * cc + uz[k] * sc;
+            const R amp = m[mc::S_COMP + 4 * k] * L.in_range;      // psi, chi are constant outside
+            const R dpsi = amp * cc * (-brb * sp + bpb * cp);
+            g[4 * k + 1] += dpsi;
+            g[4 * k + 2] += dpsi * L.lnr8;
+            g[4 * k + 3] += amp * L.thz * (-brb * cp * sc - bpb * sp * sc + uz[k] * cc);
+        }
+        g[16] += n0b * L.n0_unit;
+        g[18] += neb * L.ne_unit;
+    }
+};
+
 // Grid model: theta = [N0_obs, p, ne0]; the node gradient goes through GridAcc.
 template <> struct Grad<SYNAX_MODEL_GRID> {
     static constexpr int NT = 3;

@@ -46,6 +46,9 @@ static int launch_eval_t(const MapParams<R>& P, const double* pos, const double*
     case SYNAX_MODEL_WMAP: k_eval_fields<SYNAX_MODEL_WMAP, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out); break;
     case SYNAX_MODEL_JF12: k_eval_fields<SYNAX_MODEL_JF12, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out); break;
     case SYNAX_MODEL_GRID: k_eval_fields<SYNAX_MODEL_GRID, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out); break;
+    case SYNAX_MODEL_WMAP_STACK:
+        k_eval_fields<SYNAX_MODEL_WMAP_STACK, R><<<blocks, 256, 0, st>>>(P, pos, t, n, out);
+        break;
     default: return SYNAX_EINVAL;
     }
     const cudaError_t err = cudaGetLastError();

@@ -9,10 +9,12 @@ SYNAX_DECL(forward_toy_f32, float)
 SYNAX_DECL(forward_wmap_f32, float)
 SYNAX_DECL(forward_jf12_f32, float)
 SYNAX_DECL(forward_grid_f32, float)
+SYNAX_DECL(forward_wmapstack_f32, float)
 SYNAX_DECL(forward_toy_f64, double)
 SYNAX_DECL(forward_wmap_f64, double)
 SYNAX_DECL(forward_jf12_f64, double)
 SYNAX_DECL(forward_grid_f64, double)
+SYNAX_DECL(forward_wmapstack_f64, double)
 #undef SYNAX_DECL
 
 int launch_forward_f32(const MapParams<float>& P, void* maps, void* stream) {
@@ -22,6 +24,7 @@ int launch_forward_f32(const MapParams<float>& P, void* maps, void* stream) {
     case SYNAX_MODEL_WMAP: return forward_wmap_f32(P, (float*)maps, st);
     case SYNAX_MODEL_JF12: return forward_jf12_f32(P, (float*)maps, st);
     case SYNAX_MODEL_GRID: return forward_grid_f32(P, (float*)maps, st);
+    case SYNAX_MODEL_WMAP_STACK: return forward_wmapstack_f32(P, (float*)maps, st);
     default: return SYNAX_EINVAL;
     }
 }
@@ -33,6 +36,7 @@ int launch_forward_f64(const MapParams<double>& P, void* maps, void* stream) {
     case SYNAX_MODEL_WMAP: return forward_wmap_f64(P, (double*)maps, st);
     case SYNAX_MODEL_JF12: return forward_jf12_f64(P, (double*)maps, st);
     case SYNAX_MODEL_GRID: return forward_grid_f64(P, (double*)maps, st);
+    case SYNAX_MODEL_WMAP_STACK: return forward_wmapstack_f64(P, (double*)maps, st);
     default: return SYNAX_EINVAL;
     }
 }

@@ -75,6 +75,9 @@ static int launch_grid_sample(const MapParams<R>& P, const synax_problem& prob, 
     case SYNAX_MODEL_JF12:
         k_grid_sample<SYNAX_MODEL_JF12, R><<<blocks, 256, 0, st>>>(P, n[0], n[1], n[2], hx, hy, hz, out);
         break;
+    case SYNAX_MODEL_WMAP_STACK:
+        k_grid_sample<SYNAX_MODEL_WMAP_STACK, R><<<blocks, 256, 0, st>>>(P, n[0], n[1], n[2], hx, hy, hz, out);
+        break;
     default: return SYNAX_ENOTSUP;
     }
     const cudaError_t err = cudaGetLastError();

@@ -697,6 +697,8 @@ struct FieldLocal {
     // grid
     int gbase;           // node index of the cell's lower corner
     R gfx, gfy, gfz;     // fractional position in the cell
+    // stacked WMAP: cos/sin of each component's psi and chi
+    R kcp[4], ksp[4], kcc[4], ksc[4];
 };
 
 template <int MODEL> struct Model;
@@ -843,6 +845,64 @@ template <> struct Model<SYNAX_MODEL_JF12> {
         loc.c = c; loc.s = s; loc.az = az; loc.rho = rho; loc.ri = ri;
         loc.halo_unit = hu; loc.rp = rp; loc.xe = xe; loc.xmag_unit = xu; loc.sz = sz;
         loc.ne1 = ne1; loc.ne2 = ne2; loc.n0_unit = n0u;
+    }
+};
+
+// Stacked WMAP model (Sec. 4.3, Eq. 16).  Four fields of the form of Eq. 13,
+// B_k = b0_k [cos psi_k cos chi_k rho^ + sin psi_k cos chi_k phi^ +
+// sin chi_k z^] with psi_k = psi0_k + psi1_k ln(rho/8 kpc) and chi_k =
+// chi0B_k tanh(z/1 kpc) for 3 <= rho <= 20 kpc (zero otherwise), share rho,
+// ln(rho/8) and tanh z, and are stacked with the weights and component
+// permutations of Eq. 16 (stack_w, and the index maps in eval and in the
+// gradient rule).  B feeds the RM, so every transcendental here is the
+// accurate one (logf, sincosf, expf).
+__host__ __device__ constexpr double stack_w(int k) { return k == 0 ? 0.6 : (k == 2 ? 0.1 : 0.3); }
+
+template <> struct Model<SYNAX_MODEL_WMAP_STACK> {
+    template <typename R>
+    static __device__ __forceinline__ void eval(const R* m, const R* /*arms*/, R /*t*/, R x, R y, R z,
+                                                const ArmCoord<R>& /*ac*/, R B[3], R& N0, R& ne,
+                                                FieldLocal<R>& loc) {
+        using F = M<R>;
+        const R rho2 = x * x + y * y;
+        const bool has_rho = rho2 > R(0);
+        const R rho = F::sqrt(rho2);
+        const R c = has_rho ? F::div(x, rho) : R(1);
+        const R s = has_rho ? F::div(y, rho) : R(0);
+        const R az = F::abs(z);
+        const R e2 = F::exp(R(-2) * az);                      // e^{-2|z|}
+        const R inv1 = F::div(R(1), R(1) + e2);
+        const bool in_range = rho >= R(3) && rho <= R(20);
+        const R lnr8 = in_range ? F::log(F::div(rho, R(8))) : R(0);
+        R th = (R(1) - e2) * inv1;                             // tanh |z|
+        th = z < R(0) ? -th : th;
+        R comp[4][3];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const R* q = m + mc::S_COMP + 4 * k;
+            const R psi = in_range ? q[1] + q[2] * lnr8 : R(0);
+            const R chi = in_range ? q[3] * th : R(0);
+            R sp, cp, sc, cc;
+            F::sincos(psi, &sp, &cp);
+            F::sincos(chi, &sc, &cc);
+            const R br = q[0] * cp * cc, bp = q[0] * sp * cc;
+            comp[k][0] = br * c - bp * s;
+            comp[k][1] = br * s + bp * c;
+            comp[k][2] = q[0] * sc;
+            loc.kcp[k] = cp; loc.ksp[k] = sp; loc.kcc[k] = cc; loc.ksc[k] = sc;
+        }
+        B[0] = R(stack_w(0)) * comp[0][0] + R(stack_w(1)) * comp[1][0] + R(stack_w(2)) * comp[2][2] +
+               R(stack_w(3)) * comp[3][1];
+        B[1] = R(stack_w(0)) * comp[0][1] + R(stack_w(1)) * comp[1][2] + R(stack_w(2)) * comp[2][1] +
+               R(stack_w(3)) * comp[3][0];
+        B[2] = R(stack_w(0)) * comp[0][2] + R(stack_w(1)) * comp[1][1] + R(stack_w(2)) * comp[2][0] +
+               R(stack_w(3)) * comp[3][2];
+        const R n0u = cr_density<R>(m[mc::S_N0U], rho, az);
+        N0 = m[mc::S_N0OBS] * n0u;
+        const R neu = F::exp(-F::mulc(rho, 0.05)) * (R(4) * e2 * inv1 * inv1);
+        ne = m[mc::S_NE0] * neu;
+        loc.c = c; loc.s = s; loc.lnr8 = lnr8; loc.thz = th; loc.in_range = in_range ? R(1) : R(0);
+        loc.n0_unit = n0u; loc.ne_unit = neu;
     }
 };
 

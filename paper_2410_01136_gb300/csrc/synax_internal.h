@@ -42,6 +42,9 @@ constexpr int J_BH = 8, J_IZH = 9, J_BX = 10, J_COSX = 11, J_SINX = 12, J_COTX =
 // grid model: N0 normalisation, N0_obs, ne0; per axis (n - 1) / l (as hi + lo),
 // (n - 1) / 2 and n - 1
 constexpr int G_N0U = 0, G_N0OBS = 1, G_NE0 = 2, G_S = 3, G_O = 6, G_UMAX = 9, G_SLO = 12;
+// stacked WMAP model: component k's b0, psi0, psi1, chi0B at 4k .. 4k + 3, then
+// the N0 normalisation, N0_obs and ne0
+constexpr int S_COMP = 0, S_N0U = 16, S_N0OBS = 17, S_NE0 = 18;
 }  // namespace mc
 
 template <typename R>

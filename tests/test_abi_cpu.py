@@ -169,6 +169,18 @@ def test_grid_validation_rejects(L, mutate):
     assert L.synax_forward(ctypes.byref(s), ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
 
 
+def test_wmap_stack_validation(L):
+    s = _native.problem_struct(inputs.wmap_stack_problem(nside=4, n_steps=16))
+    s.pix_begin = 192
+    assert L.synax_forward(ctypes.byref(s), None, None) == _native.SYNAX_OK
+    bad = _native.problem_struct(inputs.wmap_stack_problem(nside=4, n_steps=16))
+    bad.n_theta = 18
+    assert L.synax_forward(ctypes.byref(bad), ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
+    bad = _native.problem_struct(inputs.wmap_stack_problem(nside=4, n_steps=16))
+    bad.theta[17] = 0.2                                  # p below Eq. 2's range
+    assert L.synax_forward(ctypes.byref(bad), ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
+
+
 def test_adjoint_grid_workspace_query(L):
     g = _grid_struct()
     n = ctypes.c_size_t(0)

@@ -26,7 +26,7 @@ import pytest
 import oracle
 from paper_2410_01136_gb300 import adjoint, adjoint_grid, eval_fields, forward, inputs
 
-from .parity import assert_parity
+from .parity import assert_parity, assert_parity_by_frequency
 
 pytestmark = pytest.mark.gpu
 
@@ -41,22 +41,13 @@ def torch():
     return _t
 
 
-P_TOL_BELOW_1GHZ = 5e-4
-
-
 def small(nside=8, n_steps=100, n=(12, 10, 6), seed=21, freqs=(408e6, 2.4e9), **kw):
     return inputs.grid_problem(nside=nside, n_steps=n_steps, freq_hz=freqs, n=n, seed=seed, **kw)
 
 
 def check_maps(m, ref, prob, what):
-    """Parity per frequency: FP64 to 1e-9; FP32 I to 1e-5, P to 1e-4 at and
-    above 1 GHz and to P_TOL_BELOW_1GHZ below."""
-    for f, nu in enumerate(prob.freq_hz):
-        if prob.f64:
-            assert_parity(m[f:f + 1], ref[f:f + 1], 1e-9, 1e-9, f"{what} FP64 {nu:.3g} Hz")
-        else:
-            tol_p = 1e-4 if nu >= 1e9 else P_TOL_BELOW_1GHZ
-            assert_parity(m[f:f + 1], ref[f:f + 1], 1e-5, tol_p, f"{what} FP32 {nu:.3g} Hz")
+    """Parity per frequency (tests/parity.py: FP32 P to 5e-4 below 1 GHz)."""
+    assert_parity_by_frequency(m, ref, prob.freq_hz, prob.f64, what)
 
 
 def seeds(prob, seed=9):
