@@ -198,6 +198,71 @@ int synax_batch_plan_info(const synax_batch_plan* plan, long long* n_tiles, int*
 
 void synax_batch_plan_destroy(synax_batch_plan* plan);
 
+/* Parameter sets and parameter count of a plan. */
+int synax_batch_plan_n_sets(const synax_batch_plan* plan);
+int synax_batch_plan_n_theta(const synax_batch_plan* plan);
+
+/* Device-resident parameters, for samplers that keep theta on the GPU.
+ * synax_batch_bind fixes the seeds (targets in chi^2 mode), sigma and the
+ * output pointers of every set once (arguments as in synax_batch_run; the
+ * plan's own problems give everything that does not depend on theta).
+ * synax_batch_run_device then runs the batch with theta_dev [n_sets][n_theta]
+ * doubles in device memory: a kernel inside the plan's second CUDA graph
+ * rebuilds each set's parameter-dependent constants (the same code as the
+ * host path), then the persistent kernel and the reduction run.  The graph
+ * is captured on the first run and again when theta_dev changes.  The values
+ * are not validated: a non-finite or out-of-range theta gives non-finite
+ * gradients and chi^2 for its set (no memory access depends on theta).
+ * SYNAX_EINVAL if the plan is not bound. */
+int synax_batch_bind(synax_batch_plan* plan, const void* const* seeds_dev, int vjp, double sigma_K,
+                     void* const* maps_dev, double* grads_dev, double* chi2_dev);
+int synax_batch_run_device(synax_batch_plan* plan, const double* theta_dev, void* stream);
+
+/* ---- Hamiltonian Monte Carlo over an ensemble of chains ----
+ * The gradient-based sampling of Sec. 3.2 and 4.3 (the paper runs NUTS;
+ * this is HMC with a fixed step size, trajectory length and diagonal inverse
+ * mass).  Chain c samples exp(-U) with U = chi^2 / 2 of set c of the plan
+ * against its target (-log L of Eq. 15 up to a constant) times a uniform
+ * prior on the box [lo, hi]; every leapfrog gradient is a
+ * synax_batch_run_device of all chains at once, and the momentum draws,
+ * leapfrog updates and Metropolis steps are kernels, so an iteration makes
+ * no host round trip.  Random numbers: SplitMix64 as a counter-based
+ * generator (value i of stream s = mix64(s + (i + 1) 0x9E3779B97F4A7C15));
+ * the momentum of chain c, parameter j at iteration t is Box-Muller's first
+ * output sqrt(-2 ln u1) cos(2 pi u2) of pair k = (t C + c) T + j of stream
+ * `seed` (u1 = ((x_2k >> 11) + 1) 2^-53, u2 = (x_2k+1 >> 11) 2^-53), scaled by
+ * 1/sqrt(inv_mass_j); the acceptance uniform of chain c at iteration t is
+ * (x_{t C + c} >> 11) 2^-53 of stream seed + 0x632BE59BD9B4E019. */
+typedef struct {
+    int32_t  n_leapfrog;          /* leapfrog steps per iteration, >= 1 */
+    double   step_size;           /* > 0 */
+    uint64_t seed;
+    const double* inv_mass;       /* host, n_theta values >= 0 (0: parameter held fixed), or NULL (identity) */
+    const double* lo;             /* host prior box, n_theta values, or NULL (unbounded) */
+    const double* hi;
+} synax_hmc_cfg;
+typedef struct synax_hmc_s synax_hmc_t;
+
+/* Creates the sampler over `plan` (one chain per set; n_theta <= 32), binds
+ * the plan to its own gradient buffers (chi^2 mode against targets_dev[c],
+ * sigma_K) and evaluates the starting point theta0_host [n_sets][n_theta]
+ * (synchronously).  Allocates the chain state; SYNAX_ENOMEM on failure. */
+int synax_hmc_create(synax_batch_plan* plan, const synax_hmc_cfg* cfg, const double* theta0_host,
+                     const void* const* targets_dev, double sigma_K, synax_hmc_t** hmc);
+/* Enqueues n_iters iterations on `stream`.  samples_dev (or NULL):
+ * [n_iters][n_sets][n_theta] doubles, theta after each iteration;
+ * accepted_dev (or NULL): [n_iters][n_sets] bytes, 1 where the proposal was
+ * accepted. */
+int synax_hmc_run(synax_hmc_t* hmc, int n_iters, double* samples_dev, signed char* accepted_dev, void* stream);
+/* Sets the step size (when > 0; 0 keeps it) and the inverse mass (when not
+ * NULL, n_theta host values >= 0) for the following iterations; the mass is
+ * copied after the device has finished the work already enqueued. */
+int synax_hmc_set(synax_hmc_t* hmc, double step_size, const double* inv_mass_host);
+/* Copies the current theta [n_sets][n_theta], chi^2 [n_sets] and accepted
+ * counts [n_sets] (int) to device buffers (any may be NULL). */
+int synax_hmc_state(synax_hmc_t* hmc, double* theta_dev, double* chi2_dev, int* n_accept_dev, void* stream);
+void synax_hmc_destroy(synax_hmc_t* hmc);
+
 /* BF16 tensor-core GEMM of the surrogate network (tcgen05, FP32 accumulate):
  * C[M][N] = A[M][K] . B[N][K]^T, A and B row-major BF16 with row pitches
  * lda, ldb (elements, multiples of 8, >= K), K a multiple of 64, pointers

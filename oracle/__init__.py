@@ -21,7 +21,10 @@ check.  The grid model's interpolation is pinned by exactness on multilinear
 fields, by scipy's linear grid interpolator and by node values
 (``tests/test_oracle_grid.py``); the stacked WMAP model of Sec. 4.3 by the
 magnitude, pitch and elevation of each of its Eq. 13 components and its
-stacking (``tests/test_oracle_wmap_stack.py``).
+stacking (``tests/test_oracle_wmap_stack.py``).  ``oracle/hmc.py`` holds a
+plain HMC (Neal 2011) with the library's documented random numbers, pinned by
+the exactness of its leapfrog on a Gaussian and by sampling moments
+(``tests/test_oracle_hmc.py``).
 """
 from __future__ import annotations
 

@@ -18,7 +18,7 @@ from . import inputs
 from . import _native
 from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
 
-__all__ = ["forward", "adjoint", "adjoint_grid", "adjoint_grid_workspace_bytes", "grid_sample", "adam_step", "GridFit", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
+__all__ = ["forward", "adjoint", "adjoint_grid", "adjoint_grid_workspace_bytes", "grid_sample", "adam_step", "GridFit", "HMC", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
            "SynaxError"]
 
 
@@ -325,6 +325,44 @@ class BatchPlan:
                                     _stream_handle(torch, stream)), "synax_batch_run")
         return grads, chi2
 
+    def bind(self, targets=None, seeds=None, sigma: float = 1.0, maps=None, grads=None, chi2=None):
+        """Fixes seeds/targets, sigma and outputs for run_device (synax_batch_bind);
+        returns (grads [n_sets, n_theta], chi2 [n_sets] or None), the tensors
+        every later run_device writes."""
+        torch = _torch()
+        if (targets is None) == (seeds is None):
+            raise ValueError("give exactly one of targets (chi^2) or seeds (VJP)")
+        src = targets if targets is not None else seeds
+        if len(src) != self._n:
+            raise ValueError("one target/seed map per set")
+        for t, p in zip(src, self.problems):
+            _check_map_tensor(torch, t, p, "target/seed")
+        if grads is None:
+            grads = torch.empty((self._n, self._n_theta), dtype=torch.float64, device="cuda")
+        if chi2 is None and targets is not None:
+            chi2 = torch.empty(self._n, dtype=torch.float64, device="cuda")
+        seed_arr = (ctypes.c_void_p * self._n)(*[t.data_ptr() for t in src])
+        map_arr = None
+        if maps is not None:
+            map_arr = (ctypes.c_void_p * self._n)(*[(t.data_ptr() if t is not None else None) for t in maps])
+        check(lib().synax_batch_bind(self._h, seed_arr, 0 if targets is not None else 1, ctypes.c_double(float(sigma)),
+                                     map_arr, ctypes.c_void_p(grads.data_ptr()),
+                                     ctypes.c_void_p(chi2.data_ptr() if chi2 is not None else 0)),
+              "synax_batch_bind")
+        self._bound = (list(src), maps, grads, chi2)          # the plan reads these on every run
+        return grads, chi2
+
+    def run_device(self, theta, stream=None):
+        """Runs the bound batch with theta [n_sets, n_theta] (CUDA float64)
+        read on the device (synax_batch_run_device)."""
+        torch = _torch()
+        if not theta.is_cuda or theta.dtype != torch.float64 or not theta.is_contiguous() \
+                or tuple(theta.shape) != (self._n, self._n_theta):
+            raise ValueError(f"theta must be a contiguous CUDA float64 tensor [{self._n}, {self._n_theta}]")
+        self._theta_dev = theta
+        check(lib().synax_batch_run_device(self._h, ctypes.c_void_p(theta.data_ptr()), _stream_handle(torch, stream)),
+              "synax_batch_run_device")
+
     def latencies(self):
         import numpy as np
         out = np.zeros(self._n, dtype=np.float64)
@@ -385,3 +423,6 @@ def _make_function():
             return g.to(ctx.theta_device), None
 
     return _SynaxMapsFn
+
+
+from .hmc import HMC, effective_sample_size  # noqa: E402  (uses BatchPlan above)

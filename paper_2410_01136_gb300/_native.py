@@ -73,6 +73,15 @@ class SynaxSurrogateCfg(ctypes.Structure):
     ]
 
 
+class SynaxHmcCfg(ctypes.Structure):
+    """Mirror of synax_hmc_cfg (include/synax.h)."""
+    _fields_ = [
+        ("n_leapfrog", ctypes.c_int32), ("step_size", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("inv_mass", ctypes.POINTER(ctypes.c_double)), ("lo", ctypes.POINTER(ctypes.c_double)),
+        ("hi", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
 SUR_PARAMS, SUR_GRADS, SUR_ADAM_M, SUR_ADAM_V, SUR_NORM, SUR_LOSS = range(6)
 _VP = ctypes.c_void_p
 
@@ -84,6 +93,21 @@ SIGNATURES = {
                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                      ctypes.c_void_p]),
+    "synax_batch_plan_n_sets": (ctypes.c_int, [ctypes.c_void_p]),
+    "synax_batch_plan_n_theta": (ctypes.c_int, [ctypes.c_void_p]),
+    "synax_batch_bind": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "synax_batch_run_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "synax_hmc_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "synax_hmc_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    "synax_hmc_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "synax_hmc_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "synax_hmc_destroy": (None, [ctypes.c_void_p]),
     "synax_grid_sample": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "synax_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -18,19 +18,11 @@
 #include <cmath>
 #include <cstring>
 
-#include "synax_internal.h"
+#include "params.cuh"
 
 namespace synax {
 
 namespace {
-// CODATA 2018, cgs
-constexpr double kC = 2.99792458e10;
-constexpr double kQe = 4.803204712570263e-10;
-constexpr double kMe = 9.1093837015e-28;
-constexpr double kKb = 1.380649e-16;
-constexpr double kKpc = 3.0856775814913673e21;
-constexpr double kMicroGauss = 1.0e-6;
-constexpr double kPiD = 3.141592653589793238;
 
 thread_local int g_last_cuda_error = 0;
 
@@ -42,16 +34,6 @@ int model_n_theta(int id) {
     case SYNAX_MODEL_GRID: return 3;
     case SYNAX_MODEL_WMAP_STACK: return 19;
     default: return -1;
-    }
-}
-
-int model_p_index(int id) {
-    switch (id) {
-    case SYNAX_MODEL_TOY: return 5;
-    case SYNAX_MODEL_WMAP: return 6;
-    case SYNAX_MODEL_GRID: return 1;
-    case SYNAX_MODEL_WMAP_STACK: return 17;
-    default: return 13;
     }
 }
 
@@ -69,23 +51,11 @@ double cr_profile(const double r[3]) {
 
 }  // namespace
 
+double observer_n0_norm(const synax_problem& P) { return 1.0 / cr_profile(P.obs_kpc); }
+
 int record_cuda_error(int err) {
     g_last_cuda_error = err;
     return SYNAX_ECUDA;
-}
-
-// Digamma for x > 0: upward recurrence to x >= 8, then the asymptotic series
-// psi(x) ~ ln x - 1/(2x) - sum_k B_{2k} / (2k x^{2k}) (Abramowitz & Stegun 6.3.18).
-double digamma(double x) {
-    double acc = 0.0;
-    while (x < 8.0) {
-        acc -= 1.0 / x;
-        x += 1.0;
-    }
-    const double x2 = 1.0 / (x * x);
-    const double series =
-        x2 * (1.0 / 12 - x2 * (1.0 / 120 - x2 * (1.0 / 252 - x2 * (1.0 / 240 - x2 * (1.0 / 132)))));
-    return acc + std::log(x) - 0.5 / x - series;
 }
 
 // Validates a problem; on success *n_pix receives the number of pixels marched.
@@ -151,31 +121,6 @@ static void set_phase(float& hi_out, float& lo_out, double v) {
 static void store_phase(ff& out, double v) { set_phase(out.hi, out.lo, v); }
 static void store_phase(double& out, double v) { out = v; }
 
-// Per-frequency physical prefactors (double).  aI, aP: K per (cm^-3 uG^{(p+1)/2}
-// kpc); crev: revolutions per (cm^-3 uG kpc); dlnaI/dp, dlnaP/dp for the adjoint.
-struct FreqConsts {
-    double aI, aP, crev, dlnaI, dlnaP;
-};
-
-static FreqConsts freq_consts(double nu, double p) {
-    FreqConsts F;
-    const double pre = std::sqrt(3.0) * kQe * kQe * kQe / (8.0 * kPiD * kMe * kC * kC);
-    const double X = 4.0 * kPiD * nu * kMe * kC / (3.0 * kQe);   // times 1/B
-    const double g1 = std::tgamma(p / 4.0 - 1.0 / 12.0);
-    const double base = pre * std::pow(X, 0.5 * (1.0 - p)) * std::pow(kMicroGauss, 0.5 * (p + 1.0));
-    const double toT = kKpc * kC * kC / (2.0 * kKb * nu * nu);
-    F.aI = base * std::pow(2.0, 0.5 * (p + 1.0)) / (p + 1.0) * g1 * std::tgamma(p / 4.0 + 19.0 / 12.0) * toT;
-    F.aP = base * std::pow(2.0, 0.5 * (p - 3.0)) * g1 * std::tgamma(p / 4.0 + 7.0 / 12.0) * toT;
-    const double lam = kC / nu;
-    const double K = kQe * kQe * kQe / (2.0 * kPiD * kMe * kMe * kC * kC * kC * kC);
-    F.crev = 2.0 * lam * lam * K * kMicroGauss * kKpc / (2.0 * kPiD);
-    const double common = -0.5 * std::log(X) + 0.5 * std::log(kMicroGauss) + 0.5 * std::log(2.0) +
-                          0.25 * digamma(p / 4.0 - 1.0 / 12.0);
-    F.dlnaI = common - 1.0 / (p + 1.0) + 0.25 * digamma(p / 4.0 + 19.0 / 12.0);
-    F.dlnaP = common + 0.25 * digamma(p / 4.0 + 7.0 / 12.0);
-    return F;
-}
-
 template <typename R>
 void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
     std::memset(&M, 0, sizeof(M));
@@ -201,70 +146,13 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
     M.r_max = R(P.r_max_kpc);
     M.dr = R(dr);
     M.dr_lo = R(dr - (double)R(dr));
-    const double p = P.theta[model_p_index(P.model_id)];
-    M.q = R((p - 3.0) / 4.0);
     for (int f = 0; f < P.n_freq; ++f) {
-        const FreqConsts F = freq_consts(P.freq_hz[f], p);
-        M.aI[f] = R(F.aI);
-        M.aP[f] = R(F.aP);
-        store_phase(M.crev[f], F.crev);
-        store_phase(M.cdr[f], F.crev * dr);
+        const double crev = freq_consts(P.freq_hz[f], 3.0).crev;   // independent of p
+        store_phase(M.crev[f], crev);
+        store_phase(M.cdr[f], crev * dr);
     }
-    const double* th = P.theta;
-    switch (P.model_id) {
-    case SYNAX_MODEL_TOY:
-        M.m[mc::TOY_B + 0] = R(th[0]);
-        M.m[mc::TOY_B + 1] = R(th[1]);
-        M.m[mc::TOY_B + 2] = R(th[2]);
-        M.m[mc::TOY_NE] = R(th[3]);
-        M.m[mc::TOY_N0] = R(th[4]);
-        M.m[mc::TOY_R0] = R(th[6]);
-        break;
-    case SYNAX_MODEL_WMAP:
-        M.m[mc::W_B0] = R(th[0]);
-        M.m[mc::W_PSI0] = R(th[1]);
-        M.m[mc::W_PSI1] = R(th[2]);
-        M.m[mc::W_CHI0] = R(th[3]);
-        M.m[mc::W_BUX] = R(th[4]);
-        M.m[mc::W_N0U] = R(1.0 / cr_profile(P.obs_kpc));
-        M.m[mc::W_N0OBS] = R(th[5]);
-        M.m[mc::W_NE0] = R(th[7]);
-        break;
-    case SYNAX_MODEL_JF12:
-        for (int k = 0; k < 8; ++k) M.m[mc::J_B + k] = R(th[k]);
-        M.m[mc::J_BH] = R(th[8]);
-        M.m[mc::J_IZH] = R(1.0 / th[9]);
-        M.m[mc::J_IZH_LO] = R(1.0 / th[9] - (double)R(1.0 / th[9]));
-        M.m[mc::J_BX] = R(th[10]);
-        M.m[mc::J_COSX] = R(std::cos(th[11]));
-        M.m[mc::J_SINX] = R(std::sin(th[11]));
-        M.m[mc::J_COTX] = R(1.0 / std::tan(th[11]));
-        M.m[mc::J_N0N] = R(th[12] / cr_profile(P.obs_kpc));
-        M.m[mc::J_N0U] = R(1.0 / cr_profile(P.obs_kpc));
-        M.m[mc::J_IH1] = R(1.0 / th[14]);
-        M.m[mc::J_IH2] = R(1.0 / th[15]);
-        M.m[mc::J_IH1_LO] = R(1.0 / th[14] - (double)R(1.0 / th[14]));
-        M.m[mc::J_IH2_LO] = R(1.0 / th[15] - (double)R(1.0 / th[15]));
-        M.m[mc::J_ZH] = R(th[9]);
-        M.m[mc::J_THX] = R(th[11]);
-        M.m[mc::J_H1] = R(th[14]);
-        M.m[mc::J_H2] = R(th[15]);
-        M.m[mc::J_N0OBS] = R(th[12]);
-        M.m[mc::J_SIN2X] = R(1.0 / (std::sin(th[11]) * std::sin(th[11])));
-        M.m[mc::J_BH_IZH2] = R(th[8] / (th[9] * th[9]));
-        M.m[mc::J_IH1_SQ] = R(1.0 / (th[14] * th[14]));
-        M.m[mc::J_IH2_SQ] = R(1.0 / (th[15] * th[15]));
-        break;
-    case SYNAX_MODEL_WMAP_STACK:
-        for (int k = 0; k < 16; ++k) M.m[mc::S_COMP + k] = R(th[k]);
-        M.m[mc::S_N0U] = R(1.0 / cr_profile(P.obs_kpc));
-        M.m[mc::S_N0OBS] = R(th[16]);
-        M.m[mc::S_NE0] = R(th[18]);
-        break;
-    case SYNAX_MODEL_GRID:
-        M.m[mc::G_N0U] = R(1.0 / cr_profile(P.obs_kpc));
-        M.m[mc::G_N0OBS] = R(th[0]);
-        M.m[mc::G_NE0] = R(th[2]);
+    fill_theta<R>(P.model_id, P.theta, P.freq_hz, P.n_freq, observer_n0_norm(P), M, nullptr);
+    if (P.model_id == SYNAX_MODEL_GRID) {
         for (int a = 0; a < 3; ++a) {
             const double n1 = (double)(P.grid_n[a] - 1);
             const double sc = n1 / P.box_kpc[a];            // node spacings per kpc
@@ -275,20 +163,15 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
             M.grid_n[a] = P.grid_n[a];
         }
         M.grid = (const R*)P.grid_dev;
-        break;
-    default: break;
     }
 }
 
 template <typename R>
 void fill_adj(const synax_problem& P, AdjParams<R>& A) {
     std::memset(&A, 0, sizeof(A));
-    const double p = P.theta[model_p_index(P.model_id)];
-    for (int f = 0; f < P.n_freq; ++f) {
-        const FreqConsts F = freq_consts(P.freq_hz[f], p);
-        A.dlnaI_dp[f] = R(F.dlnaI);
-        A.dlnaP_dp[f] = R(F.dlnaP);
-    }
+    MapParams<R> scratch;
+    std::memset(&scratch, 0, sizeof(scratch));
+    fill_theta<R>(P.model_id, P.theta, P.freq_hz, P.n_freq, observer_n0_norm(P), scratch, &A);
     A.n_theta = P.n_theta;
 }
 

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "params.cuh"
 
 namespace synax {
 int batch_kernels_jf12(int nf, int lpr, BatchKernels* out);
@@ -52,6 +53,13 @@ struct synax_batch_plan {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // device-resident theta (synax_batch_bind / synax_batch_run_device)
+    BatchSet* h_bound = nullptr;      // bound descriptors (theta-dependent fields rebuilt on the device)
+    double* d_freq = nullptr;         // [n_sets][SYNAX_MAX_FREQ]
+    double* d_n0norm = nullptr;       // [n_sets]
+    const double* dev_theta = nullptr;    // theta pointer the device graph was captured with
+    cudaGraph_t graph_dev = nullptr;
+    cudaGraphExec_t exec_dev = nullptr;
     cudaEvent_t done = nullptr;
     bool pending = false;
 };
@@ -63,6 +71,11 @@ void plan_free(synax_batch_plan* p) {
     if (p->pending && p->done) cudaEventSynchronize(p->done);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->exec_dev) cudaGraphExecDestroy(p->exec_dev);
+    if (p->graph_dev) cudaGraphDestroy(p->graph_dev);
+    cudaFree(p->d_freq);
+    cudaFree(p->d_n0norm);
+    if (p->h_bound) cudaFreeHost(p->h_bound);
     if (p->done) cudaEventDestroy(p->done);
     if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->d_sets);
@@ -82,6 +95,45 @@ int nf_variant(int n_freq) {
     if (n_freq <= 4) return 4;
     if (n_freq <= 8) return 8;
     return 16;
+}
+
+// Rebuilds the theta-dependent fields of every set's descriptor from
+// device-resident parameter vectors theta [n_sets][n_theta] (params.cuh, the
+// same code as the host path).  One thread per set.
+__global__ void k_fill_sets(BatchSet* __restrict__ sets, const double* __restrict__ theta, int n_sets, int n_theta,
+                            int model, const double* __restrict__ freq, const double* __restrict__ n0norm) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_sets) return;
+    BatchSet& d = sets[s];
+    fill_theta<float>(model, theta + (size_t)s * n_theta, freq + (size_t)s * SYNAX_MAX_FREQ, d.P.n_freq, n0norm[s],
+                      d.P, &d.A);
+}
+
+// The device-theta graph: bound descriptors -> theta fields rebuilt ->
+// counter reset -> persistent kernel -> per-set reduction.
+int capture_graph_dev(synax_batch_plan* p, const double* theta) {
+    if (p->exec_dev) { cudaGraphExecDestroy(p->exec_dev); p->exec_dev = nullptr; }
+    if (p->graph_dev) { cudaGraphDestroy(p->graph_dev); p->graph_dev = nullptr; }
+    cudaError_t err = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    cudaMemcpyAsync(p->d_sets, p->h_bound, sizeof(BatchSet) * (size_t)p->n_sets, cudaMemcpyHostToDevice, p->cap);
+    k_fill_sets<<<(p->n_sets + 127) / 128, 128, 0, p->cap>>>(p->d_sets, theta, p->n_sets, p->n_theta, p->model,
+                                                              p->d_freq, p->d_n0norm);
+    cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), p->cap);
+    cudaMemsetAsync(p->d_done, 0, sizeof(unsigned long long) * (size_t)p->n_sets, p->cap);
+    int n_sets = p->n_sets;
+    long long n_tiles = p->n_tiles;
+    void* args[] = {&p->d_sets, &p->d_begin, &p->d_order, &n_sets, &n_tiles, &p->d_counter,
+                    &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0};
+    cudaLaunchKernel(p->kern.batch, dim3(p->grid), dim3(kAdjThreads), args, 0, p->cap);
+    void* rargs[] = {&p->d_sets, &p->d_partial};
+    cudaLaunchKernel(p->kern.reduce, dim3(p->n_sets), dim3(256), rargs, 0, p->cap);
+    err = cudaStreamEndCapture(p->cap, &p->graph_dev);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    err = cudaGraphInstantiate(&p->exec_dev, p->graph_dev, 0);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    p->dev_theta = theta;
+    return SYNAX_OK;
 }
 
 int capture_graph(synax_batch_plan* p) {
@@ -276,6 +328,79 @@ int synax_batch_plan_info(const synax_batch_plan* p, long long* n_tiles, int* la
     if (grid) *grid = p->grid;
     return SYNAX_OK;
 }
+
+int synax_batch_bind(synax_batch_plan* p, const void* const* seeds_dev, int vjp, double sigma_K,
+                     void* const* maps_dev, double* grads_dev, double* chi2_dev) {
+    if (!p || !seeds_dev || !grads_dev) return SYNAX_EINVAL;
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    if (dev != p->device) return SYNAX_EINVAL;
+    if (!vjp) {
+        if (!std::isfinite(sigma_K)) return SYNAX_ENONFINITE;
+        if (!(sigma_K > 0.0)) return SYNAX_EINVAL;
+    }
+    for (int s = 0; s < p->n_sets; ++s)
+        if (!seeds_dev[s]) return SYNAX_EINVAL;
+    if (p->pending) {
+        err = cudaEventSynchronize(p->done);
+        if (err != cudaSuccess) return record_cuda_error((int)err);
+        p->pending = false;
+    }
+    if (!p->h_bound) {
+        if (cudaMallocHost(&p->h_bound, sizeof(BatchSet) * p->n_sets) != cudaSuccess ||
+            cudaMalloc(&p->d_freq, sizeof(double) * SYNAX_MAX_FREQ * p->n_sets) != cudaSuccess ||
+            cudaMalloc(&p->d_n0norm, sizeof(double) * p->n_sets) != cudaSuccess) {
+            cudaGetLastError();
+            return SYNAX_ENOMEM;
+        }
+    }
+    std::vector<double> freq((size_t)SYNAX_MAX_FREQ * p->n_sets, 0.0), n0n(p->n_sets);
+    for (int s = 0; s < p->n_sets; ++s) {
+        BatchSet& d = p->h_bound[s];
+        std::memset(&d, 0, sizeof(d));
+        fill_params<float>(p->probs[s], p->npix[s], d.P);
+        fill_adj<float>(p->probs[s], d.A);
+        d.A.mode_chi2 = vjp ? 0 : 1;
+        d.A.inv_sigma2 = vjp ? 0.0f : (float)(1.0 / (sigma_K * sigma_K));
+        d.seed = (const float*)seeds_dev[s];
+        d.maps = maps_dev ? (float*)maps_dev[s] : nullptr;
+        d.grad = grads_dev + (size_t)s * p->n_theta;
+        d.chi2 = chi2_dev ? chi2_dev + s : nullptr;
+        const long long k = p->pos_of[s];
+        d.tile_begin = p->begin[k];
+        d.n_tiles = p->begin[k + 1] - p->begin[k];
+        for (int f = 0; f < p->probs[s].n_freq; ++f) freq[(size_t)s * SYNAX_MAX_FREQ + f] = p->probs[s].freq_hz[f];
+        n0n[s] = observer_n0_norm(p->probs[s]);
+    }
+    err = cudaMemcpy(p->d_freq, freq.data(), sizeof(double) * freq.size(), cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(p->d_n0norm, n0n.data(), sizeof(double) * n0n.size(), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    return SYNAX_OK;
+}
+
+int synax_batch_run_device(synax_batch_plan* p, const double* theta_dev, void* stream) {
+    if (!p || !theta_dev) return SYNAX_EINVAL;
+    if (!p->h_bound) return SYNAX_EINVAL;                    // synax_batch_bind first
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    if (dev != p->device) return SYNAX_EINVAL;
+    if (!p->exec_dev || p->dev_theta != theta_dev) {
+        const int rc = capture_graph_dev(p, theta_dev);
+        if (rc != SYNAX_OK) return rc;
+    }
+    err = cudaGraphLaunch(p->exec_dev, (cudaStream_t)stream);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    err = cudaEventRecord(p->done, (cudaStream_t)stream);
+    if (err != cudaSuccess) return record_cuda_error((int)err);
+    p->pending = true;
+    return SYNAX_OK;
+}
+
+int synax_batch_plan_n_theta(const synax_batch_plan* p) { return p ? p->n_theta : 0; }
+int synax_batch_plan_n_sets(const synax_batch_plan* p) { return p ? p->n_sets : 0; }
 
 void synax_batch_plan_destroy(synax_batch_plan* p) { plan_free(p); }
 

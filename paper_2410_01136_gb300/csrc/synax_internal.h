@@ -93,6 +93,8 @@ struct AdjParams {
 int validate_problem(const synax_problem* P, long long* n_pix);
 template <typename R> void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M);
 template <typename R> void fill_adj(const synax_problem& P, AdjParams<R>& A);
+// 1 / (e^{-rho/5} sech^2 z) at the problem's observer (the CR normalisation).
+double observer_n0_norm(const synax_problem& P);
 
 // Lanes per ray (32, 16 or 8) for a map of n_pix rays of n_steps samples:
 // the launch tuning table (tune.cu), overridable per process.
