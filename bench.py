@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--only-grid", action="store_true",
                     help="run only the grid-model measurement (no interpolation study) and print its JSON")
     ap.add_argument("--grid-runs", type=int, default=10, help="timed steps of the grid-model measurement")
+    ap.add_argument("--only-hmc", action="store_true", help="run only the HMC sampling measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the learned surrogate")
     ap.add_argument("--surrogate-steps", type=int, default=20000, help="Adam steps of the surrogate training")
     ap.add_argument("--surrogate-maps", type=int, default=50000, help="training maps of the surrogate")
@@ -365,6 +366,53 @@ def bench_wmap_stack(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
             "forward_samples_per_s": prob.samples / (ms_fwd * 1e-3), "gpu_launches_per_step": 2}
 
 
+def bench_hmc(sx, inputs, torch, dev, n_chains: int = 16, n_warm: int = 40, n_draws: int = 60) -> dict:
+    """Gradient-based sampling as in Sec. 3.2: the WMAP-type model with the
+    Sec. 3.1 values (b0 = 1.2 uG, psi0 = 0.4712, psi1 = 0.0157, chi0B =
+    0.4363; no x field; N0_obs, p, n_e0 fixed) in the (40, 40, 10) kpc box,
+    Nside 64, 512 steps, 2.4 GHz, a mock with 1 mK noise; HMC chains on the
+    batch (synax_hmc_*), the four field parameters free, diagonal Laplace
+    mass, warm-up then timed draws; ESS per second of sampling over all
+    chains (multi-chain ESS)."""
+    import numpy as np
+    th = np.array([1.2, 0.4712, 0.0157, 0.4363, 0.0, inputs.N0_EARTH, 3.0, 0.03])
+    prob = inputs.Problem(nside=64, n_steps=512, freq_hz=(2.4e9,), model_id=inputs.MODEL_WMAP, theta=th,
+                          box_clip=True, obs_kpc=inputs.OBS_PAPER_KPC)
+    mock = sx.forward(prob)
+    target = (mock + 1e-3 * torch.tensor(inputs.target_noise(tuple(mock.shape), seed=84, sigma=1.0),
+                                         dtype=torch.float32, device=dev)).contiguous()
+    free = [0, 1, 2, 3]
+    inv_mass = sx.laplace_inv_mass(prob, target, 1e-3, free)
+    sd = np.sqrt(inv_mass)
+    th0 = np.stack([th + sd * inputs.normal(inputs.substream(85, c), th.size) for c in range(n_chains)])
+    hmc = sx.HMC([prob.with_theta(t) for t in th0], [target] * n_chains, 1e-3, th0, step_size=0.5, n_leapfrog=8,
+                 seed=86, inv_mass=inv_mass)
+    hist = hmc.warmup(n_warm)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    draws, acc = hmc.run(n_draws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) * 1e-3
+    d = draws.cpu().numpy()
+    ess = sx.effective_sample_size(d[:, :, free])
+    post_sd = d[:, :, free].reshape(-1, len(free)).std(axis=0)
+    hmc.close()
+    return {"workload": "WMAP-type (Sec. 3.1 values), box (40, 40, 10) kpc, Nside 64, 512 steps, 2.4 GHz, sigma 1 mK; "
+                        f"{n_chains} HMC chains x {n_draws} draws after {n_warm} warm-up, 8 leapfrog steps, "
+                        "b0, psi0, psi1, chi0B free",
+            "seconds_sampling": s, "ms_per_iteration": 1e3 * s / n_draws,
+            "gradient_evals_per_s": n_chains * 8 * n_draws / s,
+            "acceptance": float(acc.float().mean().item()),
+            "final_step_size": hist[-1][0] if hist else None,
+            "ess": {k: float(v) for k, v in zip(["b0", "psi0", "psi1", "chi0B"], ess)},
+            "ess_per_s": {k: float(v / s) for k, v in zip(["b0", "psi0", "psi1", "chi0B"], ess)},
+            "posterior_sd": {k: float(v) for k, v in zip(["b0", "psi0", "psi1", "chi0B"], post_sd)},
+            "paper_context_ess_per_s_nuts_a100": {"b0": 1.90, "psi0": 1.73, "psi1": 1.07, "chi0B": 0.87}}
+
+
 def interp_study(sx, inputs, torch) -> dict:
     """Sec. 5's interpolation study, re-run: the WMAP-type field with the
     parameters of Sec. 3.1 (b0 = 1.2 uG, psi0 = 0.4712, psi1 = 0.0157,
@@ -529,6 +577,10 @@ def run_synax(args):
     import paper_2410_01136_gb300 as sx
     from paper_2410_01136_gb300 import _native, inputs, tune
     sx.build()
+    if args.only_hmc:
+        if rank == 0:
+            print(json.dumps({"hmc": bench_hmc(sx, inputs, torch, dev)}), flush=True)
+        return
     if args.only_grid:
         if rank == 0:
             print(json.dumps({"grid": bench_grid(sx, inputs, torch, dev, max(args.grid_runs, 1),
@@ -693,6 +745,7 @@ def run_synax(args):
         out["grid"] = bench_grid(sx, inputs, torch, dev)
         out["interp_study"] = interp_study(sx, inputs, torch)
         out["wmap_stack"] = bench_wmap_stack(sx, inputs, torch, dev)
+        out["hmc"] = bench_hmc(sx, inputs, torch, dev)
     if rank == 0 and not args.no_surrogate:
         peaks = {}
         try:

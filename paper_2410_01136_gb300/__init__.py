@@ -425,4 +425,4 @@ def _make_function():
     return _SynaxMapsFn
 
 
-from .hmc import HMC, effective_sample_size  # noqa: E402  (uses BatchPlan above)
+from .hmc import HMC, effective_sample_size, laplace_inv_mass  # noqa: E402  (uses BatchPlan above)

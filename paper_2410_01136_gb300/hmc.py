@@ -130,6 +130,26 @@ class HMC:
             pass
 
 
+def laplace_inv_mass(prob, target, sigma: float, free, h_rel: float = 1e-3) -> np.ndarray:
+    """Diagonal Laplace estimate of the posterior variance of the free
+    parameters at prob.theta: U = chi^2 / 2 has curvature U''_jj =
+    (g_j(theta + h e_j) - g_j(theta - h e_j)) / (4 h) with g = d chi^2 / d theta
+    from synax_adjoint; the variance is 1 / U''_jj (0 for fixed parameters,
+    and where the curvature is not positive)."""
+    from . import adjoint
+    th = np.asarray(prob.theta, dtype=np.float64)
+    out = np.zeros(th.size)
+    for j in free:
+        h = h_rel * max(abs(th[j]), 1e-3)
+        e = np.zeros(th.size)
+        e[j] = h
+        gp, _ = adjoint(prob.with_theta(th + e), target=target, sigma=sigma)
+        gm, _ = adjoint(prob.with_theta(th - e), target=target, sigma=sigma)
+        curv = (float(gp[j].item()) - float(gm[j].item())) / (4.0 * h)
+        out[j] = 1.0 / curv if curv > 0 else 0.0
+    return out
+
+
 def effective_sample_size(draws) -> np.ndarray:
     """Multi-chain effective sample size per parameter of draws [n, m, k]
     (n draws, m chains), after Gelman et al., Bayesian Data Analysis (3rd
