@@ -440,6 +440,47 @@ def interp_study(sx, inputs, torch) -> dict:
     return out
 
 
+def bench_surrogate_sh(sx, inputs, torch, dev, steps: int, n_maps: int = 50000) -> dict:
+    """The surrogate on the low-order basis (the first 3072 real spherical
+    harmonics, l <= 55): same network, data and training as bench_surrogate,
+    judged on the 512 held-out draws as a full-map error: the in-subspace
+    RMS of the judge combined with each true map's own truncation outside
+    the basis (||x||^2 - ||c||^2 per Stokes map, over npix)."""
+    import numpy as np
+    from paper_2410_01136_gb300.surrogate import Surrogate
+    prob = inputs.config5_problem()
+    sur = Surrogate.for_workload(batch=512, total_steps=steps, lr=1e-3, lr_min=1e-5, basis="sh")
+    thetas = inputs.config5_thetas(n_maps, seed=50)
+    t0 = time.perf_counter()
+    sur.dataset(prob, thetas)
+    sur.train(steps, seed=1)
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t0
+    hold = inputs.config5_thetas(512, seed=51)
+    c = sur(torch.tensor(hold, dtype=torch.float32, device=dev))
+    _, rms, _ = sur.judge(prob, hold, c, 1.0)
+    rms = rms.cpu().numpy()
+    npix = 12 * 64 * 64
+    trunc = np.empty((512, 3))
+    for k in range(0, 512, 64):
+        maps = torch.stack([sx.forward(prob.with_theta(t))[0] for t in hold[k:k + 64]])      # [64, 3, npix]
+        cc = sur.project(maps.reshape(-1, npix)).reshape(64, 3, -1).double()
+        x2 = maps.double().pow(2).sum(dim=-1)
+        trunc[k:k + 64] = ((x2 - cc.pow(2).sum(dim=-1)).clamp_min(0.0) / npix).sqrt().cpu().numpy()
+    full = np.sqrt(rms.astype(np.float64) ** 2 + trunc ** 2)
+    sur.close()
+
+    def q(a):
+        return {"median": float(np.median(a)), "p90": float(np.percentile(a, 90))}
+    return {"workload": "as 'surrogate', basis = real spherical harmonics l <= 55 (first 3072), orthonormalised",
+            "dataset_and_train_s": t_all,
+            "in_subspace_rms_K": {n: q(rms[:, i]) for i, n in enumerate("IQU")},
+            "truncation_rms_K": {n: q(trunc[:, i]) for i, n in enumerate("IQU")},
+            "full_map_rms_K": {n: q(full[:, i]) for i, n in enumerate("IQU")},
+            "pass_frac_1K_full_map_I": float(np.mean(full[:, 0] <= 1.0)),
+            "pass_frac_1K_full_map_all": float(np.mean(full.max(axis=1) <= 1.0))}
+
+
 def bench_surrogate(sx, inputs, torch, dev, steps: int, peaks: dict, n_maps: int = 50000) -> dict:
     """The learned surrogate on its workload: 50 000 Nside-64 JF12-type maps at
     408 MHz (parameters uniform in +-20 % of the fiducial scale), an MLP
@@ -595,7 +636,9 @@ def run_synax(args):
             pass
         if rank == 0:
             print(json.dumps({"surrogate": bench_surrogate(sx, inputs, torch, dev, args.surrogate_steps, peaks,
-                                                           args.surrogate_maps)}), flush=True)
+                                                           args.surrogate_maps),
+                              "surrogate_sh": bench_surrogate_sh(sx, inputs, torch, dev, args.surrogate_steps,
+                                                                 args.surrogate_maps)}), flush=True)
         return
     if args.lanes:
         tune.reset()
@@ -754,6 +797,7 @@ def run_synax(args):
         except (OSError, ValueError):
             pass
         out["surrogate"] = bench_surrogate(sx, inputs, torch, dev, args.surrogate_steps, peaks, args.surrogate_maps)
+        out["surrogate_sh"] = bench_surrogate_sh(sx, inputs, torch, dev, args.surrogate_steps, args.surrogate_maps)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             rate, dt, threads, desc = oracle_map_grad_rate(8192)

@@ -340,6 +340,21 @@ int synax_eval_fields(const synax_problem* prob, const double* pos_dev, const do
  * maps and falls back to them.  The library owns every buffer of the handle;
  * all calls are on one device and, unless stated, asynchronous on `stream`.
  * ------------------------------------------------------------------------ */
+/* Basis kinds.  SRHT: the seeded +-1 rows above (exact in BF16, orthonormal
+ * by construction).  SH: the low-order basis of real spherical harmonics
+ * Y_lm (l = 0, 1, ... in the order l^2 + l + m, Condon-Shortley phase) at the
+ * pixel centres, orthonormalised in that order by CholeskyQR2 in FP64 (its
+ * first k rows span the first k harmonics), stored as BF16 hi + lo; needs
+ * (l_max + 1)^2 >= n_basis with l_max <= 2 nside.  With SH the surrogate's
+ * coefficients are the map's large-scale content, so a full-map error is the
+ * in-subspace error plus the map's own truncation error outside l_max. */
+#define SYNAX_SUR_BASIS_SRHT 0
+#define SYNAX_SUR_BASIS_SH   1
+
+/* The SH basis rows [n_basis][12 nside^2] as FP64 in device memory
+ * (basis_dev, caller-owned), the same construction as the surrogate's. */
+int synax_sh_basis(int nside, int n_basis, double* basis_dev);
+
 typedef struct synax_surrogate_s synax_surrogate_t;
 
 typedef struct {
@@ -352,12 +367,12 @@ typedef struct {
     int32_t max_eval;      /* rows per internal chunk of synax_surrogate, 1..65536 */
     int32_t map_chunk;     /* maps rendered per projection chunk (dataset, judge), 1..1024 */
     int32_t total_steps;   /* length of the cosine learning-rate schedule, >= 1 */
-    int32_t reserved;
+    int32_t basis_kind;    /* SYNAX_SUR_BASIS_SRHT (0) or SYNAX_SUR_BASIS_SH (1) */
     double lr, lr_min;     /* Adam step size: cosine decay lr -> lr_min over total_steps */
     double beta1, beta2, eps;
     double theta_lo[64], theta_hi[64];   /* input box (physical units), hi > lo */
-    const int8_t* basis_sign;            /* host [12 nside^2], each +1 or -1; copied */
-    const int32_t* basis_rows;           /* host [n_basis], distinct, in [0, 12 nside^2); copied */
+    const int8_t* basis_sign;            /* SRHT: host [12 nside^2], each +1 or -1; copied (SH: unused) */
+    const int32_t* basis_rows;           /* SRHT: host [n_basis], distinct, in [0, 12 nside^2); copied */
 } synax_surrogate_cfg;
 
 enum {

@@ -32,7 +32,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import erf
+from scipy.special import erf, lpmv
 
 # ---------------------------------------------------------------------------
 # basis
@@ -89,6 +89,58 @@ def project(maps, nside: int, signs, rows, chunk: int = 256) -> np.ndarray:
         E = basis(nside, signs, rows[k0:k0 + chunk])
         out[..., k0:k0 + chunk] = maps @ E.T
     return out
+
+
+def sh_index(l: int, m: int) -> int:
+    """Position of the real harmonic (l, m), m in [-l, l], in the basis order."""
+    return l * l + l + m
+
+
+def real_sph_harm_pixels(nside: int, n_basis: int) -> np.ndarray:
+    """Real spherical harmonics at the RING pixel centres, [n_basis][npix]:
+    Y_l0 = N_l0 P_l^0(cos t), Y_lm = sqrt(2) N_lm P_l^m(cos t) cos(m phi) and
+    Y_l,-m = sqrt(2) N_lm P_l^m(cos t) sin(m phi) for m > 0, with
+    N_lm = sqrt((2l + 1) / (4 pi) (l - m)! / (l + m)!) and P_l^m the associated
+    Legendre function with the Condon-Shortley phase (scipy's lpmv), in the
+    order (l, m) -> l^2 + l + m."""
+    import oracle
+    npix = 12 * nside * nside
+    zs = np.empty(npix)
+    ph = np.empty(npix)
+    for p in range(npix):
+        zs[p], ph[p] = oracle.healpix_centre(nside, p)
+    out = np.empty((n_basis, npix))
+    l = 0
+    while l * l < n_basis:
+        for m in range(0, l + 1):
+            norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - m) / math.factorial(l + m))
+            P = norm * lpmv(m, l, zs)
+            if m == 0:
+                if sh_index(l, 0) < n_basis:
+                    out[sh_index(l, 0)] = P
+            else:
+                if sh_index(l, m) < n_basis:
+                    out[sh_index(l, m)] = math.sqrt(2.0) * P * np.cos(m * ph)
+                if sh_index(l, -m) < n_basis:
+                    out[sh_index(l, -m)] = math.sqrt(2.0) * P * np.sin(m * ph)
+        l += 1
+    return out
+
+
+def cholesky_qr2(Y) -> np.ndarray:
+    """Orthonormal rows spanning, for every k, the span of Y's first k rows:
+    E = L^-1 Y with G = Y Y^T = L L^T (Cholesky), applied twice."""
+    E = np.asarray(Y, dtype=np.float64)
+    for _ in range(2):
+        L = np.linalg.cholesky(E @ E.T)
+        E = np.linalg.solve(L, E)
+    return E
+
+
+def sh_basis(nside: int, n_basis: int) -> np.ndarray:
+    """The low-order surrogate basis: real spherical harmonics at the pixel
+    centres, orthonormalised in their (l, m) order (cholesky_qr2)."""
+    return cholesky_qr2(real_sph_harm_pixels(nside, n_basis))
 
 
 def judge_rms(c_sur, c_true, nside: int) -> np.ndarray:

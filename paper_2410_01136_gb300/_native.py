@@ -65,7 +65,7 @@ class SynaxSurrogateCfg(ctypes.Structure):
         ("n_theta", ctypes.c_int32), ("width", ctypes.c_int32), ("depth", ctypes.c_int32),
         ("nside", ctypes.c_int32), ("n_basis", ctypes.c_int32), ("batch", ctypes.c_int32),
         ("max_eval", ctypes.c_int32), ("map_chunk", ctypes.c_int32), ("total_steps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("basis_kind", ctypes.c_int32),
         ("lr", ctypes.c_double), ("lr_min", ctypes.c_double), ("beta1", ctypes.c_double),
         ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
         ("theta_lo", ctypes.c_double * 64), ("theta_hi", ctypes.c_double * 64),
@@ -83,6 +83,7 @@ class SynaxHmcCfg(ctypes.Structure):
 
 
 SUR_PARAMS, SUR_GRADS, SUR_ADAM_M, SUR_ADAM_V, SUR_NORM, SUR_LOSS = range(6)
+SUR_BASIS_SRHT, SUR_BASIS_SH = 0, 1
 _VP = ctypes.c_void_p
 
 SIGNATURES = {
@@ -108,6 +109,7 @@ SIGNATURES = {
     "synax_hmc_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p]),
     "synax_hmc_destroy": (None, [ctypes.c_void_p]),
+    "synax_sh_basis": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "synax_grid_sample": (ctypes.c_int, [ctypes.POINTER(SynaxProblem), ctypes.POINTER(ctypes.c_int32),
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "synax_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

@@ -49,6 +49,9 @@
 using bf16 = __nv_bfloat16;
 
 namespace synax {
+// sh_basis.cu
+int build_sh_basis(int nside, int n_basis, __nv_bfloat16* S_hi, __nv_bfloat16* S_lo, double* E_out);
+
 namespace {
 
 constexpr int kMaxLayers = 9;          // depth <= 8 hidden layers + output
@@ -475,6 +478,8 @@ struct synax_surrogate_s {
     int8_t* sign_dev = nullptr;
     int* basis_rows_dev = nullptr;
     bf16* S = nullptr;
+    bf16* S_lo = nullptr;       // basis_kind 1: the basis' BF16 low part (E = S + S_lo)
+    float proj_scale = 1.0f;    // coefficient = proj_scale * (S x): 1/sqrt(npix) for the +-1 basis
     float* maps = nullptr;
     bf16 *mhi = nullptr, *mlo = nullptr;
     float* ctrue = nullptr;
@@ -494,7 +499,8 @@ namespace {
 void free_all(synax_surrogate_t* s) {
     void* ptrs[] = {s->W, s->dW, s->mW, s->vW, s->b, s->db, s->mb, s->vb, s->Wb, s->Wt, s->lo, s->inv2, s->mean,
                     s->rows_dev, s->ybuf, s->loss_part, s->loss_hist, s->t_dev, s->adam_coef, s->err, s->eD0, s->eD1,
-                    s->sign_dev, s->basis_rows_dev, s->S, s->maps, s->mhi, s->mlo, s->ctrue, s->ds_theta, s->ds_y};
+                    s->sign_dev, s->basis_rows_dev, s->S, s->S_lo, s->maps, s->mhi, s->mlo, s->ctrue, s->ds_theta,
+                    s->ds_y};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < kMaxLayers; ++l) {
@@ -623,6 +629,23 @@ GatherArgs gather_identity(const synax_surrogate_t* s, const float* theta, int c
     return a;
 }
 
+// Coefficients of `rows` maps already split into s->mhi + s->mlo:
+// out = proj_scale (S_hi x_hi + S_hi x_lo [+ S_lo x_hi for basis_kind 1]).
+int project_split(synax_surrogate_t* s, int rows, float* out, cudaStream_t st) {
+    GemmEpiParams ep{};
+    ep.out_f32 = out;
+    ep.ld_f32 = s->cfg.n_basis;
+    ep.scale = s->proj_scale;
+    ep.accumulate = 0;
+    SX_TRY(gemm_bf16(s->mhi, s->npix, s->S, s->npix, rows, s->cfg.n_basis, s->npix, EPI_SCALE_ACC, ep, s->err, st));
+    ep.accumulate = 1;
+    SX_TRY(gemm_bf16(s->mlo, s->npix, s->S, s->npix, rows, s->cfg.n_basis, s->npix, EPI_SCALE_ACC, ep, s->err, st));
+    if (s->S_lo)
+        SX_TRY(gemm_bf16(s->mhi, s->npix, s->S_lo, s->npix, rows, s->cfg.n_basis, s->npix, EPI_SCALE_ACC, ep, s->err,
+                         st));
+    return SYNAX_OK;
+}
+
 // Render `count` maps of the fiducial problem at theta_host rows into
 // s->maps and project them into out [count][3][n_basis].
 int render_and_project(synax_surrogate_t* s, const synax_problem* fid, const double* theta_host, int count, float* out,
@@ -636,16 +659,7 @@ int render_and_project(synax_surrogate_t* s, const synax_problem* fid, const dou
     const long long n = (long long)count * 3 * s->npix;
     k_split_hi_lo<<<grid_for(n), 256, 0, st>>>(s->maps, n, s->mhi, s->mlo);
     SX_TRY(launch_status());
-    GemmEpiParams ep{};
-    ep.out_f32 = out;
-    ep.ld_f32 = s->cfg.n_basis;
-    ep.scale = (float)(1.0 / std::sqrt((double)s->npix));
-    ep.accumulate = 0;
-    SX_TRY(gemm_bf16(s->mhi, s->npix, s->S, s->npix, 3 * count, s->cfg.n_basis, s->npix, EPI_SCALE_ACC, ep, s->err,
-                     st));
-    ep.accumulate = 1;
-    return gemm_bf16(s->mlo, s->npix, s->S, s->npix, 3 * count, s->cfg.n_basis, s->npix, EPI_SCALE_ACC, ep, s->err,
-                     st);
+    return project_split(s, 3 * count, out, st);
 }
 
 int check_fiducial(const synax_surrogate_t* s, const synax_problem* fid) {
@@ -708,23 +722,38 @@ int synax_surrogate_create(const synax_surrogate_cfg* cfg, synax_surrogate_t** o
     for (int j = 0; j < c.n_theta; ++j)
         if (!std::isfinite(c.theta_lo[j]) || !std::isfinite(c.theta_hi[j]) || !(c.theta_hi[j] > c.theta_lo[j]))
             return SYNAX_EINVAL;
-    if (!c.basis_sign || !c.basis_rows) return SYNAX_EINVAL;
-    std::vector<char> seen(npix, 0);
-    for (int i = 0; i < c.n_basis; ++i) {
-        const int r = c.basis_rows[i];
-        if (r < 0 || r >= npix || seen[r]) return SYNAX_EINVAL;
-        seen[r] = 1;
+    if (c.basis_kind != SYNAX_SUR_BASIS_SRHT && c.basis_kind != SYNAX_SUR_BASIS_SH) return SYNAX_EINVAL;
+    if (c.basis_kind == SYNAX_SUR_BASIS_SRHT) {
+        if (!c.basis_sign || !c.basis_rows) return SYNAX_EINVAL;
+        std::vector<char> seen(npix, 0);
+        for (int i = 0; i < c.n_basis; ++i) {
+            const int r = c.basis_rows[i];
+            if (r < 0 || r >= npix || seen[r]) return SYNAX_EINVAL;
+            seen[r] = 1;
+        }
+        for (int p = 0; p < npix; ++p)
+            if (c.basis_sign[p] != 1 && c.basis_sign[p] != -1) return SYNAX_EINVAL;
+    } else {
+        // the pixels resolve harmonics up to l ~ 3 nside; keep well inside that
+        int lmax = 0;
+        while ((lmax + 1) * (lmax + 1) < c.n_basis) ++lmax;
+        if (lmax > 2 * c.nside) return SYNAX_EINVAL;
     }
-    for (int p = 0; p < npix; ++p)
-        if (c.basis_sign[p] != 1 && c.basis_sign[p] != -1) return SYNAX_EINVAL;
 
     synax_surrogate_t* s = new (std::nothrow) synax_surrogate_t();
     if (!s) return SYNAX_ENOMEM;
     s->cfg = c;
     s->cfg.basis_sign = nullptr;
     s->cfg.basis_rows = nullptr;
-    s->sign.assign(c.basis_sign, c.basis_sign + npix);
-    s->rows.assign(c.basis_rows, c.basis_rows + c.n_basis);
+    if (c.basis_kind == SYNAX_SUR_BASIS_SRHT) {
+        s->sign.assign(c.basis_sign, c.basis_sign + npix);
+        s->rows.assign(c.basis_rows, c.basis_rows + c.n_basis);
+        s->proj_scale = (float)(1.0 / std::sqrt((double)npix));
+    } else {
+        s->sign.assign(npix, 0);
+        s->rows.assign(c.n_basis, 0);
+        s->proj_scale = 1.0f;
+    }
     s->npix = npix;
     s->n_out = 3 * c.n_basis;
     s->B = c.batch;
@@ -768,6 +797,7 @@ int synax_surrogate_create(const synax_surrogate_cfg* cfg, synax_surrogate_t** o
     SX_ALLOC(s->t_dev, 1) SX_ALLOC(s->adam_coef, 4) SX_ALLOC(s->err, 1)
     SX_ALLOC(s->sign_dev, npix) SX_ALLOC(s->basis_rows_dev, c.n_basis)
     SX_ALLOC(s->S, (long long)c.n_basis * npix)
+    if (c.basis_kind == SYNAX_SUR_BASIS_SH) SX_ALLOC(s->S_lo, (long long)c.n_basis * npix)
     SX_ALLOC(s->maps, (long long)s->chunk * 3 * npix)
     SX_ALLOC(s->mhi, (long long)s->chunk * 3 * npix) SX_ALLOC(s->mlo, (long long)s->chunk * 3 * npix)
     SX_ALLOC(s->ctrue, (long long)s->chunk * s->n_out)
@@ -795,9 +825,13 @@ int synax_surrogate_create(const synax_surrogate_cfg* cfg, synax_surrogate_t** o
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(record_cuda_error((int)e));
     if ((rc = gemm_init()) != SYNAX_OK) return fail(rc);
-    k_build_basis<<<grid_for((long long)c.n_basis * npix), 256>>>(s->S, s->sign_dev, s->basis_rows_dev, c.n_basis,
-                                                                   npix, c.nside * c.nside);
-    if ((rc = launch_status()) != SYNAX_OK) return fail(rc);
+    if (c.basis_kind == SYNAX_SUR_BASIS_SRHT) {
+        k_build_basis<<<grid_for((long long)c.n_basis * npix), 256>>>(s->S, s->sign_dev, s->basis_rows_dev, c.n_basis,
+                                                                       npix, c.nside * c.nside);
+        if ((rc = launch_status()) != SYNAX_OK) return fail(rc);
+    } else if ((rc = build_sh_basis(c.nside, c.n_basis, s->S, s->S_lo, nullptr)) != SYNAX_OK) {
+        return fail(rc);
+    }
     if ((rc = refresh_copies(s, 0, 0)) != SYNAX_OK) return fail(rc);
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(record_cuda_error((int)e));
@@ -922,16 +956,7 @@ int synax_surrogate_project(synax_surrogate_t* s, const float* maps_dev, long lo
         const long long n = (long long)rows * s->npix;
         k_split_hi_lo<<<grid_for(n), 256, 0, st>>>(maps_dev + r0 * s->npix, n, s->mhi, s->mlo);
         SX_TRY(launch_status());
-        GemmEpiParams ep{};
-        ep.out_f32 = coeffs_dev + r0 * s->cfg.n_basis;
-        ep.ld_f32 = s->cfg.n_basis;
-        ep.scale = (float)(1.0 / std::sqrt((double)s->npix));
-        ep.accumulate = 0;
-        SX_TRY(gemm_bf16(s->mhi, s->npix, s->S, s->npix, rows, s->cfg.n_basis, s->npix, EPI_SCALE_ACC, ep, s->err,
-                         st));
-        ep.accumulate = 1;
-        SX_TRY(gemm_bf16(s->mlo, s->npix, s->S, s->npix, rows, s->cfg.n_basis, s->npix, EPI_SCALE_ACC, ep, s->err,
-                         st));
+        SX_TRY(project_split(s, rows, coeffs_dev + r0 * s->cfg.n_basis, st));
     }
     return SYNAX_OK;
 }
@@ -1150,7 +1175,7 @@ int synax_surrogate_status(synax_surrogate_t* s, void* stream) {
     return h ? SYNAX_ETIMEOUT : SYNAX_OK;
 }
 
-// file: magic, version, n_theta, width, depth, nside, n_basis, t, scale,
+// file: magic, version, n_theta, width, depth, nside, n_basis, t, basis_kind, scale,
 // then sign[npix] (int8), rows[n_basis] (int32), W, b, mW, mb, vW, vb (flat
 // layout of synax_surrogate_get), mean[n_out], theta_lo/hi (double).
 int synax_surrogate_save(synax_surrogate_t* s, const char* path) {
@@ -1166,7 +1191,7 @@ int synax_surrogate_save(synax_surrogate_t* s, const char* path) {
     FILE* f = std::fopen(path, "wb");
     if (!f) return SYNAX_EINVAL;
     const int32_t hdr[9] = {(int32_t)kMagic, (int32_t)kFileVersion, s->cfg.n_theta, s->cfg.width, s->cfg.depth,
-                            s->cfg.nside, s->cfg.n_basis, t, 0};
+                            s->cfg.nside, s->cfg.n_basis, t, s->cfg.basis_kind};
     bool ok = std::fwrite(hdr, sizeof hdr, 1, f) == 1;
     ok = ok && std::fwrite(&s->scale, 4, 1, f) == 1;
     ok = ok && std::fwrite(s->sign.data(), 1, s->sign.size(), f) == s->sign.size();
@@ -1194,7 +1219,7 @@ int synax_surrogate_load(synax_surrogate_t* s, const char* path) {
     bool ok = std::fread(hdr, sizeof hdr, 1, f) == 1 && std::fread(&scale, 4, 1, f) == 1;
     ok = ok && hdr[0] == (int32_t)kMagic && hdr[1] == (int32_t)kFileVersion && hdr[2] == s->cfg.n_theta &&
          hdr[3] == s->cfg.width && hdr[4] == s->cfg.depth && hdr[5] == s->cfg.nside && hdr[6] == s->cfg.n_basis &&
-         hdr[7] >= 0;
+         hdr[7] >= 0 && hdr[8] == s->cfg.basis_kind;
     ok = ok && std::fread(sign.data(), 1, sign.size(), f) == sign.size() &&
          std::fread(rows.data(), 4, rows.size(), f) == rows.size();
     ok = ok && std::fread(w.data(), 4, np, f) == np && std::fread(m.data(), 4, np, f) == np &&

@@ -35,12 +35,16 @@ class Surrogate:
 
     def __init__(self, n_theta, theta_lo, theta_hi, basis_sign, basis_rows, *, width=1024, depth=4, nside=64,
                  batch=512, max_eval=16384, map_chunk=128, total_steps=10000, lr=1e-3, lr_min=1e-5,
-                 beta1=0.9, beta2=0.999, eps=1e-8, init=None):
+                 beta1=0.9, beta2=0.999, eps=1e-8, init=None, basis="srht", n_basis=None):
         import torch
         self._torch = torch
         cfg = _native.SynaxSurrogateCfg()
         cfg.n_theta, cfg.width, cfg.depth, cfg.nside = n_theta, width, depth, nside
-        self.n_basis = int(len(basis_rows))
+        if basis not in ("srht", "sh"):
+            raise ValueError("basis is 'srht' (seeded +-1 rows) or 'sh' (spherical harmonics)")
+        self.basis = basis
+        cfg.basis_kind = _native.SUR_BASIS_SRHT if basis == "srht" else _native.SUR_BASIS_SH
+        self.n_basis = int(len(basis_rows)) if basis == "srht" else int(n_basis)
         cfg.n_basis, cfg.batch, cfg.max_eval, cfg.map_chunk = self.n_basis, batch, max_eval, map_chunk
         cfg.total_steps, cfg.lr, cfg.lr_min = total_steps, lr, lr_min
         cfg.beta1, cfg.beta2, cfg.eps = beta1, beta2, eps
@@ -49,10 +53,11 @@ class Surrogate:
         for j in range(n_theta):
             cfg.theta_lo[j] = float(lo[j])
             cfg.theta_hi[j] = float(hi[j])
-        self._sign = np.ascontiguousarray(basis_sign, dtype=np.int8)
-        self._rows = np.ascontiguousarray(basis_rows, dtype=np.int32)
-        cfg.basis_sign = self._sign.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
-        cfg.basis_rows = self._rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if basis == "srht":
+            self._sign = np.ascontiguousarray(basis_sign, dtype=np.int8)
+            self._rows = np.ascontiguousarray(basis_rows, dtype=np.int32)
+            cfg.basis_sign = self._sign.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+            cfg.basis_rows = self._rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         h = ctypes.c_void_p()
         check(lib().synax_surrogate_create(ctypes.byref(cfg), ctypes.byref(h)), "synax_surrogate_create")
         self._h = h
@@ -67,11 +72,16 @@ class Surrogate:
     @classmethod
     def for_workload(cls, **kw):
         """The Nside-64 JF12-type surrogate: 16 -> 1024 x 4 -> 3 x 3072, box
-        theta_fid -/+ 20 % of each parameter's scale, basis seed 5, init seed 7."""
+        theta_fid -/+ 20 % of each parameter's scale, init seed 7; basis
+        'srht' (seed 5) or 'sh' (the first 3072 real harmonics, l <= 55)."""
         lo, hi = inputs.config5_box()
-        sign, rows = inputs.surrogate_basis_spec(64, 3072, seed=kw.pop("basis_seed", 5))
         init_seed = kw.pop("init_seed", 7)
-        sur = cls(16, lo, hi, sign, rows, **kw)
+        if kw.get("basis", "srht") == "sh":
+            kw.pop("basis_seed", None)
+            sur = cls(16, lo, hi, None, None, n_basis=3072, **kw)
+        else:
+            sign, rows = inputs.surrogate_basis_spec(64, 3072, seed=kw.pop("basis_seed", 5))
+            sur = cls(16, lo, hi, sign, rows, **kw)
         sur.set_params(inputs.mlp_init(sur.widths, seed=init_seed))
         return sur
 

@@ -162,3 +162,41 @@ def test_cosine_lr_endpoints():
     assert abs(so.cosine_lr(100, 1e-3, 1e-5, 100) - 1e-5) < 1e-18
     assert abs(so.cosine_lr(50, 1e-3, 1e-5, 100) - 0.5 * (1e-3 + 1e-5)) < 1e-15
     assert so.cosine_lr(500, 1e-3, 1e-5, 100) == so.cosine_lr(100, 1e-3, 1e-5, 100)
+
+
+# ---------------------------------------------------------------------------
+# low-order basis: real spherical harmonics at the pixel centres
+# ---------------------------------------------------------------------------
+
+def test_sh_values_match_scipy():
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy without sph_harm_y")
+    import oracle
+    from oracle import surrogate as osur
+    nside, nb = 4, 49                                   # l <= 6
+    Y = osur.real_sph_harm_pixels(nside, nb)
+    for p in (0, 7, 50, 95, 140, 191):
+        z, phi = oracle.healpix_centre(nside, p)
+        t = np.arccos(z)
+        for l in range(7):
+            for m in range(-l, l + 1):
+                c = sp.sph_harm_y(l, abs(m), t, phi)      # complex, Condon-Shortley phase
+                want = c.real if m == 0 else np.sqrt(2.0) * (c.real if m > 0 else c.imag)
+                assert Y[osur.sh_index(l, m), p] == pytest.approx(want, abs=1e-12)
+
+
+def test_sh_basis_orthonormal_and_nested():
+    from oracle import surrogate as osur
+    nside, nb = 4, 64
+    Y = osur.real_sph_harm_pixels(nside, nb)
+    E = osur.sh_basis(nside, nb)
+    np.testing.assert_allclose(E @ E.T, np.eye(nb), atol=1e-12)
+    # nested: the first k rows of E span the first k harmonics (E = L^-1 Y, lower triangular)
+    for k in (1, 4, 9, 16, 36):
+        R = Y[:k] @ E[:k].T                              # coordinates of Y_i in the first k rows of E
+        np.testing.assert_allclose(R @ E[:k], Y[:k], atol=1e-11)
+    # the monopole: a constant map has only its first coefficient
+    c = E @ np.ones(12 * nside * nside)
+    assert abs(c[0]) == pytest.approx(np.sqrt(12 * nside * nside), rel=1e-12)
+    np.testing.assert_allclose(c[1:], 0.0, atol=1e-11)
