@@ -387,7 +387,7 @@ def bench_hmc(sx, inputs, torch, dev, n_chains: int = 16, n_warm: int = 40, n_dr
     th0 = np.stack([th + sd * inputs.normal(inputs.substream(85, c), th.size) for c in range(n_chains)])
     hmc = sx.HMC([prob.with_theta(t) for t in th0], [target] * n_chains, 1e-3, th0, step_size=0.5, n_leapfrog=8,
                  seed=86, inv_mass=inv_mass)
-    hist = hmc.warmup(n_warm)
+    hist = hmc.warmup(n_warm, adapt_mass=False)          # the Laplace mass already sets the scales
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

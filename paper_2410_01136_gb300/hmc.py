@@ -90,30 +90,36 @@ class HMC:
                                     ctypes.c_void_p(na.data_ptr()), self._stream()), "synax_hmc_state")
         return th, c2, na
 
-    def warmup(self, n_iters: int, target_accept: float = 0.7, window: int = 10) -> list:
+    def warmup(self, n_iters: int, target_accept: float = 0.7, window: int = 5, adapt_mass: bool = True) -> list:
         """Runs n_iters iterations in windows of `window`.  After each window
-        the step size is scaled by exp(2 (acceptance - target)).  Halfway, the
-        free parameters' inverse masses become the variance of the draws so
-        far over all chains (a diagonal estimate of the posterior covariance)
-        and the step size restarts at 0.5 (the scale of a unit-variance
-        target).  Returns the (step size, acceptance) history."""
+        the step size is scaled by exp(3 (acceptance - target)).  Halfway, the
+        free parameters' inverse masses become the variance of the draws of
+        the second quarter (after the start-up transient), a diagonal
+        estimate of the posterior covariance, and the step size is rescaled
+        so that the typical position step eps sqrt(inv_mass) is unchanged
+        (geometric mean over the free parameters); adapt_mass=False keeps the
+        given mass (e.g. a Laplace estimate).  Returns the (step size,
+        acceptance) history."""
         hist = []
         free = self.inv_mass > 0
-        done, mass_set, seen = 0, False, []
+        done, mass_set, seen = 0, not adapt_mass, []
         while done < n_iters:
             k = min(window, n_iters - done)
             draws, acc = self.run(k)
-            seen.append(draws)
+            seen.append((done, draws))
             a = float(acc.float().mean().item())
             hist.append((self.step_size, a))
             done += k
+            eps = self.step_size * float(np.exp(3.0 * (a - target_accept)))
             if not mass_set and done >= n_iters // 2:
-                var = self._torch.cat(seen).reshape(-1, self.T).var(dim=0).cpu().numpy()
+                mass_set = True
+                part = [d for start, d in seen if start >= n_iters // 4] or [d for _, d in seen]
+                var = self._torch.cat(part).reshape(-1, self.T).var(dim=0).cpu().numpy()
                 if np.all(var[free] > 0):
-                    self.set(0.5, np.where(free, var, 0.0))
-                    mass_set = True
+                    ratio = float(np.exp(np.mean(np.log(self.inv_mass[free] / var[free]))))
+                    self.set(eps * np.sqrt(ratio), np.where(free, var, 0.0))
                     continue
-            self.set(self.step_size * float(np.exp(2.0 * (a - target_accept))))
+            self.set(eps)
         return hist
 
     def close(self):
@@ -155,7 +161,8 @@ def effective_sample_size(draws) -> np.ndarray:
     (n draws, m chains), after Gelman et al., Bayesian Data Analysis (3rd
     ed.), Sec. 11.5: rho_t = 1 - (W - mean autocovariance_t) / var+, summed
     over Geyer's initial positive and monotone sequence of pair sums;
-    ESS = m n / (-1 + 2 sum of the pair sums)."""
+    ESS = m n / (-1 + 2 sum of the pair sums), capped at m n log10(m n) (as
+    Stan does); 0 for chains that do not move (no within-chain variance)."""
     x = np.asarray(draws, dtype=np.float64)
     n, m, k = x.shape
     out = np.empty(k)
@@ -166,8 +173,9 @@ def effective_sample_size(draws) -> np.ndarray:
         W = acov[0].mean() * n / (n - 1)
         B_over_n = x[:, :, j].mean(axis=0).var(ddof=1) if m > 1 else 0.0
         var_plus = W * (n - 1) / n + B_over_n
-        if not var_plus > 0:
-            out[j] = float(m * n)
+        scale = max(float(np.abs(x[:, :, j]).max()), 1e-300)
+        if not W > (1e-14 * scale) ** 2:
+            out[j] = 0.0
             continue
         rho = 1.0 - (W - acov.mean(axis=1)) / var_plus
         rho[0] = 1.0
@@ -179,5 +187,5 @@ def effective_sample_size(draws) -> np.ndarray:
             pair = min(pair, prev)
             tau += 2.0 * pair
             prev = pair
-        out[j] = m * n / max(tau, 1e-12)
+        out[j] = min(m * n / max(tau, 1e-12), m * n * np.log10(m * n))
     return out

@@ -124,3 +124,35 @@ def test_warmed_up_ensemble_mixes(torch):
     assert np.all(ess > 10), ess           # correlated psi0, psi1, chi0B mix slower under a diagonal mass
     assert np.all(d[:, :, 4:] == th0[0, 4:])
     hmc.close()
+
+
+def test_error_paths(torch):
+    from paper_2410_01136_gb300 import SynaxError, _native
+    prob = small_wmap()
+    plan = BatchPlan([prob, prob])
+    th = torch.tensor(np.stack([prob.theta, prob.theta]), dtype=torch.float64, device="cuda")
+    with pytest.raises(SynaxError) as e:
+        plan.run_device(th)                              # not bound
+    assert e.value.status == _native.SYNAX_EINVAL
+    tgt = torch.zeros((2, 3, prob.npix), dtype=torch.float32, device="cuda")
+    with pytest.raises(SynaxError):
+        plan.bind(targets=[tgt, tgt], sigma=0.0)
+    with pytest.raises(SynaxError) as e:
+        plan.bind(targets=[tgt, tgt], sigma=float("nan"))
+    assert e.value.status == _native.SYNAX_ENONFINITE
+    plan.close()
+    th0 = np.stack([prob.theta, prob.theta])
+    for kw in (dict(step_size=0.0, n_leapfrog=2), dict(step_size=0.1, n_leapfrog=0),
+               dict(step_size=0.1, n_leapfrog=2, inv_mass=-np.ones(8)),
+               dict(step_size=0.1, n_leapfrog=2, lo=np.ones(8), hi=np.zeros(8))):
+        with pytest.raises(SynaxError):
+            HMC([prob, prob], [tgt, tgt], 0.05, th0, **kw)
+    bad = th0.copy()
+    bad[1, 0] = np.nan
+    with pytest.raises(SynaxError) as e:
+        HMC([prob, prob], [tgt, tgt], 0.05, bad, 0.1, 2)
+    assert e.value.status == _native.SYNAX_ENONFINITE
+    hmc = HMC([prob, prob], [tgt, tgt], 0.05, th0, 0.1, 2)
+    with pytest.raises(SynaxError):
+        hmc.set(step_size=-1.0)
+    hmc.close()
