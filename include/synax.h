@@ -462,6 +462,17 @@ int synax_surrogate_gate(synax_surrogate_t* a, synax_surrogate_t* b, const float
  * kernel of this surrogate gave up since creation, else SYNAX_OK. */
 int synax_surrogate_status(synax_surrogate_t* s, void* stream);
 
+/* Self-test of the failure handling of the tensor-core kernels' bounded
+ * waits (no counterpart in the paper).  Enqueues one CTA that holds 32 TMEM
+ * columns and waits, with the GEMM's own bounded wait (~2e9 SM clocks, about
+ * 1 s), on an mbarrier that nothing arrives at.  When the wait gives up the
+ * CTA sets *err_dev (device int) to 1, writes the SM clocks the wait took to
+ * *cycles_dev (device int64), frees its TMEM and returns, so the context
+ * stays usable.  The caller zeroes *err_dev and reads both after the stream
+ * synchronises.  SYNAX_EINVAL for a NULL pointer; SYNAX_ECUDA if the launch
+ * fails. */
+int synax_wait_selftest(int* err_dev, long long* cycles_dev, void* stream);
+
 /* Checkpoint: weights, Adam moments, step counter, normalisation, basis
  * definition and input box to a binary file; load requires a surrogate
  * created with the same configuration and basis.  Synchronous. */

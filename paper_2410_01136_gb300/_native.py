@@ -155,6 +155,7 @@ SIGNATURES = {
                                              ctypes.c_double, _VP, _VP, _VP]),
     "synax_surrogate_gate": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "synax_surrogate_status": (ctypes.c_int, [_VP, _VP]),
+    "synax_wait_selftest": (ctypes.c_int, [_VP, _VP, _VP]),
     "synax_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "synax_surrogate_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "synax_last_cuda_error": (ctypes.c_int, []),

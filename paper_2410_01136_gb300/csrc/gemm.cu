@@ -416,6 +416,38 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
 }
 
+// Self-test of the bounded wait and its exit path (failure handling, not part
+// of the method).  One CTA holds 32 TMEM columns and waits, through the same
+// mbar_wait_clock as the GEMM, on an mbarrier that nothing arrives at.  The
+// wait gives up after kWaitCycles; the CTA then sets *err, frees its TMEM and
+// returns.  *cycles receives the SM clocks the wait took.
+__global__ void __launch_bounds__(64, 1) k_wait_selftest(int* err, long long* cycles) {
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, 32);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        const bool ok = mbar_wait_clock(&bar, 0);
+        *cycles = clock64() - t0;
+        if (!ok) atomicExch(err, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 32);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -596,4 +628,11 @@ extern "C" int synax_gemm_bf16(const void* a_dev, int lda, const void* b_dev, in
     ep.out_f32 = c_dev;
     ep.ld_f32 = ldc;
     return gemm_bf16(a_dev, lda, b_dev, ldb, M, N, K, EPI_F32, ep, err_dev, (cudaStream_t)stream);
+}
+
+extern "C" int synax_wait_selftest(int* err_dev, long long* cycles_dev, void* stream) {
+    if (!err_dev || !cycles_dev) return SYNAX_EINVAL;
+    k_wait_selftest<<<1, 64, 0, (cudaStream_t)stream>>>(err_dev, cycles_dev);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
 }

@@ -267,3 +267,8 @@ def test_set_lanes_per_ray_validation(L):
     for lanes in (8, 16, 32, 0):
         assert L.synax_set_lanes_per_ray(512, lanes) == _native.SYNAX_OK
     assert L.synax_set_lanes_per_ray(-1, 0) == _native.SYNAX_OK
+
+
+def test_wait_selftest_rejects_null(L):
+    assert L.synax_wait_selftest(None, ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
+    assert L.synax_wait_selftest(ctypes.c_void_p(16), None, None) == _native.SYNAX_EINVAL

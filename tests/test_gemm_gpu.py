@@ -69,3 +69,28 @@ def test_gemm_row_pitch_and_validation(torch):
     assert L.synax_gemm_bf16(ctypes.c_void_p(A.data_ptr()), 128, ctypes.c_void_p(B.data_ptr()), 64, 4, 4, 32,
                              ctypes.c_void_p(Cbad.data_ptr()), 4, ctypes.c_void_p(err.data_ptr()), None) \
         == _native.SYNAX_EINVAL
+
+
+def test_bounded_wait_gives_up_and_context_survives(torch):
+    """A wait on an mbarrier that nothing arrives at ends by its clock limit
+    with the error word set, its CTA frees its TMEM, and the context stays
+    usable: a GEMM (which allocates TMEM on every SM it runs on) still runs
+    and matches afterwards."""
+    import time
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cycles = torch.zeros(1, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = _native.lib().synax_wait_selftest(ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(cycles.data_ptr()),
+                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, rc
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    assert int(err.item()) == 1
+    assert int(cycles.item()) > 2_000_000_000          # the limit, in SM clocks
+    assert 0.3 < elapsed < 30.0, elapsed                # ~1 s at 2 GHz
+    A = torch.randn((256, 512), device="cuda").to(torch.bfloat16)
+    B = torch.randn((1024, 512), device="cuda").to(torch.bfloat16)
+    C = run_gemm(torch, A, B)
+    ref = A.float() @ B.float().T
+    assert (C - ref).abs().max().item() <= 1e-4 * ref.abs().max().item()
