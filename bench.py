@@ -45,7 +45,7 @@ FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 # DRAM bytes (read + write) of one k_adjoint launch of this workload, from the
 # ncu capture summarised in profiles/k_adjoint_jf12_nside64_512steps.md
-ADJ_DRAM_BYTES = 2.439e6
+ADJ_DRAM_BYTES = 2.438e6
 
 
 def parse():
@@ -827,7 +827,7 @@ def run_synax(args):
         out["surrogate_sh"] = bench_surrogate_sh(sx, inputs, torch, dev, args.surrogate_steps, args.surrogate_maps)
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            rate, dt, threads, desc = oracle_map_grad_rate(8192)
+            rate, dt, threads, desc = oracle_map_grad_rate(16384)   # ~10 s on 16 cores
             out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
                                    "kind": "oracle", "sample": desc, "seconds": dt}
         except Exception as exc:  # the oracle is a baseline; report why it is absent

@@ -249,7 +249,8 @@ def grid_device(prob):
     key = (id(g), dt, torch.cuda.current_device())
     cached = getattr(prob, "_grid_device_copy", None)
     if cached is None or cached[0] != key:
-        t = torch.as_tensor(g).to(device="cuda", dtype=dt).contiguous()
+        import numpy as np
+        t = torch.as_tensor(np.array(g, copy=True)).to(device="cuda", dtype=dt).contiguous()   # host grids are read-only
         cached = (key, t)
         object.__setattr__(prob, "_grid_device_copy", cached)
     return cached[1]

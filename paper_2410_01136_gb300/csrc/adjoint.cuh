@@ -15,8 +15,12 @@ namespace synax {
 constexpr int kAdjThreads = 128;
 constexpr int kAdjMinBlocks = 5;
 // The grid model's reverse march holds its cell's trilinear coefficients and
-// node-gradient sums (48 registers): 4 CTAs per SM leave it 128 registers.
-template <int MODEL> constexpr int adj_min_blocks() { return MODEL == SYNAX_MODEL_GRID ? 4 : kAdjMinBlocks; }
+// node-gradient sums (48 registers), and the FP32 JF12-type one two samples'
+// field intermediates: 4 CTAs per SM leave them 128 registers (JF12-type map
+// + gradient 0.604 ms against 0.624 ms at 5 CTAs, where 264 bytes spilled).
+template <int MODEL> constexpr int adj_min_blocks() {
+    return MODEL == SYNAX_MODEL_GRID || MODEL == SYNAX_MODEL_JF12 ? 4 : kAdjMinBlocks;
+}
 
 template <int MODEL> struct Grad;
 
@@ -196,6 +200,151 @@ struct GridAcc {
     }
 };
 
+// The FP32 JF12-type reverse march of one lane, two samples per iteration:
+// samples n and n - 1 as element pairs (the forward lane march pairs n and
+// n + 1), with the field, emission, phase and gradient arithmetic of the
+// per-sample loop in adjoint_cta element by element.  The walk back of the RM
+// (Q) and the suffix sum of its adjoint (after) stay sequential.  Positions,
+// B, n_e and the RM integrand are those of the forward pair march, so that Q
+// retraces pass 1's sums.  An odd chunk start leaves a placeholder second
+// element whose emission, integrand and seed are zero.  Gradient terms with a
+// constant factor are summed raw and scaled once at the end.
+template <int NF>
+__device__ __forceinline__ void reverse_lane_pair_jf12(const MapParams<float>& P, const AdjParams<float>& A,
+                                                       const float* s_arms, const Los<float>& L, const ff* nd,
+                                                       int n0, int n1, float dr, float dr_lo, const ff* cd,
+                                                       const float* hr, const float* hi, const float* c2, float GI,
+                                                       float GIp, ff Q, float after, float* g, float* garm) {
+    const float* m = P.m;
+    ArmTracker<float> trk;
+    trk.init(P, nd, n1 - 1, dr, dr_lo);
+    const float q = P.q, w_own = P.w_own;
+    const float half_p1 = 2.0f * q + 2.0f;
+    const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
+    float s8 = 0.f, s9 = 0.f, s10 = 0.f, s11a = 0.f, s11b = 0.f, s12 = 0.f, s13 = 0.f, s14 = 0.f, s15 = 0.f;
+    float2 nh = make_float2(float(n1 - 1) + 0.5f, float(n1 - 2) + 0.5f);     // n + 1/2, exact
+    for (int n = n1 - 1; n >= n0; n -= 2, nh = add2(nh, dup2(-2.0f))) {
+        const float live_b = n - 1 >= n0 ? 1.0f : 0.0f;
+        const float2 t = fma2(nh, dup2(dr), mul2(nh, dup2(dr_lo)));
+        const float2 x = fma2(t, dup2(L.n[0]), obs_x);
+        const float2 y = fma2(t, dup2(L.n[1]), obs_y);
+        const float2 z = fma2(t, dup2(L.n[2]), obs_z);
+        const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
+        ArmCoord<float> ab;
+        trk.step_pair(-1, ab);
+        float2 B[3], N0, ne;
+        pair2::Jf12Loc2 lc;
+        pair2::jf12_eval<true>(m, s_arms, x, y, z, aa, ab, B, N0, ne, &lc);
+
+        // emission (Eq. 2, 5, 8) and RM integrand (Eq. 7), as the forward pair march
+        float2 v = mul2(B[0], dup2(L.n[0]));
+        v = fma2(B[1], dup2(L.n[1]), v);
+        const float2 bn = fma2(B[2], dup2(L.n[2]), v);
+        float2 u = mul2(B[0], dup2(L.eb[0]));
+        u = fma2(B[1], dup2(L.eb[1]), u);
+        const float2 bb = fma2(B[2], dup2(L.eb[2]), u);
+        const float2 bl = fma2(B[0], dup2(L.el[0]), mul2(B[1], dup2(L.el[1])));
+        const float2 bp2 = fma2(bl, bl, mul2(bb, bb));
+        const bool lit_a = bp2.x > 1e-30f, lit_b = bp2.y > 1e-30f;
+        const float2 lg = make_float2(lit_a ? lg2_approx(bp2.x) : 0.0f, lit_b ? lg2_approx(bp2.y) : 0.0f);
+        const float2 qa = mul2(dup2(q), lg);
+        const float2 w = make_float2(lit_a ? ex2_approx(qa.x) : 0.0f, lit_b ? ex2_approx(qa.y) * live_b : 0.0f);
+        const float2 nw = mul2(N0, w);
+        const float2 pc = mul2(nw, fma2(bl, bl, neg2(mul2(bb, bb))));
+        const float2 ps = mul2(nw, mul2(dup2(2.0f), mul2(bl, bb)));
+        const float2 f = mul2(neg2(mul2(ne, bn)), make_float2(1.0f, live_b));
+
+        // Q <- Q - f_n (the RM before sample n), s_n = that + w f_n; then n - 1
+        ff s_a, s_b, Q1;
+        ff_add_f_pair(Q, make_float2((w_own - 1.0f) * f.x, -f.x), s_a, Q1);
+        ff_add_f_pair(Q1, make_float2((w_own - 1.0f) * f.y, -f.y), s_b, Q);
+
+        // Omega = sum_f h_f e^{i phi_f} and its dp- and RM-weighted sums
+        float2 Or = dup2(0.f), Oi = dup2(0.f), Opr = dup2(0.f), Opi = dup2(0.f), Odr = dup2(0.f), Odi = dup2(0.f);
+        const float2 sh = make_float2(s_a.hi, s_b.hi), sl = make_float2(s_a.lo, s_b.lo);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {   // beyond n_freq h, c2 and dlnaP_dp are 0
+            const float2 ch = dup2(cd[k].hi), cl = dup2(cd[k].lo);
+            const float2 p = mul2(ch, sh);
+            float2 e = fma2(ch, sh, neg2(p));
+            e = fma2(ch, sl, e);
+            e = fma2(cl, sh, e);
+            const float2 kk = make_float2(rintf(p.x), rintf(p.y));
+            const float2 a = mul2(add2(add2(p, neg2(kk)), e), dup2(6.2831853071795865f));
+            const float2 sn = make_float2(sin_approx(a.x), sin_approx(a.y));
+            const float2 cs = make_float2(cos_approx(a.x), cos_approx(a.y));
+            const float2 ur = fma2(dup2(hr[k]), cs, neg2(mul2(dup2(hi[k]), sn)));
+            const float2 ui = fma2(dup2(hr[k]), sn, mul2(dup2(hi[k]), cs));
+            Or = add2(Or, ur);
+            Oi = add2(Oi, ui);
+            Opr = fma2(dup2(A.dlnaP_dp[k]), ur, Opr);
+            Opi = fma2(dup2(A.dlnaP_dp[k]), ui, Opi);
+            Odr = fma2(dup2(c2[k]), ur, Odr);
+            Odi = fma2(dup2(c2[k]), ui, Odi);
+        }
+        const float2 d = neg2(fma2(Odr, ps, mul2(Odi, pc)));     // dL/dS_n = -Im(Omega' E)
+        const float fbar_a = after + w_own * d.x;
+        after += d.x;
+        const float fbar_b = (after + w_own * d.y) * live_b;
+        after += d.y;
+        const float2 fbar = make_float2(fbar_a, fbar_b);
+
+        // emission adjoints: (t1, t2) = Omega z, t3 = Re(Omega z^2), u3 = Re(Omega_p z^2)
+        const float2 t1 = fma2(Or, bl, neg2(mul2(Oi, bb)));
+        const float2 t2 = fma2(Or, bb, mul2(Oi, bl));
+        const float2 u1 = fma2(Opr, bl, neg2(mul2(Opi, bb)));
+        const float2 u2 = fma2(Opr, bb, mul2(Opi, bl));
+        const float2 t3 = fma2(t1, bl, neg2(mul2(t2, bb)));
+        const float2 u3 = fma2(u1, bl, neg2(mul2(u2, bb)));
+        const float2 rb = pair2::rcp_nr(bp2);
+        const float2 ibp = make_float2(lit_a ? rb.x : 0.0f, lit_b ? rb.y : 0.0f);
+        const float2 kq = fma2(dup2(2.0f * q), mul2(t3, ibp), dup2(GI * half_p1));
+        const float2 abar = mul2(nw, fma2(bl, kq, mul2(dup2(2.0f), t1)));
+        const float2 bbar = mul2(nw, fma2(bb, kq, mul2(dup2(-2.0f), t2)));
+        const float2 gb = fma2(dup2(GI), bp2, t3);
+        const float2 n0bar = mul2(w, gb);
+        const float2 pbar = mul2(nw, fma2(mul2(gb, lg), dup2((float)(0.25 * kLn2)), fma2(dup2(GIp), bp2, u3)));
+        const float2 bnb = mul2(neg2(ne), fbar);                  // d f / d(B.n) = -n_e
+        const float2 neb = mul2(neg2(bn), fbar);                  // d f / d n_e = -B.n
+        const float2 bxb = fma2(bnb, dup2(L.n[0]), fma2(bbar, dup2(L.eb[0]), mul2(abar, dup2(L.el[0]))));
+        const float2 byb = fma2(bnb, dup2(L.n[1]), fma2(bbar, dup2(L.eb[1]), mul2(abar, dup2(L.el[1]))));
+        const float2 bzb = fma2(bnb, dup2(L.n[2]), mul2(bbar, dup2(L.eb[2])));
+
+        // Grad<JF12>::accum element by element
+        const float2 brb = fma2(bxb, lc.c, mul2(byb, lc.s));
+        const float2 bpb = fma2(byb, lc.c, neg2(mul2(bxb, lc.s)));
+        const float2 beta = fma2(brb, dup2((float)kPitchSin), mul2(bpb, dup2((float)kPitchCos)));
+        const float2 ga = mul2(beta, lc.arm_a), gbw = mul2(beta, lc.arm_b);
+        garm[lc.ka.x * kAdjThreads] += ga.x;
+        garm[lc.kb.x * kAdjThreads] += gbw.x;
+        garm[lc.ka.y * kAdjThreads] += ga.y;
+        garm[lc.kb.y * kAdjThreads] += gbw.y;
+        const float2 bsz = mul2(brb, lc.sz);
+        const float2 proj = fma2(bsz, dup2(m[mc::J_COSX]), mul2(bzb, dup2(m[mc::J_SINX])));
+        const float2 perp = fma2(bzb, dup2(m[mc::J_COSX]), neg2(mul2(bsz, dup2(m[mc::J_SINX]))));
+        const float2 v8 = mul2(bpb, lc.halo), v9 = mul2(bpb, lc.halo_az);
+        const float2 v10 = mul2(lc.xmag, proj), v11a = mul2(lc.xdrp, proj), v11b = mul2(lc.xmag, perp);
+        const float2 v12 = mul2(n0bar, lc.n0u), v14 = mul2(neb, lc.ne1az), v15 = mul2(neb, lc.ne2az);
+        s8 += v8.x + v8.y;
+        s9 += v9.x + v9.y;
+        s10 += v10.x + v10.y;
+        s11a += v11a.x + v11a.y;
+        s11b += v11b.x + v11b.y;
+        s12 += v12.x + v12.y;
+        s13 += pbar.x + pbar.y;
+        s14 += v14.x + v14.y;
+        s15 += v15.x + v15.y;
+    }
+    g[8] += s8;
+    g[9] += s9 * m[mc::J_BH_IZH2];
+    g[10] += s10;
+    g[11] += m[mc::J_BX] * (m[mc::J_SIN2X] * s11a + s11b);
+    g[12] += s12;
+    g[13] += s13;
+    g[14] += s14 * m[mc::J_IH1_SQ];
+    g[15] += s15 * m[mc::J_IH2_SQ];
+}
+
 // Shared-memory scratch of one adjoint CTA.
 template <int MODEL, int NF, int LPR, typename R>
 struct AdjSmem {
@@ -323,7 +472,11 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
         R* garm = &sm.garm[0][threadIdx.x];
 #pragma unroll
         for (int kk = 0; kk < NSLOT; ++kk) garm[kk * kAdjThreads] = R(0);
-        if (n0 < n1) {
+        if constexpr (MODEL == SYNAX_MODEL_JF12 && sizeof(R) == 4) {
+            if (n0 < n1)
+                reverse_lane_pair_jf12<NF>(P, A, s_arms, L, nd, n0, n1, dr, dr_lo, cd, hr, hi, c2, GI, GIp,
+                                           Ph::add(O, S), after, g, garm);
+        } else if (n0 < n1) {
             PT Q = Ph::add(O, S);                       // O + sum of f before sample n (after the update)
             ArmTracker<R> trk;
             if constexpr (MODEL == SYNAX_MODEL_JF12) trk.init(P, nd, n1 - 1, dr, dr_lo);

@@ -1191,10 +1191,27 @@ __device__ __forceinline__ void logistic_pair(float2 x, double h, double w, floa
     L = mul2(e, omL);
 }
 
-// B (uG), N0 and n_e (cm^-3) of the JF12-type model at two points.
+// Intermediates of the JF12-type field at two points that its parameter
+// gradient needs: the JF12-type members of FieldLocal, with the products the
+// gradient rule uses formed once.
+struct Jf12Loc2 {
+    float2 c, s;              // rho-hat
+    int2 ka, kb;              // arms blended at each point
+    float2 arm_a, arm_b;      // disc_unit (1 - wgt), disc_unit wgt
+    float2 halo, halo_az;     // halo_unit, halo_unit |z|
+    float2 sz;                // smooth sign of z
+    float2 xmag;              // |B_X| / B_X = e^{-rp/4.8} rp / rho
+    float2 xdrp;              // e^{-rp/4.8} (1 - rp/4.8) |z| / rho  (d|B_X|/d theta_X / (B_X sin 2 theta_X))
+    float2 n0u;               // N0 / N0_obs
+    float2 ne1az, ne2az;      // thick and thin n_e discs times |z|
+};
+
+// B (uG), N0 and n_e (cm^-3) of the JF12-type model at two points; with LOC
+// also the intermediates of the parameter gradient (the same B, N0 and n_e).
+template <bool LOC = false>
 __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, float2 x, float2 y, float2 z,
                                           const ArmCoord<float>& aa, const ArmCoord<float>& ab, float2 B[3],
-                                          float2& N0, float2& ne) {
+                                          float2& N0, float2& ne, Jf12Loc2* lc = nullptr) {
     const float2 rho2 = fma2(x, x, mul2(y, y));
     const float2 rho = f2(__fsqrt_rn(rho2.x), __fsqrt_rn(rho2.y));
     const float2 rr = rcp_nr(rho);
@@ -1219,8 +1236,19 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
         const float2 wgt = smoothstep_unit(f2(la ? aa.f + 0.5f : aa.f - 0.5f, lb ? ab.f + 0.5f : ab.f - 0.5f));
         const float2 a0 = f2(arms[ka_a], arms[ka_b]), a1 = f2(arms[kb_a], arms[kb_b]);
         beta = fma2(add2(a1, neg2(a0)), wgt, a0);
+        if constexpr (LOC) {
+            lc->ka = make_int2(ka_a, ka_b);
+            lc->kb = make_int2(kb_a, kb_b);
+            lc->arm_b = wgt;
+            lc->arm_a = add2(dup2(1.0f), neg2(wgt));
+        }
     }
-    const float2 amp = mul2(beta, mul2(mul2(mul2(dup2(5.0f), ri), W), omLz));
+    const float2 unit = mul2(mul2(mul2(dup2(5.0f), ri), W), omLz);
+    const float2 amp = mul2(beta, unit);
+    if constexpr (LOC) {
+        lc->arm_a = mul2(lc->arm_a, unit);
+        lc->arm_b = mul2(lc->arm_b, unit);
+    }
     float2 br = mul2(amp, dup2((float)kPitchSin));
     float2 bp = mul2(amp, dup2((float)kPitchCos));
 
@@ -1230,12 +1258,24 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
     const float2 hz = mul2(az, dup2(m[mc::J_IZH]));
     const float2 hu = mul2(mul2(mul2(exp_shape2(neg2(hz)), Lz), omLr), sz);
     bp = fma2(dup2(m[mc::J_BH]), hu, bp);
+    if constexpr (LOC) {
+        lc->halo = hu;
+        lc->halo_az = mul2(hu, az);
+        lc->sz = sz;
+        lc->c = c;
+        lc->s = s;
+    }
 
     // X field
     const float2 rp = fma2(neg2(az), dup2(m[mc::J_COTX]), rho);
     const float2 ex = exp_shape2(neg2(mul2(rp, dup2((float)(1.0 / 4.8)))));
     const float2 xe = f2(rp.x > 0.0f ? ex.x : 0.0f, rp.y > 0.0f ? ex.y : 0.0f);
-    const float2 mag = mul2(dup2(m[mc::J_BX]), mul2(mul2(xe, rp), ri));
+    const float2 xu = mul2(mul2(xe, rp), ri);
+    const float2 mag = mul2(dup2(m[mc::J_BX]), xu);
+    if constexpr (LOC) {
+        lc->xmag = xu;
+        lc->xdrp = mul2(mul2(mul2(xe, ri), fma2(rp, dup2((float)(-1.0 / 4.8)), dup2(1.0f))), az);
+    }
     br = fma2(mul2(mag, sz), dup2(m[mc::J_COSX]), br);
     const float2 bz = mul2(mag, dup2(m[mc::J_SINX]));
 
@@ -1247,7 +1287,15 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
     const float2 a1r = mulc(rho, 0.05), a2r = mulc(rho, 0.25);
     const float2 a1 = add2(a1r, fma2(az, dup2(m[mc::J_IH1]), mul2(az, dup2(m[mc::J_IH1_LO]))));
     const float2 a2 = add2(a2r, fma2(az, dup2(m[mc::J_IH2]), mul2(az, dup2(m[mc::J_IH2_LO]))));
-    ne = fma2(dup2(0.025f), expf2(neg2(a1)), mul2(dup2(0.10f), expf2(neg2(a2))));
+    if constexpr (LOC) {
+        const float2 e1 = expf2(neg2(a1));
+        const float2 ne2 = mul2(dup2(0.10f), expf2(neg2(a2)));
+        ne = fma2(dup2(0.025f), e1, ne2);
+        lc->ne1az = mul2(mul2(dup2(0.025f), e1), az);
+        lc->ne2az = mul2(ne2, az);
+    } else {
+        ne = fma2(dup2(0.025f), expf2(neg2(a1)), mul2(dup2(0.10f), expf2(neg2(a2))));
+    }
 
     // CR density (fast primitives: magnitudes only)
     const float2 e2a = mul2(dup2((float)(-2.0 * kLog2e)), az);
@@ -1256,7 +1304,9 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
     const float2 inv1 = f2(rcp_approx(onep.x), rcp_approx(onep.y));
     const float2 er = mul2(dup2((float)(-0.2 * kLog2e)), rho);
     const float2 eR = f2(ex2_approx(er.x), ex2_approx(er.y));
-    N0 = mul2(dup2(m[mc::J_N0OBS] * m[mc::J_N0U]), mul2(eR, mul2(mul2(dup2(4.0f), e2), mul2(inv1, inv1))));
+    const float2 prof = mul2(eR, mul2(mul2(dup2(4.0f), e2), mul2(inv1, inv1)));
+    N0 = mul2(dup2(m[mc::J_N0OBS] * m[mc::J_N0U]), prof);
+    if constexpr (LOC) lc->n0u = mul2(dup2(m[mc::J_N0U]), prof);
 }
 
 }  // namespace pair2
