@@ -43,6 +43,17 @@ ADJ_FACTOR = 3
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
+# The same count for every field model, without the Faraday phase: each
+# frequency adds 8 FP32 operations (phase, reduction to one turn, complex
+# accumulation) and 2 MUFU (sin, cos).  JF12-type: 168 + 14 (200 + 22 at four
+# frequencies, as above).  WMAP-type (Eq. 12-13): 60 + 14, with the
+# sqrt, reciprocal, exponentials, log and two sincos of the field.  Stacked
+# (Eq. 16): 99 + 25, four sincos pairs.  Grid: 142 + 9, the trilinear
+# blend and cell location in place of the field model; its adjoint adds 36
+# FP32 of node weights and sums per sample.  FP32 runs on 128 lanes per SM and
+# MUFU on 16, so the WMAP-type and stacked models are bound by the MUFU count.
+MODEL_OPS = {"jf12": (168, 14), "wmap": (60, 14), "wmap_stack": (99, 25), "grid": (142, 9)}
+GRID_ADJ_EXTRA_FP32 = 36
 # DRAM bytes (read + write) of one k_adjoint launch of this workload, from the
 # ncu capture summarised in profiles/k_adjoint_jf12_nside64_512steps.md
 ADJ_DRAM_BYTES = 2.438e6
@@ -126,6 +137,52 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smmax) if smmax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def march_roofline(model: str, n_freq: int, samples_per_s: float, clk_mhz: float, adjoint: bool,
+                   kernel: str) -> dict:
+    """Roofline of a march kernel from the per-sample operation counts of
+    MODEL_OPS: the pipe (FP32 or MUFU) that the count keeps busier bounds it."""
+    fp32, mufu = MODEL_OPS[model]
+    fp32 += 8 * n_freq
+    mufu += 2 * n_freq
+    if adjoint:
+        fp32 = ADJ_FACTOR * fp32 + (GRID_ADJ_EXTRA_FP32 if model == "grid" else 0)
+        mufu = ADJ_FACTOR * mufu
+    on_fp32 = fp32 / FP32_LANES_PER_SM >= mufu / MUFU_LANES_PER_SM
+    ops, lanes, pipe = (fp32, FP32_LANES_PER_SM, "FP32") if on_fp32 else (mufu, MUFU_LANES_PER_SM, "MUFU")
+    peak = SM_COUNT * lanes * clk_mhz * 1e6 / 1e12
+    achieved = samples_per_s * ops / 1e12
+    return {"bound": "alu", "pipe": pipe, "achieved": achieved, "peak": peak, "unit": f"T {pipe} op/s",
+            "frac": achieved / peak, "kernel": kernel, "ops_per_sample": {"fp32": fp32, "mufu": mufu},
+            "peak_basis": f"{SM_COUNT} SMs x {lanes} {pipe} lanes x {clk_mhz:.0f} MHz (median SM clock of "
+                          "the main timed region)"}
+
+
+def oracle_row(prob, n_pix_sample: int, free, note: str = "") -> dict:
+    """The FP64 oracle on a pixel sample of a workload: one map and
+    central differences over the parameters `free` (2 maps each); LOS samples
+    of the map + gradient per second of host time."""
+    import oracle
+    from paper_2410_01136_gb300 import inputs
+    oracle.build()
+    pix = inputs.sample_pixels(prob.npix, n_pix_sample, seed=41)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.forward(prob, pix=pix, threads=threads)
+    for i in free:
+        for sgn in (1.0, -1.0):
+            th = prob.theta.copy()
+            th[i] += sgn * 1e-4 * max(abs(th[i]), 1e-3)
+            oracle.forward(prob.with_theta(th), pix=pix, threads=threads)
+    dt = time.perf_counter() - t0
+    rate = pix.size * prob.n_steps / dt
+    out = {"samples_per_s": rate, "maps_grad_per_s": rate / prob.samples, "cores": threads, "seconds": dt,
+           "kind": "oracle", "sample": f"{pix.size} of {prob.npix} pixels x {prob.n_steps} steps, map + "
+                                       f"{2 * len(free)}-map central-difference gradient"}
+    if note:
+        out["note"] = note
+    return out
 
 
 def dist_env():
@@ -366,6 +423,14 @@ def bench_wmap_stack(sx, inputs, torch, dev, n_runs: int = 10) -> dict:
             "forward_samples_per_s": prob.samples / (ms_fwd * 1e-3), "gpu_launches_per_step": 2}
 
 
+def hmc_problem(inputs):
+    """The WMAP-type map of the sampling workload at the Sec. 3.1 values."""
+    import numpy as np
+    th = np.array([1.2, 0.4712, 0.0157, 0.4363, 0.0, inputs.N0_EARTH, 3.0, 0.03])
+    return inputs.Problem(nside=64, n_steps=512, freq_hz=(2.4e9,), model_id=inputs.MODEL_WMAP, theta=th,
+                          box_clip=True, obs_kpc=inputs.OBS_PAPER_KPC)
+
+
 def bench_hmc(sx, inputs, torch, dev, n_chains: int = 16, n_warm: int = 40, n_draws: int = 60) -> dict:
     """Gradient-based sampling as in Sec. 3.2: the WMAP-type model with the
     Sec. 3.1 values (b0 = 1.2 uG, psi0 = 0.4712, psi1 = 0.0157, chi0B =
@@ -375,9 +440,8 @@ def bench_hmc(sx, inputs, torch, dev, n_chains: int = 16, n_warm: int = 40, n_dr
     mass, warm-up then timed draws; ESS per second of sampling over all
     chains (multi-chain ESS)."""
     import numpy as np
-    th = np.array([1.2, 0.4712, 0.0157, 0.4363, 0.0, inputs.N0_EARTH, 3.0, 0.03])
-    prob = inputs.Problem(nside=64, n_steps=512, freq_hz=(2.4e9,), model_id=inputs.MODEL_WMAP, theta=th,
-                          box_clip=True, obs_kpc=inputs.OBS_PAPER_KPC)
+    prob = hmc_problem(inputs)
+    th = prob.theta
     mock = sx.forward(prob)
     target = (mock + 1e-3 * torch.tensor(inputs.target_noise(tuple(mock.shape), seed=84, sigma=1.0),
                                          dtype=torch.float32, device=dev)).contiguous()
@@ -403,7 +467,7 @@ def bench_hmc(sx, inputs, torch, dev, n_chains: int = 16, n_warm: int = 40, n_dr
     return {"workload": "WMAP-type (Sec. 3.1 values), box (40, 40, 10) kpc, Nside 64, 512 steps, 2.4 GHz, sigma 1 mK; "
                         f"{n_chains} HMC chains x {n_draws} draws after {n_warm} warm-up, 8 leapfrog steps, "
                         "b0, psi0, psi1, chi0B free",
-            "seconds_sampling": s, "ms_per_iteration": 1e3 * s / n_draws,
+            "seconds_sampling": s, "ms_per_iteration": 1e3 * s / n_draws, "samples_per_map": prob.samples,
             "gradient_evals_per_s": n_chains * 8 * n_draws / s,
             "acceptance": float(acc.float().mean().item()),
             "final_step_size": hist[-1][0] if hist else None,
@@ -816,6 +880,28 @@ def run_synax(args):
         out["interp_study"] = interp_study(sx, inputs, torch)
         out["wmap_stack"] = bench_wmap_stack(sx, inputs, torch, dev)
         out["hmc"] = bench_hmc(sx, inputs, torch, dev)
+    # every row against its kernel's roofline (same clock as the main line)
+    for key in ("batch", "batch_low_res"):
+        if key in out:
+            out[key]["roofline"] = march_roofline("jf12", 4, out[key]["samples_per_s"], clk_mhz, True,
+                                                  "k_batch (+ k_batch_reduce)")
+    if "grid" in out:
+        g = out["grid"]
+        g["roofline"] = march_roofline("grid", 1, g["samples_per_s"], clk_mhz, True,
+                                       "k_adjoint<GRID> (+ k_reduce_partials, k_grid_unpad)")
+        g["forward_roofline"] = march_roofline("grid", 1, g["forward_samples_per_s"], clk_mhz, False,
+                                               "k_forward<GRID>")
+    if "wmap_stack" in out:
+        w = out["wmap_stack"]
+        w["roofline"] = march_roofline("wmap_stack", 1, w["samples_per_s"], clk_mhz, True,
+                                       "k_adjoint<WMAP_STACK> (+ k_reduce_partials)")
+        w["forward_roofline"] = march_roofline("wmap_stack", 1, w["forward_samples_per_s"], clk_mhz, False,
+                                               "k_forward<WMAP_STACK>")
+    if "hmc" in out:
+        h = out["hmc"]
+        h["roofline"] = march_roofline("wmap", 1, h["gradient_evals_per_s"] * h["samples_per_map"], clk_mhz,
+                                       True, "k_batch<WMAP> per leapfrog step (momenta, leapfrog and "
+                                             "Metropolis kernels included in the time)")
     if rank == 0 and not args.no_surrogate:
         peaks = {}
         try:
@@ -833,6 +919,25 @@ def run_synax(args):
         except Exception as exc:  # the oracle is a baseline; report why it is absent
             out["cpu_baseline"] = {"value": None, "unit": "samples/s", "cores": os.cpu_count(),
                                    "kind": "oracle", "sample": f"failed: {exc}"}
+        # the oracle beside each further row, on bounded samples (~1-3 s each)
+        try:
+            for key in ("batch", "batch_low_res"):
+                if key in out:
+                    out[key]["oracle"] = {"samples_per_s": out["cpu_baseline"]["value"],
+                                          "note": "the sets are JF12-type maps at 4 frequencies: the "
+                                                  "oracle's rate per LOS sample is cpu_baseline's"}
+            if "grid" in out:
+                out["grid"]["oracle"] = oracle_row(
+                    inputs.grid_problem(), 8192, range(3),
+                    "map + theta gradient; the oracle's central differences of the 1.57 M grid values "
+                    "would take 3.1 M maps")
+            if "wmap_stack" in out:
+                out["wmap_stack"]["oracle"] = oracle_row(inputs.wmap_stack_problem(), 2048, range(19))
+            if "hmc" in out:
+                out["hmc"]["oracle"] = oracle_row(hmc_problem(inputs), 8192, range(4),
+                                                  "one gradient evaluation = map + 8 difference maps")
+        except Exception as exc:
+            out["oracle_rows_error"] = str(exc)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -726,16 +726,18 @@ template <> struct Model<SYNAX_MODEL_WMAP> {
         const R rho2 = x * x + y * y;
         const bool has_rho = rho2 > R(0);
         const R rho = F::sqrt(rho2);
-        const R c = has_rho ? F::div(x, rho) : R(1);
-        const R s = has_rho ? F::div(y, rho) : R(0);
+        // FMA-Newton reciprocals (~1 ulp, no systematic sign); rho/8 exact
+        const R ri = has_rho ? F::rcp_nr(rho) : R(0);
+        const R c = has_rho ? x * ri : R(1);
+        const R s = has_rho ? y * ri : R(0);
         const R az = F::abs(z);
         const R e2 = F::exp(R(-2) * az);                      // e^{-2|z|}
-        const R inv1 = F::div(R(1), R(1) + e2);
+        const R inv1 = F::rcp_nr(R(1) + e2);
         const R sech2 = R(4) * e2 * inv1 * inv1;
         R psi = R(0), chi = R(0), lnr8 = R(0), th = R(0);
         const bool in_range = rho >= R(3) && rho <= R(20);
         if (in_range) {
-            lnr8 = F::log(F::div(rho, R(8)));
+            lnr8 = F::log(rho * R(0.125));
             psi = m[mc::W_PSI0] + m[mc::W_PSI1] * lnr8;
             th = (R(1) - e2) * inv1;                         // tanh |z|
             th = z < R(0) ? -th : th;
@@ -867,13 +869,14 @@ template <> struct Model<SYNAX_MODEL_WMAP_STACK> {
         const R rho2 = x * x + y * y;
         const bool has_rho = rho2 > R(0);
         const R rho = F::sqrt(rho2);
-        const R c = has_rho ? F::div(x, rho) : R(1);
-        const R s = has_rho ? F::div(y, rho) : R(0);
+        const R ri = has_rho ? F::rcp_nr(rho) : R(0);
+        const R c = has_rho ? x * ri : R(1);
+        const R s = has_rho ? y * ri : R(0);
         const R az = F::abs(z);
         const R e2 = F::exp(R(-2) * az);                      // e^{-2|z|}
-        const R inv1 = F::div(R(1), R(1) + e2);
+        const R inv1 = F::rcp_nr(R(1) + e2);
         const bool in_range = rho >= R(3) && rho <= R(20);
-        const R lnr8 = in_range ? F::log(F::div(rho, R(8))) : R(0);
+        const R lnr8 = in_range ? F::log(rho * R(0.125)) : R(0);
         R th = (R(1) - e2) * inv1;                             // tanh |z|
         th = z < R(0) ? -th : th;
         R comp[4][3];
@@ -1068,7 +1071,7 @@ __device__ __forceinline__ void grid_eval(const MapParams<R>& P, GridCell<R>& gc
     const R rho = F::sqrt(x * x + y * y);
     const R az = F::abs(z);
     const R e2 = F::exp(R(-2) * az);                          // e^{-2|z|}
-    const R inv1 = F::div(R(1), R(1) + e2);
+    const R inv1 = F::rcp_nr(R(1) + e2);
     const R n0u = cr_density<R>(P.m[mc::G_N0U], rho, az);
     N0 = P.m[mc::G_N0OBS] * n0u;
     const R neu = F::exp(-F::mulc(rho, 0.05)) * (R(4) * e2 * inv1 * inv1);

@@ -106,7 +106,10 @@ def chi2_problem(nside, n_steps):
     return prob, target, sigma
 
 
-@pytest.mark.parametrize("n_steps", [64, 100])
+# 3 and 13 steps give lane chunks of 0-1 and 1-2 samples at 8 lanes per ray
+# (a lone sample pairs with a masked placeholder in the two-sample reverse
+# pass); 100 gives chunks of 12 and 13
+@pytest.mark.parametrize("n_steps", [3, 13, 64, 100])
 def test_chi2_jf12(torch, n_steps):
     prob, target, sigma = chi2_problem(8, n_steps)
     maps = torch.empty((4, 3, prob.npix), device="cuda")
