@@ -14,10 +14,13 @@ the Gaussian chi^2 of Sec. 3.1 (Eq. 15, up to the factor -1/2) and central
 finite differences, the gradient reference for the adjoint.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
-(closed forms, textbook forms, invariants, brute force); see the pin list in
-the design notes.  The JF12-type field model is defined by this project, so
-its absolute values are "parity unpinned" beyond the invariants those tests
-check.  The grid model's interpolation is pinned by exactness on multilinear
+(closed forms, textbook forms, invariants, brute force).  The JF12-type field
+model is defined by this project (after Jansson & Farrar 2012), so no
+published values pin it; its evaluation is pinned by properties the
+definition implies (``tests/test_oracle_jf12.py``: a divergence-free disc
+and halo, the disc's pitch, the arm weights' partition of unity, the arm
+layout and winding, the X field's lines and flux, the densities).  The grid
+model's interpolation is pinned by exactness on multilinear
 fields, by scipy's linear grid interpolator and by node values
 (``tests/test_oracle_grid.py``); the stacked WMAP model of Sec. 4.3 by the
 magnitude, pitch and elevation of each of its Eq. 13 components and its
