@@ -432,7 +432,11 @@ int synax_surrogate_train(synax_surrogate_t* s, int n_steps, uint64_t seed, void
 
 /* Evaluate: theta_dev [n][n_theta] -> coeffs_dev [n][3][n_basis] (device
  * float32, physical units).  With gcoeff_dev [n][3][n_basis] (a seed
- * dL/dc) also writes gtheta_dev [n][n_theta] = dL/dtheta (both or neither). */
+ * dL/dc) also writes gtheta_dev [n][n_theta] = dL/dtheta (both or neither).
+ * Stream-ordered on `stream`; the seed's conversion forks onto a stream of
+ * the handle and joins back before the call's last kernels, so the call
+ * may be captured into a CUDA graph.  Calls on one handle must not overlap
+ * (they share its buffers). */
 int synax_surrogate(synax_surrogate_t* s, const float* theta_dev, int n, float* coeffs_dev,
                     const float* gcoeff_dev, float* gtheta_dev, void* stream);
 

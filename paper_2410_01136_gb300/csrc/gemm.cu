@@ -3,7 +3,8 @@
 // for the surrogate MLP (bias, GELU, GELU', MSE, affine output, transposed
 // copies).
 //
-// Persistent and warp-specialised: min(tiles, SMs) CTAs of 192 threads walk
+// Persistent and warp-specialised: min(tiles, SMs) CTAs (192 threads, or 320
+// for the GELU, GELU' and MSE epilogues, which get 8 epilogue warps) walk
 // the 128 x BN output tiles (row-major tile order, so concurrent CTAs share
 // A row blocks and the whole B operand stays in L2):
 //   warp 0 (one thread)  TMA producer: a ring of ST stages, each a 128x64 A
@@ -14,9 +15,11 @@
 //                        tcgen05.commit frees the stage ("empty") and, after
 //                        a tile's last stage, hands the accumulator to the
 //                        epilogue ("acc_full");
-//   warps 2-5            epilogue: tcgen05.ld of their 32 TMEM lanes (warp w
-//                        reads lanes 32 (w % 4) .. +31), epilogue arithmetic,
-//                        then release the accumulator ("acc_empty").  FP32
+//   warps 2-5 (2-9)      epilogue: tcgen05.ld of their 32 TMEM lanes (warp w
+//                        reads lanes 32 (w % 4) .. +31; with 8 warps, warps
+//                        w and w + 4 take the two column halves), epilogue
+//                        arithmetic, then release the accumulator
+//                        ("acc_empty", one arrival per warp).  FP32
 //                        outputs go through shared memory: 128 x 32 chunks in
 //                        the 128-byte swizzle (conflict-free writes), stored by
 //                        one thread with TMA (cp.async.bulk.tensor, bounds
@@ -42,7 +45,20 @@ namespace synax {
 
 constexpr int kGemmBM = 128;
 constexpr int kGemmBK = 64;
-constexpr int kGemmThreads = 192;
+// Warp roles: 0 TMA producer, 1 MMA issuer, then the epilogue warps.  The
+// epilogues that store from registers (GELU, GELU', MSE: BF16 outputs, one
+// row per thread) are latency-bound with one warp per scheduler, so they get
+// 8 warps, two per TMEM lane quadrant, each taking half of the tile's
+// columns; the FP32 epilogues keep 4, one per quadrant, which their TMA-store
+// staging chunks (128 rows x 32 columns) are laid out for.
+template <int EPI>
+constexpr int gemm_epi_warps() {
+    return EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD || EPI == EPI_MSE ? 8 : 4;
+}
+template <int EPI>
+constexpr int gemm_threads() {
+    return 64 + 32 * gemm_epi_warps<EPI>();
+}
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
 
 template <int BN>
@@ -183,7 +199,7 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
 }
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(gemm_threads<EPI>(), 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ CUtensorMap tmC, int M, int N, int K, GemmEpiParams ep, int* err) {
     using C = GemmCfg<BN>;
@@ -199,7 +215,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     uint64_t* acc_empty = acc_full + 2;   // [2]
     uint64_t* drain = acc_empty + 2;
     uint32_t* tmem_slot = (uint32_t*)(drain + 1);
-    __shared__ float red[4];
+    constexpr int EW = gemm_epi_warps<EPI>();
+    __shared__ float red[8];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -212,7 +229,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&acc_full[b], 1);
-            tc::mbar_init(&acc_empty[b], 4);
+            tc::mbar_init(&acc_empty[b], EW);
         }
         tc::mbar_init(drain, 1);
         tc::fence_mbar_init();
@@ -289,16 +306,19 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
         }
     } else {
-        // epilogue warps 2..5: TMEM lanes 32 (warp % 4) .. +31
+        // epilogue warps 2 .. 2 + EW - 1: TMEM lanes 32 (warp % 4) .. +31,
+        // columns [c_lo, c_lo + COLS) of the tile
         const int q = warp & 3;
+        constexpr int COLS = BN / (EW / 4);
+        const int c_lo = ((warp - 2) >> 2) * COLS;
         int j = 0;
         int stg = 0;       // staging chunks used (TMA-store path)
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             const int buf = j & 1;
-            // all four epilogue warps agree (they share named barriers below):
+            // all EW epilogue warps agree (they share named barriers below):
             // every one of them reaches this reduction each tile, waited or not
             const bool mine = mbar_wait_clock(&acc_full[buf], (j >> 1) & 1);
-            const bool have = tc::named_and(2, 128, mine);
+            const bool have = tc::named_and(2, 32 * EW, mine);
             if (!have) {
                 ok = false;
                 break;
@@ -313,6 +333,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             }
             const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
             constexpr bool kF32Out = EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC;
+            static_assert(!kF32Out || EW == 4, "the TMA-store staging serves one warp per lane quadrant");
             if (kF32Out && ep.tma_store) {
                 // 32 columns at a time through a swizzled staging chunk and a TMA store
                 const int r = q * 32 + lane;                      // row within the tile
@@ -369,9 +390,9 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 // TMEM reads pipelined one 16-column chunk ahead of the epilogue
                 // arithmetic: even chunks in ra, odd chunks in rb (BN is a multiple of 32)
                 uint32_t ra[16], rb[16];
-                tc::tmem_ld16_async(base, ra);
+                tc::tmem_ld16_async(base + (uint32_t)c_lo, ra);
                 tc::tmem_wait_ld();
-                for (int c = 0; c < BN; c += 32) {
+                for (int c = c_lo; c < c_lo + COLS; c += 32) {
                     tc::tmem_ld16_async(base + (uint32_t)(c + 16), rb);
                     if (row_ok && n0 + c < N) {
                         float v[16];
@@ -381,7 +402,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq);
                     }
                     tc::tmem_wait_ld();
-                    if (c + 32 < BN) tc::tmem_ld16_async(base + (uint32_t)(c + 32), ra);
+                    if (c + 32 < c_lo + COLS) tc::tmem_ld16_async(base + (uint32_t)(c + 32), ra);
                     if (row_ok && n0 + c + 16 < N) {
                         float v[16];
 #pragma unroll
@@ -389,7 +410,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         const int nv = N - (n0 + c + 16) < 16 ? N - (n0 + c + 16) : 16;
                         epilogue16<EPI>(ep, v, row, n0 + c + 16, nv, trow, sq);
                     }
-                    if (c + 32 < BN) tc::tmem_wait_ld();
+                    if (c + 32 < c_lo + COLS) tc::tmem_wait_ld();
                 }
             }
             tc::fence_before_sync();
@@ -408,7 +429,11 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     __syncthreads();
     if constexpr (EPI == EPI_MSE) {
         // fixed-order reduction of the squared residuals of this CTA's tiles
-        if (threadIdx.x == 0) ep.loss_partial[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+        if (threadIdx.x == 0) {
+            float l = (red[0] + red[1]) + (red[2] + red[3]);
+            if constexpr (EW == 8) l += (red[4] + red[5]) + (red[6] + red[7]);
+            ep.loss_partial[blockIdx.x] = l;
+        }
     }
     if (warp == 1) {
         tc::fence_after_sync();
@@ -546,7 +571,7 @@ int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, in
         ((uintptr_t)ep.out_f32 & 15) == 0 && (ep.ld_f32 & 3) == 0 &&
         make_out_map(&mc, ep.out_f32, M, N, ep.ld_f32) == SYNAX_OK)
         ep.tma_store = 1;
-    k_gemm_bf16<BN, EPI><<<grid, kGemmThreads, GemmCfg<BN>::SMEM, st>>>(ma, mb, mc, M, N, K, ep, err);
+    k_gemm_bf16<BN, EPI><<<grid, gemm_threads<EPI>(), GemmCfg<BN>::SMEM, st>>>(ma, mb, mc, M, N, K, ep, err);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
 }

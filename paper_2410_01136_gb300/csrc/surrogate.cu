@@ -492,6 +492,10 @@ struct synax_surrogate_s {
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_seed = 0;
     long long graph_n = -1;
+    // evaluation: the VJP seed's conversion runs on a side stream forked from
+    // the caller's and joined before the backward products
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -510,6 +514,9 @@ void free_all(synax_surrogate_t* s) {
     }
     if (s->graph) cudaGraphExecDestroy(s->graph);
     if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
 }
 
 LayerTable layer_table(const synax_surrogate_t* s, bool with_tiles) {
@@ -823,6 +830,9 @@ int synax_surrogate_create(const synax_surrogate_cfg* cfg, synax_surrogate_t** o
     if (e == cudaSuccess) e = cudaMemcpy(s->basis_rows_dev, s->rows.data(), 4 * (size_t)c.n_basis, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_h12, h12, sizeof h12);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) return fail(record_cuda_error((int)e));
     if ((rc = gemm_init()) != SYNAX_OK) return fail(rc);
     if (c.basis_kind == SYNAX_SUR_BASIS_SRHT) {
@@ -1085,6 +1095,21 @@ int synax_surrogate(synax_surrogate_t* s, const float* theta_dev, int n, float* 
     const bool vjp = gcoeff_dev != nullptr;
     for (int r0 = 0; r0 < n; r0 += s->E) {
         const int m = n - r0 < s->E ? n - r0 : s->E;
+        if (vjp) {
+            // the seed's scaling and BF16 rounding depend only on the caller's
+            // seed: they run on the side stream (after everything enqueued so
+            // far, including the previous chunk's use of eD0) while the
+            // forward products run here; HBM-bound, it overlaps the
+            // epilogue-bound forward layers
+            cudaError_t e = cudaEventRecord(s->ev_fork, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+            if (e != cudaSuccess) return record_cuda_error((int)e);
+            k_seed_out<<<grid_for((long long)m * s->n_out), 256, 0, s->side>>>(
+                gcoeff_dev + (long long)r0 * s->n_out, (long long)m * s->n_out, s->scale, s->eD0);
+            SX_TRY(launch_status());
+            e = cudaEventRecord(s->ev_join, s->side);
+            if (e != cudaSuccess) return record_cuda_error((int)e);
+        }
         GatherArgs a = gather_identity(s, theta_dev + (long long)r0 * nt, m, s->eX[0], nullptr, nullptr);
         k_gather_input<<<(m + 3) / 4, 128, 0, st>>>(a);
         SX_TRY(launch_status());
@@ -1108,11 +1133,12 @@ int synax_surrogate(synax_surrogate_t* s, const float* theta_dev, int n, float* 
             }
         }
         if (!vjp) continue;
+        {
+            const cudaError_t e = cudaStreamWaitEvent(st, s->ev_join, 0);
+            if (e != cudaSuccess) return record_cuda_error((int)e);
+        }
         bf16* d = s->eD0;
         bf16* d2 = s->eD1;
-        k_seed_out<<<grid_for((long long)m * s->n_out), 256, 0, st>>>(gcoeff_dev + (long long)r0 * s->n_out,
-                                                                       (long long)m * s->n_out, s->scale, d);
-        SX_TRY(launch_status());
         for (int l = L - 1; l > 0; --l) {
             GemmEpiParams eb{};
             eb.aux = s->eZ[l - 1];
