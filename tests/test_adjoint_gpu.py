@@ -130,6 +130,28 @@ def test_chi2_jf12(torch, n_steps):
     assert_parity(maps.cpu().numpy(), fwd, 1e-6, 1e-5, "adjoint maps_out vs forward")
 
 
+def test_chi2_jf12_max_sizes(torch):
+    """The chi^2 gradient at the ABI's largest Nside (8192: pixel runs at
+    the polar-cap boundary and at the last pixel) and largest step count
+    (65536), against Richardson differences of the oracle on those pixels."""
+    npix = 12 * 8192 ** 2
+    ncap = 2 * 8192 * (8192 - 1)
+    cases = [(inputs.config2().replace(nside=8192, n_steps=64), ncap - 24, 48),
+             (inputs.config2().replace(nside=8192, n_steps=64), npix - 32, 32),
+             (inputs.config2().replace(nside=2, n_steps=65536), 20, 6)]
+    for base, begin, count in cases:
+        pix = np.arange(begin, begin + count)
+        th_t = inputs.perturbed_theta(base.theta, seed=9)
+        target = oracle.forward(base.with_theta(th_t), pix=pix)
+        target = target + inputs.target_noise(target.shape, seed=10, sigma=0.5)
+        prob = base.replace(pix_begin=begin, pix_count=count)
+        grad, chi2 = adjoint(prob, target=torch.tensor(target, dtype=torch.float32, device="cuda"), sigma=0.5)
+        maps = oracle.forward(base, pix=pix)
+        assert float(chi2.item()) == pytest.approx(oracle.chi2(maps, target, 0.5), rel=1e-5)
+        ref, _ = fd_reference(base, lambda m: oracle.chi2(m, target, 0.5), pix=pix)
+        assert_grad(grad.cpu().numpy(), ref, what=f"chi2 Nside {base.nside}, N {base.n_steps}, pixels {begin}+{count}")
+
+
 @pytest.mark.slow
 def test_vjp_full_size_sampled(torch):
     """Nside 64, 512 steps, 4 frequencies, 16 parameters (the adjoint workload),

@@ -118,6 +118,28 @@ def test_pixel_ranges_bitwise(torch):
         assert np.array_equal(part, full[:, :, begin:begin + n])
 
 
+def test_max_nside_pixel_runs(torch):
+    """Nside 8192, the largest the ABI takes (805 M pixels): runs of pixels
+    at the north pole, across the polar-cap / equatorial-belt boundary, on
+    the equator and up to the last pixel at the south pole."""
+    base = inputs.config2().replace(nside=8192, n_steps=64)
+    npix = 12 * 8192 ** 2
+    ncap = 2 * 8192 * (8192 - 1)                 # pixels of the north polar cap
+    for begin, count in ((0, 96), (ncap - 40, 80), (npix // 2 - 40, 80), (npix - 96, 96)):
+        g = gpu_map(torch, base.replace(pix_begin=begin, pix_count=count))
+        o = oracle.forward(base, pix=np.arange(begin, begin + count))
+        assert g.shape == (4, 3, count)
+        assert_parity(g, o, what=f"Nside 8192, pixels {begin} .. +{count}")
+
+
+def test_max_steps(torch):
+    """65536 steps per ray, the largest the ABI takes (24 rays)."""
+    base = inputs.config2().replace(nside=2, n_steps=65536)
+    g = gpu_map(torch, base.replace(pix_begin=10, pix_count=24))
+    o = oracle.forward(base, pix=np.arange(10, 34))
+    assert_parity(g, o, what="65536 steps")
+
+
 @pytest.mark.parametrize("rule", [1, 2])
 def test_rm_rules(torch, rule):
     prob = inputs.config2().replace(nside=4, n_steps=128, rm_rule=rule)
