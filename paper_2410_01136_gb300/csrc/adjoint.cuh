@@ -19,7 +19,7 @@ constexpr int kAdjMinBlocks = 5;
 // field intermediates: 4 CTAs per SM leave them 128 registers (JF12-type map
 // + gradient 0.604 ms against 0.624 ms at 5 CTAs, where 264 bytes spilled).
 template <int MODEL> constexpr int adj_min_blocks() {
-    return MODEL == SYNAX_MODEL_GRID || MODEL == SYNAX_MODEL_JF12 ? 4 : kAdjMinBlocks;
+    return MODEL == SYNAX_MODEL_GRID || MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP ? 4 : kAdjMinBlocks;
 }
 
 template <int MODEL> struct Grad;
@@ -200,7 +200,7 @@ struct GridAcc {
     }
 };
 
-// The FP32 JF12-type reverse march of one lane, two samples per iteration:
+// The FP32 JF12-type and WMAP-type reverse march of one lane, two samples per iteration:
 // samples n and n - 1 as element pairs (the forward lane march pairs n and
 // n + 1), with the field, emission, phase and gradient arithmetic of the
 // per-sample loop in adjoint_cta element by element.  The walk back of the RM
@@ -209,19 +209,21 @@ struct GridAcc {
 // retraces pass 1's sums.  An odd chunk start leaves a placeholder second
 // element whose emission, integrand and seed are zero.  Gradient terms with a
 // constant factor are summed raw and scaled once at the end.
-template <int NF>
-__device__ __forceinline__ void reverse_lane_pair_jf12(const MapParams<float>& P, const AdjParams<float>& A,
-                                                       const float* s_arms, const Los<float>& L, const ff* nd,
-                                                       int n0, int n1, float dr, float dr_lo, const ff* cd,
-                                                       const float* hr, const float* hi, const float* c2, float GI,
-                                                       float GIp, ff Q, float after, float* g, float* garm) {
+template <int MODEL, int NF>
+__device__ __forceinline__ void reverse_lane_pair(const MapParams<float>& P, const AdjParams<float>& A,
+                                                  const float* s_arms, const Los<float>& L, const ff* nd,
+                                                  int n0, int n1, float dr, float dr_lo, const ff* cd,
+                                                  const float* hr, const float* hi, const float* c2, float GI,
+                                                  float GIp, ff Q, float after, float* g, float* garm) {
+    static_assert(MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP, "paired reverse march");
     const float* m = P.m;
     ArmTracker<float> trk;
-    trk.init(P, nd, n1 - 1, dr, dr_lo);
+    if constexpr (MODEL == SYNAX_MODEL_JF12) trk.init(P, nd, n1 - 1, dr, dr_lo);
     const float q = P.q, w_own = P.w_own;
     const float half_p1 = 2.0f * q + 2.0f;
     const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
     float s8 = 0.f, s9 = 0.f, s10 = 0.f, s11a = 0.f, s11b = 0.f, s12 = 0.f, s13 = 0.f, s14 = 0.f, s15 = 0.f;
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f, w6 = 0.f, w7 = 0.f;   // WMAP-type
     float2 nh = make_float2(float(n1 - 1) + 0.5f, float(n1 - 2) + 0.5f);     // n + 1/2, exact
     for (int n = n1 - 1; n >= n0; n -= 2, nh = add2(nh, dup2(-2.0f))) {
         const float live_b = n - 1 >= n0 ? 1.0f : 0.0f;
@@ -229,12 +231,17 @@ __device__ __forceinline__ void reverse_lane_pair_jf12(const MapParams<float>& P
         const float2 x = fma2(t, dup2(L.n[0]), obs_x);
         const float2 y = fma2(t, dup2(L.n[1]), obs_y);
         const float2 z = fma2(t, dup2(L.n[2]), obs_z);
-        const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
-        ArmCoord<float> ab;
-        trk.step_pair(-1, ab);
         float2 B[3], N0, ne;
         pair2::Jf12Loc2 lc;
-        pair2::jf12_eval<true>(m, s_arms, x, y, z, aa, ab, B, N0, ne, &lc);
+        pair2::WmapLoc2 lw;
+        if constexpr (MODEL == SYNAX_MODEL_JF12) {
+            const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
+            ArmCoord<float> ab;
+            trk.step_pair(-1, ab);
+            pair2::jf12_eval<true>(m, s_arms, x, y, z, aa, ab, B, N0, ne, &lc);
+        } else {
+            pair2::wmap_eval<true>(m, x, y, z, B, N0, ne, &lw);
+        }
 
         // emission (Eq. 2, 5, 8) and RM integrand (Eq. 7), as the forward pair march
         float2 v = mul2(B[0], dup2(L.n[0]));
@@ -310,6 +317,28 @@ __device__ __forceinline__ void reverse_lane_pair_jf12(const MapParams<float>& P
         const float2 byb = fma2(bnb, dup2(L.n[1]), fma2(bbar, dup2(L.eb[1]), mul2(abar, dup2(L.el[1]))));
         const float2 bzb = fma2(bnb, dup2(L.n[2]), mul2(bbar, dup2(L.eb[2])));
 
+        if constexpr (MODEL == SYNAX_MODEL_WMAP) {
+            // Grad<WMAP>::accum element by element, b0 factored out of the
+            // psi and chi terms and the range test a 0/1 weight
+            const float2 brb = fma2(bxb, lw.c, mul2(byb, lw.s));
+            const float2 bpb = fma2(byb, lw.c, neg2(mul2(bxb, lw.s)));
+            const float2 rad = fma2(brb, lw.cp, mul2(bpb, lw.sp));       // brb cos psi + bpb sin psi
+            const float2 v0 = mul2(lw.env, fma2(lw.cc, rad, mul2(bzb, lw.sc)));
+            const float2 ea = mul2(lw.env, lw.inr);
+            const float2 dpsi = mul2(mul2(ea, lw.cc), fma2(bpb, lw.cp, neg2(mul2(brb, lw.sp))));
+            const float2 v3 = mul2(mul2(ea, lw.thz), fma2(bzb, lw.cc, neg2(mul2(lw.sc, rad))));
+            const float2 v2 = mul2(dpsi, lw.lnr8);
+            const float2 v5 = mul2(n0bar, lw.n0u), v7 = mul2(neb, lw.neu);
+            w0 += v0.x + v0.y;
+            w1 += dpsi.x + dpsi.y;
+            w2 += v2.x + v2.y;
+            w3 += v3.x + v3.y;
+            w4 += bxb.x + bxb.y;
+            w5 += v5.x + v5.y;
+            w6 += pbar.x + pbar.y;
+            w7 += v7.x + v7.y;
+            continue;
+        }
         // Grad<JF12>::accum element by element
         const float2 brb = fma2(bxb, lc.c, mul2(byb, lc.s));
         const float2 bpb = fma2(byb, lc.c, neg2(mul2(bxb, lc.s)));
@@ -334,6 +363,18 @@ __device__ __forceinline__ void reverse_lane_pair_jf12(const MapParams<float>& P
         s13 += pbar.x + pbar.y;
         s14 += v14.x + v14.y;
         s15 += v15.x + v15.y;
+    }
+    if constexpr (MODEL == SYNAX_MODEL_WMAP) {
+        const float b0 = m[mc::W_B0];
+        g[0] += w0;
+        g[1] += b0 * w1;
+        g[2] += b0 * w2;
+        g[3] += b0 * w3;
+        g[4] += w4;
+        g[5] += w5;
+        g[6] += w6;
+        g[7] += w7;
+        return;
     }
     g[8] += s8;
     g[9] += s9 * m[mc::J_BH_IZH2];
@@ -472,10 +513,10 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
         R* garm = &sm.garm[0][threadIdx.x];
 #pragma unroll
         for (int kk = 0; kk < NSLOT; ++kk) garm[kk * kAdjThreads] = R(0);
-        if constexpr (MODEL == SYNAX_MODEL_JF12 && sizeof(R) == 4) {
+        if constexpr ((MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP) && sizeof(R) == 4) {
             if (n0 < n1)
-                reverse_lane_pair_jf12<NF>(P, A, s_arms, L, nd, n0, n1, dr, dr_lo, cd, hr, hi, c2, GI, GIp,
-                                           Ph::add(O, S), after, g, garm);
+                reverse_lane_pair<MODEL, NF>(P, A, s_arms, L, nd, n0, n1, dr, dr_lo, cd, hr, hi, c2, GI, GIp,
+                                             Ph::add(O, S), after, g, garm);
         } else if (n0 < n1) {
             PT Q = Ph::add(O, S);                       // O + sum of f before sample n (after the update)
             ArmTracker<R> trk;

@@ -1312,22 +1312,95 @@ __device__ __forceinline__ void jf12_eval(const float* m, const float* arms, flo
     if constexpr (LOC) lc->n0u = mul2(dup2(m[mc::J_N0U]), prof);
 }
 
+// Intermediates of the WMAP-type field at two points for its parameter
+// gradient (the WMAP-type members of FieldLocal; inr is the 3-20 kpc range
+// as 0 or 1).
+struct WmapLoc2 {
+    float2 c, s, env, cp, sp, cc, sc, lnr8, thz, inr, n0u, neu;
+};
+
+// B (uG), N0 and n_e (cm^-3) of the WMAP-type model (Eq. 12-13) at two
+// points, element by element as Model<WMAP>::eval, the range test a select
+// instead of a branch; with LOC also the gradient's intermediates.
+template <bool LOC = false>
+__device__ __forceinline__ void wmap_eval(const float* m, float2 x, float2 y, float2 z, float2 B[3], float2& N0,
+                                          float2& ne, WmapLoc2* lc = nullptr) {
+    const float2 rho2 = fma2(x, x, mul2(y, y));
+    const float2 rho = f2(__fsqrt_rn(rho2.x), __fsqrt_rn(rho2.y));
+    const float2 rr = rcp_nr(rho);
+    const float2 ri = f2(rho2.x > 0.0f ? rr.x : 0.0f, rho2.y > 0.0f ? rr.y : 0.0f);
+    const float2 cq = mul2(x, ri), sq = mul2(y, ri);
+    const float2 c = f2(rho2.x > 0.0f ? cq.x : 1.0f, rho2.y > 0.0f ? cq.y : 1.0f);
+    const float2 s = f2(rho2.x > 0.0f ? sq.x : 0.0f, rho2.y > 0.0f ? sq.y : 0.0f);
+    const float2 az = f2(fabsf(z.x), fabsf(z.y));
+    const float2 e2a = mul2(dup2(-2.0f), az);
+    const float2 e2 = expf2(e2a);                                    // e^{-2|z|}
+    const float2 inv1 = rcp_nr(add2(dup2(1.0f), e2));
+    const float2 sech2 = mul2(mul2(mul2(dup2(4.0f), e2), inv1), inv1);
+    const bool in_a = rho.x >= 3.0f && rho.x <= 20.0f, in_b = rho.y >= 3.0f && rho.y <= 20.0f;
+    const float2 r8 = mul2(rho, dup2(0.125f));
+    const float2 lnr8 = f2(in_a ? logf(r8.x) : 0.0f, in_b ? logf(r8.y) : 0.0f);
+    const float2 psi = f2(in_a ? fmaf(m[mc::W_PSI1], lnr8.x, m[mc::W_PSI0]) : 0.0f,
+                          in_b ? fmaf(m[mc::W_PSI1], lnr8.y, m[mc::W_PSI0]) : 0.0f);
+    float2 th = mul2(add2(dup2(1.0f), neg2(e2)), inv1);                 // tanh |z|
+    th = f2(z.x < 0.0f ? -th.x : th.x, z.y < 0.0f ? -th.y : th.y);
+    const float2 chi = f2(in_a ? m[mc::W_CHI0] * th.x : 0.0f, in_b ? m[mc::W_CHI0] * th.y : 0.0f);
+    const float2 env = expf2(neg2(add2(mulc(rho, 0.125), az)));
+    const float2 amp = mul2(dup2(m[mc::W_B0]), env);
+    float2 sp, cp, sc, cc;
+    sincosf(psi.x, &sp.x, &cp.x);
+    sincosf(psi.y, &sp.y, &cp.y);
+    sincosf(chi.x, &sc.x, &cc.x);
+    sincosf(chi.y, &sc.y, &cc.y);
+    const float2 br = mul2(mul2(amp, cp), cc), bp = mul2(mul2(amp, sp), cc);
+    B[0] = add2(fma2(br, c, neg2(mul2(bp, s))), dup2(m[mc::W_BUX]));
+    B[1] = fma2(br, s, mul2(bp, c));
+    B[2] = mul2(amp, sc);
+    // CR density (fast primitives: magnitudes only), as cr_density
+    const float2 e2c = mul2(dup2((float)(-2.0 * kLog2e)), az);
+    const float2 ec = f2(ex2_approx(e2c.x), ex2_approx(e2c.y));
+    const float2 onep = add2(dup2(1.0f), ec);
+    const float2 iv = f2(rcp_approx(onep.x), rcp_approx(onep.y));
+    const float2 er = mul2(dup2((float)(-0.2 * kLog2e)), rho);
+    const float2 eR = f2(ex2_approx(er.x), ex2_approx(er.y));
+    const float2 n0u = mul2(dup2(m[mc::W_N0U]), mul2(eR, mul2(mul2(dup2(4.0f), ec), mul2(iv, iv))));
+    N0 = mul2(dup2(m[mc::W_N0OBS]), n0u);
+    const float2 neu = mul2(expf2(neg2(mulc(rho, 0.05))), sech2);
+    ne = mul2(dup2(m[mc::W_NE0]), neu);
+    if constexpr (LOC) {
+        lc->c = c;
+        lc->s = s;
+        lc->env = env;
+        lc->cp = cp;
+        lc->sp = sp;
+        lc->cc = cc;
+        lc->sc = sc;
+        lc->lnr8 = lnr8;
+        lc->thz = th;
+        lc->inr = f2(in_a ? 1.0f : 0.0f, in_b ? 1.0f : 0.0f);
+        lc->n0u = n0u;
+        lc->neu = neu;
+    }
+}
+
 }  // namespace pair2
 
-// The FP32 JF12-type lane march, two samples per iteration (see pair2).  Same
-// contract as march_lane.
-template <int NF>
-__device__ __forceinline__ void march_lane_pair_jf12(const MapParams<float>& P, const float* s_arms,
-                                                     const Los<float>& L, const ff* nd, int n0, int n1, float dr,
-                                                     float dr_lo, const ff* cd, float& accI, float* zr, float* zi,
-                                                     ff& S) {
+// The FP32 JF12-type and WMAP-type lane march, two samples per iteration
+// (see pair2).  Same contract as march_lane.
+template <int MODEL, int NF>
+__device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const float* s_arms,
+                                                const Los<float>& L, const ff* nd, int n0, int n1, float dr,
+                                                float dr_lo, const ff* cd, float& accI, float* zr, float* zi,
+                                                ff& S) {
     float2 zrp[NF], zip[NF];                      // (even samples, odd samples) per frequency
 #pragma unroll
     for (int k = 0; k < NF; ++k) { zrp[k] = dup2(0.0f); zip[k] = dup2(0.0f); }
     float2 accI2 = dup2(0.0f);
     S = ff{0.0f, 0.0f};
     ArmTracker<float> trk;
-    if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
+    if constexpr (MODEL == SYNAX_MODEL_JF12) {
+        if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
+    }
     float2 nh = make_float2(float(n0) + 0.5f, float(n0) + 1.5f);     // n + 1/2, exact
     const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
     for (int n = n0; n < n1; n += 2, nh = add2(nh, dup2(2.0f))) {
@@ -1337,11 +1410,15 @@ __device__ __forceinline__ void march_lane_pair_jf12(const MapParams<float>& P, 
         const float2 x = fma2(t, dup2(L.n[0]), obs_x);
         const float2 y = fma2(t, dup2(L.n[1]), obs_y);
         const float2 z = fma2(t, dup2(L.n[2]), obs_z);
-        const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
-        ArmCoord<float> ab;
-        trk.step_pair(+1, ab);
         float2 B[3], N0, ne;
-        pair2::jf12_eval(P.m, s_arms, x, y, z, aa, ab, B, N0, ne);
+        if constexpr (MODEL == SYNAX_MODEL_JF12) {
+            const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
+            ArmCoord<float> ab;
+            trk.step_pair(+1, ab);
+            pair2::jf12_eval(P.m, s_arms, x, y, z, aa, ab, B, N0, ne);
+        } else {
+            pair2::wmap_eval(P.m, x, y, z, B, N0, ne);
+        }
         // emission (Eq. 2, 5, 8) and RM integrand (Eq. 7), element-wise as emit()
         float2 v = mul2(B[0], dup2(L.n[0]));
         v = fma2(B[1], dup2(L.n[1]), v);
@@ -1430,8 +1507,8 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
                                            typename PhaseOps<R>::T& S) {
     using Ph = PhaseOps<R>;
     using PT = typename Ph::T;
-    if constexpr (sizeof(R) == 4 && MODEL == SYNAX_MODEL_JF12) {
-        march_lane_pair_jf12<NF>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
+    if constexpr (sizeof(R) == 4 && (MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP)) {
+        march_lane_pair<MODEL, NF>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
         return;
     }
     accI = R(0);
