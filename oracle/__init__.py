@@ -19,8 +19,9 @@ model is defined by this project (after Jansson & Farrar 2012), so no
 published values pin it; its evaluation is pinned by properties the
 definition implies (``tests/test_oracle_jf12.py``: a divergence-free disc
 and halo, the disc's pitch, the arm weights' partition of unity, the arm
-layout and winding, the X field's lines and flux, the densities).  The grid
-model's interpolation is pinned by exactness on multilinear
+layout and winding, the X field's lines and flux, the densities); the
+WMAP-type field by Eq. 13's direction, its symmetry, the uniform x field and
+its densities (``tests/test_oracle_wmap.py``).  The grid model's interpolation is pinned by exactness on multilinear
 fields, by scipy's linear grid interpolator and by node values
 (``tests/test_oracle_grid.py``); the stacked WMAP model of Sec. 4.3 by the
 magnitude, pitch and elevation of each of its Eq. 13 components and its
