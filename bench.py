@@ -185,6 +185,25 @@ def oracle_row(prob, n_pix_sample: int, free, note: str = "") -> dict:
     return out
 
 
+def slowest_rank_times(times, device=None) -> list:
+    """Each per-rank time (ms) replaced by its maximum over the ranks of the
+    initialised process group (the job takes as long as its slowest rank);
+    unchanged on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(x) for x in times]
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Units of all ranks over the slowest rank's time (weak scaling: every
+    rank processes its own units)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -819,13 +838,9 @@ def run_synax(args):
     ms = float(np.mean(step_ms))
     ms_e2e = float(np.mean(e2e_ms))
     ms_fwd = float(np.mean(fwd_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, ms_e2e, ms_fwd], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e, ms_fwd = [float(x) for x in t.tolist()]
+    ms, ms_e2e, ms_fwd = slowest_rank_times([ms, ms_e2e, ms_fwd], device=dev)
     samples = prob.samples
-    value = world * samples / (ms * 1e-3)
+    value = whole_job_rate(world, samples, ms)
 
     # roofline of the dominant kernel (the adjoint march): algorithmic FP32 and
     # MUFU work per launch over the launch's measured duration
@@ -858,12 +873,12 @@ def run_synax(args):
         "config": {"workload": WORKLOAD, "nside": 64, "n_steps": 512, "n_freq": 4, "n_theta": 16,
                    "samples_per_step": samples, "global_batch": world, "l2": "flushed between steps "
                    "(256 MiB write), inputs 2.4 MB", "parallelism": f"replicas x{world}"},
-        "maps_grad_per_s": world / (ms * 1e-3),
-        "forward_samples_per_s": world * samples / (ms_fwd * 1e-3),
+        "maps_grad_per_s": whole_job_rate(world, 1, ms),
+        "forward_samples_per_s": whole_job_rate(world, samples, ms_fwd),
         "forward_ms": ms_fwd,
         "roofline": roof,
         "clocks": clk,
-        "e2e": {"value": world * samples / (ms_e2e * 1e-3), "unit": "samples/s",
+        "e2e": {"value": whole_job_rate(world, samples, ms_e2e), "unit": "samples/s",
                 "h2d_bytes_per_step": int(target.numel() * 4),
                 "d2h_bytes_per_step": int(maps.numel() * 4 + 16 * 8 + 8),
                 "ms_per_step": ms_e2e,

@@ -1,0 +1,76 @@
+"""The benchmark's multi-rank bookkeeping on CPU ranks (gloo, world size 2):
+every rank's per-step times are replaced by their maximum over the ranks,
+the whole-job rate is all ranks' units over the slowest rank's time, and
+the reference arm does its work on rank 0 only."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r measured (1 + r, 5 - r, 2) ms for (step, end to end, forward)
+        got = bench.slowest_rank_times([1.0 + rank, 5.0 - rank, 2.0], device="cpu")
+        np.save(f"{out_path}.{rank}.npy", np.array(got))
+    finally:
+        dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_slowest_rank_times_two_gloo_ranks(tmp_path):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "times")
+    mp.spawn(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True)
+    for r in range(2):
+        assert np.array_equal(np.load(f"{out}.{r}.npy"), [2.0, 5.0, 2.0])
+
+
+def test_single_process_and_rate():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.slowest_rank_times([1.5, 2.5]) == [1.5, 2.5]
+    # weak scaling: 4 ranks of 25 165 824 samples in 0.605 ms
+    assert bench.whole_job_rate(4, 25165824, 0.605) == pytest.approx(4 * 25165824 / 0.605e-3, rel=1e-15)
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    """Under torchrun a rank other than 0 prints nothing and exits 0 without
+    running the oracle."""
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
+
+
+def test_gpu_arm_fails_loudly_without_a_gpu():
+    """The product path has no CPU fallback: without CUDA the GPU arm exits
+    non-zero instead of printing a number."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "1", "--warmup", "0",
+                        "--no-batch", "--no-grid", "--no-surrogate", "--no-cpu-baseline"],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    for line in r.stdout.splitlines():
+        assert "value" not in json.loads(line) if line.startswith("{") else True
