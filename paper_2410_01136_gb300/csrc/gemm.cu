@@ -23,9 +23,11 @@
 //                        outputs go through shared memory: 128 x 32 chunks in
 //                        the 128-byte swizzle (conflict-free writes), stored by
 //                        one thread with TMA (cp.async.bulk.tensor, bounds
-//                        clipped), two staging buffers in flight; other
-//                        outputs are vectorised row stores (coalesced
-//                        transposed stores).
+//                        clipped), two staging buffers in flight; the GELU
+//                        epilogue's FP32 pre-activation likewise, per warp
+//                        in 32 x 32 blocks of its 4 KB slot of the same
+//                        area; other outputs are vectorised row stores
+//                        (coalesced transposed stores).
 // With two accumulators the MMAs of tile i+1 run while tile i is stored.
 // Every mbarrier wait gives up after ~1 s of SM clocks and sets *err; each
 // role then stops, the MMA issuer waits (bounded) for its issued MMAs, the
@@ -108,9 +110,11 @@ __device__ __forceinline__ void load16(const float* __restrict__ p, int col0, in
 }
 
 // Epilogue of 16 consecutive columns col0.. of one row (nv of them valid).
+// With zkeep (EPI_BIAS_GELU whose pre-activation goes through the TMA-store
+// staging), the 16 pre-activations are copied there instead of stored.
 template <int EPI>
 __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float* v, int row, int col0, int nv,
-                                           long long trow, float& sq) {
+                                           long long trow, float& sq, float* zkeep = nullptr) {
     if constexpr (EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC) {
         float* o = ep.out_f32 + (long long)row * ep.ld_f32 + col0;
         float r[16], b[16], sc[16], sh[16];
@@ -162,7 +166,10 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
             r[i] = x;
         }
         if constexpr (EPI == EPI_BIAS_GELU) {
-            if (ep.out_z) {
+            if (zkeep) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) zkeep[i] = z16[i];
+            } else if (ep.out_z) {
                 float* oz = ep.out_z + (long long)row * ep.ld_z + col0;
                 if (nv == 16 && (((uintptr_t)oz) & 15) == 0) {
                     float4* d = reinterpret_cast<float4*>(oz);
@@ -313,6 +320,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int c_lo = ((warp - 2) >> 2) * COLS;
         int j = 0;
         int stg = 0;       // staging chunks used (TMA-store path)
+        int zblk = 0;      // pre-activation blocks stored by this warp (GELU)
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             const int buf = j & 1;
             // all EW epilogue warps agree (they share named barriers below):
@@ -389,7 +397,16 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             } else {
                 // TMEM reads pipelined one 16-column chunk ahead of the epilogue
                 // arithmetic: even chunks in ra, odd chunks in rb (BN is a multiple of 32)
+                // The GELU pre-activation (ep.tma_store) goes through this
+                // warp's 4 KB slot of the staging area: 32 rows x 32 columns in
+                // the 128-byte swizzle, one TMA store per block.
+                constexpr bool kZStage = EPI == EPI_BIAS_GELU;
+                const bool zst = kZStage && ep.tma_store;
+                uint8_t* zslot = sC + (warp - 2) * 4096;
                 uint32_t ra[16], rb[16];
+                float za[16], zb[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) za[i] = zb[i] = 0.0f;
                 tc::tmem_ld16_async(base + (uint32_t)c_lo, ra);
                 tc::tmem_wait_ld();
                 for (int c = c_lo; c < c_lo + COLS; c += 32) {
@@ -399,7 +416,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
                         const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
-                        epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq);
+                        epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq, zst ? za : nullptr);
                     }
                     tc::tmem_wait_ld();
                     if (c + 32 < c_lo + COLS) tc::tmem_ld16_async(base + (uint32_t)(c + 32), ra);
@@ -408,7 +425,30 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(rb[i]);
                         const int nv = N - (n0 + c + 16) < 16 ? N - (n0 + c + 16) : 16;
-                        epilogue16<EPI>(ep, v, row, n0 + c + 16, nv, trow, sq);
+                        epilogue16<EPI>(ep, v, row, n0 + c + 16, nv, trow, sq, zst ? zb : nullptr);
+                    }
+                    if constexpr (kZStage) {
+                        if (zst && n0 + c < N) {          // the same for every lane of the warp
+                            // the slot's previous block has been read by its store
+                            if (lane == 0 && zblk > 0) tc::bulk_wait_read<0>();
+                            __syncwarp();
+                            // rows past M hold stale values: the store clips them
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                *reinterpret_cast<float4*>(zslot + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                                    make_float4(za[4 * j], za[4 * j + 1], za[4 * j + 2], za[4 * j + 3]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                *reinterpret_cast<float4*>(zslot + lane * 128 + (((j + 4) ^ (lane & 7)) << 4)) =
+                                    make_float4(zb[4 * j], zb[4 * j + 1], zb[4 * j + 2], zb[4 * j + 3]);
+                            tc::fence_proxy_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                tc::tma_store_2d(&tmC, zslot, n0 + c, m0 + q * 32);
+                                tc::bulk_commit();
+                            }
+                            ++zblk;
+                        }
                     }
                     if (c + 32 < c_lo + COLS) tc::tmem_wait_ld();
                 }
@@ -423,6 +463,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (lane == 0) red[warp - 2] = sq;
         }
         if (threadIdx.x == 64 && stg > 0) tc::bulk_wait_all();   // every TMA store has completed
+        if (lane == 0 && zblk > 0) tc::bulk_wait_all();            // this warp's pre-activation stores
     }
     if (!ok) atomicExch(err, 1);
     tc::fence_before_sync();
@@ -543,13 +584,13 @@ cudaError_t set_smem_attrs() {
     return e;
 }
 
-// 2-D FP32 tensor map of the output [rows][ld], box 32 x 128, 128-byte swizzle.
-int make_out_map(CUtensorMap* map, const void* base, int rows, int cols, int ld) {
+// 2-D FP32 tensor map of an output [rows][ld], box 32 x box_rows, 128-byte swizzle.
+int make_out_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows = kGemmBM) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return SYNAX_ECUDA;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {32u, (cuuint32_t)kGemmBM};
+    cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -570,6 +611,10 @@ int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, in
     if (kF32Out && !(EPI == EPI_SCALE_ACC && ep.accumulate) && ep.out_f32 &&
         ((uintptr_t)ep.out_f32 & 15) == 0 && (ep.ld_f32 & 3) == 0 &&
         make_out_map(&mc, ep.out_f32, M, N, ep.ld_f32) == SYNAX_OK)
+        ep.tma_store = 1;
+    // GELU: the FP32 pre-activation through per-warp 32 x 32 staging blocks
+    if (EPI == EPI_BIAS_GELU && ep.out_z && ((uintptr_t)ep.out_z & 15) == 0 && (ep.ld_z & 3) == 0 &&
+        make_out_map(&mc, ep.out_z, M, N, ep.ld_z, 32) == SYNAX_OK)
         ep.tma_store = 1;
     k_gemm_bf16<BN, EPI><<<grid, gemm_threads<EPI>(), GemmCfg<BN>::SMEM, st>>>(ma, mb, mc, M, N, K, ep, err);
     const cudaError_t e = cudaGetLastError();
