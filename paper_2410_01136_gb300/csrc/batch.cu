@@ -195,7 +195,6 @@ int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_p
         wsum += (double)npix[s] * sets[s].n_steps;
     }
     p->lpr = lanes_per_ray((int)std::lround(wsteps / wsum), tot_rays);
-    if (model == SYNAX_MODEL_WMAP) p->lpr = 32;
     p->rays = kAdjThreads / p->lpr;
     int rc = model == SYNAX_MODEL_JF12 ? batch_kernels_jf12(p->nf, p->lpr, &p->kern)
                                        : batch_kernels_wmap(p->nf, p->lpr, &p->kern);

@@ -126,10 +126,8 @@ inline int batch_kernels_for(int nf, int lpr, BatchKernels* out) {
         return SYNAX_OK;                                           \
     }
     SYNAX_PICK(1, 32) SYNAX_PICK(2, 32) SYNAX_PICK(4, 32) SYNAX_PICK(8, 32) SYNAX_PICK(16, 32)
-    if constexpr (MODEL == SYNAX_MODEL_JF12) {
-        SYNAX_PICK(1, 16) SYNAX_PICK(2, 16) SYNAX_PICK(4, 16) SYNAX_PICK(8, 16) SYNAX_PICK(16, 16)
-        SYNAX_PICK(1, 8) SYNAX_PICK(2, 8) SYNAX_PICK(4, 8) SYNAX_PICK(8, 8) SYNAX_PICK(16, 8)
-    }
+    SYNAX_PICK(1, 16) SYNAX_PICK(2, 16) SYNAX_PICK(4, 16) SYNAX_PICK(8, 16) SYNAX_PICK(16, 16)
+    SYNAX_PICK(1, 8) SYNAX_PICK(2, 8) SYNAX_PICK(4, 8) SYNAX_PICK(8, 8) SYNAX_PICK(16, 8)
 #undef SYNAX_PICK
     return SYNAX_ENOTSUP;
 }
