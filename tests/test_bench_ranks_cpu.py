@@ -74,3 +74,25 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
     assert r.returncode != 0
     for line in r.stdout.splitlines():
         assert "value" not in json.loads(line) if line.startswith("{") else True
+
+
+def test_roofline_accounting():
+    """The per-sample operation counts behind every row's roofline: the
+    JF12-type adjoint is 3 x (200 FP32 + 22 MUFU) at four frequencies and
+    FP32-bound; the grid adjoint adds 36 FP32 of node weights; the WMAP-type
+    and stacked models are bound by their MUFU counts (16 lanes per SM
+    against 128)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.march_roofline("jf12", 4, 4.0e10, 2070.0, True, "k")
+    assert r["ops_per_sample"] == {"fp32": 600, "mufu": 66} and r["pipe"] == "FP32"
+    assert r["peak"] == pytest.approx(152 * 128 * 2070e6 / 1e12)
+    assert r["frac"] == pytest.approx(4.0e10 * 600 / (152 * 128 * 2070e6))
+    f = bench.march_roofline("jf12", 4, 1.0e11, 2070.0, False, "k")
+    assert f["ops_per_sample"] == {"fp32": 200, "mufu": 22}
+    g = bench.march_roofline("grid", 1, 1.0, 2070.0, True, "k")
+    assert g["ops_per_sample"] == {"fp32": 486, "mufu": 33} and g["pipe"] == "FP32"
+    for model, fwd in (("wmap", {"fp32": 68, "mufu": 16}), ("wmap_stack", {"fp32": 107, "mufu": 27})):
+        w = bench.march_roofline(model, 1, 1.0e10, 2070.0, False, "k")
+        assert w["ops_per_sample"] == fwd and w["pipe"] == "MUFU"
+        assert w["peak"] == pytest.approx(152 * 16 * 2070e6 / 1e12)
