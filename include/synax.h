@@ -196,6 +196,8 @@ int synax_batch_latencies(synax_batch_plan* plan, double* ms_out);
 int synax_batch_plan_info(const synax_batch_plan* plan, long long* n_tiles, int* lanes_per_ray,
                           int* grid);
 
+/* Waits for the plan's last host-side run if it is still in flight, then
+ * frees its graphs, device and pinned buffers.  NULL is ignored. */
 void synax_batch_plan_destroy(synax_batch_plan* plan);
 
 /* Parameter sets and parameter count of a plan. */

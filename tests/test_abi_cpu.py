@@ -272,3 +272,24 @@ def test_set_lanes_per_ray_validation(L):
 def test_wait_selftest_rejects_null(L):
     assert L.synax_wait_selftest(None, ctypes.c_void_p(16), None) == _native.SYNAX_EINVAL
     assert L.synax_wait_selftest(ctypes.c_void_p(16), None, None) == _native.SYNAX_EINVAL
+
+
+def test_every_entry_point_is_documented():
+    """Each function the header declares sits under a comment block (its
+    passage, arguments, layout, ownership and errors)."""
+    import re
+    lines = open(os.path.join(ROOT, "include", "synax.h")).read().split("\n")
+    decl = re.compile(r"^(?:int|void|size_t|int64_t|double|const char\*)\s+\**(synax_\w+)\s*\(")
+    undocumented = []
+    for i, line in enumerate(lines):
+        m = decl.match(line)
+        if not m:
+            continue
+        j = i - 1
+        # step over the other declarations of the same block and continuation lines
+        while j >= 0 and (decl.match(lines[j]) or lines[j].startswith("typedef")
+                          or (lines[j].startswith(" ") and not lines[j].lstrip().startswith(("*", "/*")))):
+            j -= 1
+        if j < 0 or not lines[j].rstrip().endswith("*/"):
+            undocumented.append(m.group(1))
+    assert not undocumented, undocumented
