@@ -128,3 +128,20 @@ def test_los_triad(oracle_lib):
             assert math.sin(t["b"]) == pytest.approx(z, abs=1e-14)
     t = oracle_lib.los(1, 4)   # equatorial pixel at phi = 0
     assert np.allclose(t["n"], [1, 0, 0], atol=1e-15)
+
+
+@pytest.mark.parametrize("nside", [1024, 8192])
+def test_roundtrip_large_nside(oracle_lib, nside):
+    """Up to Nside 8192 (the largest the library takes): sampled centres map
+    back to their own index under the independent inverse map, at both
+    poles, across both cap/belt boundaries, on the equator and at random."""
+    npix = 12 * nside * nside
+    ncap = 2 * nside * (nside - 1)
+    runs = [range(0, 200), range(ncap - 100, ncap + 100), range(npix // 2 - 100, npix // 2 + 100),
+            range(npix - ncap - 100, npix - ncap + 100), range(npix - 200, npix)]
+    rng = np.random.default_rng(nside)
+    pix = list(rng.integers(0, npix, 2000)) + [p for r in runs for p in r]
+    for p in pix:
+        z, phi = oracle_lib.healpix_centre(nside, int(p))
+        assert -1.0 < z < 1.0 and 0.0 <= phi < 2 * math.pi
+        assert ang2pix_ring(nside, z, phi) == p
