@@ -887,13 +887,15 @@ def run_synax(args):
         "gpu_launches": 2 * args.steps,
         "lanes_per_ray": {str(k): v for k, v in lanes_table.items()},
     }
-    if rank == 0 and not args.no_batch:
+    # the further rows are one-GPU measurements: reported from single-process runs only
+    extras = rank == 0 and world == 1
+    if extras and not args.no_batch:
         out["batch"] = bench_batch(sx, inputs, torch, dev)
         chains = [p.replace(nside=16, n_steps=256) for p in inputs.config4()]
         out["batch_low_res"] = bench_batch(sx, inputs, torch, dev, n_runs=20, sets=chains,
                                            name="256 chains, Nside 16, 256 steps, chi^2 map+gradient")
         out["gpu_launches_batch_per_run"] = 2
-    if rank == 0 and not args.no_grid:
+    if extras and not args.no_grid:
         out["grid"] = bench_grid(sx, inputs, torch, dev)
         out["interp_study"] = interp_study(sx, inputs, torch)
         out["wmap_stack"] = bench_wmap_stack(sx, inputs, torch, dev)
@@ -920,7 +922,7 @@ def run_synax(args):
         h["roofline"] = march_roofline("wmap", 1, h["gradient_evals_per_s"] * h["samples_per_map"], clk_mhz,
                                        True, "k_batch<WMAP> per leapfrog step (momenta, leapfrog and "
                                              "Metropolis kernels included in the time)")
-    if rank == 0 and not args.no_surrogate:
+    if extras and not args.no_surrogate:
         peaks = {}
         try:
             with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -929,7 +931,7 @@ def run_synax(args):
             pass
         out["surrogate"] = bench_surrogate(sx, inputs, torch, dev, args.surrogate_steps, peaks, args.surrogate_maps)
         out["surrogate_sh"] = bench_surrogate_sh(sx, inputs, torch, dev, args.surrogate_steps, args.surrogate_maps)
-    if rank == 0 and not args.no_cpu_baseline:
+    if extras and not args.no_cpu_baseline:
         try:
             rate, dt, threads, desc = oracle_map_grad_rate(16384)   # ~10 s on 16 cores
             out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
