@@ -40,9 +40,6 @@ WORKLOAD = "JF12-type map+gradient, Nside 64, 512 steps, 4 freq, 16 params, chi^
 FWD_FP32_OPS = 200
 FWD_MUFU_OPS = 22
 ADJ_FACTOR = 3
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-MUFU_LANES_PER_SM = 16
 # The same count for every field model, without the Faraday phase: each
 # frequency adds 8 FP32 operations (phase, reduction to one turn, complex
 # accumulation) and 2 MUFU (sin, cos).  JF12-type: 168 + 14 (200 + 22 at four
@@ -50,8 +47,8 @@ MUFU_LANES_PER_SM = 16
 # sqrt, reciprocal, exponentials, log and two sincos of the field.  Stacked
 # (Eq. 16): 99 + 25, four sincos pairs.  Grid: 142 + 9, the trilinear
 # blend and cell location in place of the field model; its adjoint adds 36
-# FP32 of node weights and sums per sample.  FP32 runs on 128 lanes per SM and
-# MUFU on 16, so the WMAP-type and stacked models are bound by the MUFU count.
+# FP32 of node weights and sums per sample.  The pipe whose share of the
+# measured peaks (measure_peaks) is larger bounds each model.
 MODEL_OPS = {"jf12": (168, 14), "wmap": (60, 14), "wmap_stack": (99, 25), "grid": (142, 9)}
 GRID_ADJ_EXTRA_FP32 = 36
 # DRAM bytes (read + write) of one k_adjoint launch of this workload, from the
@@ -139,24 +136,46 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def march_roofline(model: str, n_freq: int, samples_per_s: float, clk_mhz: float, adjoint: bool,
+def measure_peaks(sx) -> dict:
+    """FP32 and SFU throughput measured on this GPU (synax_pipe_peak): the
+    FP32 peak is the faster of scalar FFMA and paired FFMA2 (element
+    operations), the MUFU peak the fastest of the six SFU instructions the
+    march uses, so that neither flatters a kernel's fraction."""
+    r = sx.pipe_peaks(iters=16384)
+    mufu = {k: r[k] / 1e12 for k in ("ex2", "lg2", "sin", "cos", "rcp", "rsqrt")}
+    return {"fp32_top": max(r["ffma"], r["ffma2"]) / 1e12, "mufu_top": max(mufu.values()),
+            "unit": "T element op/s", "ffma": r["ffma"] / 1e12, "ffma2": r["ffma2"] / 1e12, "mufu": mufu,
+            "sms": r["sms"]}
+
+
+def roofline_alu(fp32_ops: float, mufu_ops: float, t_s: float, peaks: dict, kernel: str) -> dict:
+    """Roofline of a march kernel from its algorithmic FP32 and MUFU
+    operations over a measured duration t_s: the pipe whose share of its
+    measured peak is larger bounds it."""
+    fp32_ach = fp32_ops / t_s / 1e12
+    mufu_ach = mufu_ops / t_s / 1e12
+    on_fp32 = fp32_ach / peaks["fp32_top"] >= mufu_ach / peaks["mufu_top"]
+    pipe, ach, peak = ("FP32", fp32_ach, peaks["fp32_top"]) if on_fp32 else ("MUFU", mufu_ach, peaks["mufu_top"])
+    other = mufu_ach / peaks["mufu_top"] if on_fp32 else fp32_ach / peaks["fp32_top"]
+    return {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": f"T {pipe} op/s",
+            "frac": ach / peak, "frac_other_pipe": other, "kernel": kernel,
+            "peak_basis": f"measured {pipe} peak of this GPU (synax_pipe_peak, peaks_measured; "
+                          f"{'max of FFMA, FFMA2' if pipe == 'FP32' else 'fastest SFU instruction'})"}
+
+
+def march_roofline(model: str, n_freq: int, samples_per_s: float, peaks: dict, adjoint: bool,
                    kernel: str) -> dict:
     """Roofline of a march kernel from the per-sample operation counts of
-    MODEL_OPS: the pipe (FP32 or MUFU) that the count keeps busier bounds it."""
+    MODEL_OPS against the measured pipe peaks."""
     fp32, mufu = MODEL_OPS[model]
     fp32 += 8 * n_freq
     mufu += 2 * n_freq
     if adjoint:
         fp32 = ADJ_FACTOR * fp32 + (GRID_ADJ_EXTRA_FP32 if model == "grid" else 0)
         mufu = ADJ_FACTOR * mufu
-    on_fp32 = fp32 / FP32_LANES_PER_SM >= mufu / MUFU_LANES_PER_SM
-    ops, lanes, pipe = (fp32, FP32_LANES_PER_SM, "FP32") if on_fp32 else (mufu, MUFU_LANES_PER_SM, "MUFU")
-    peak = SM_COUNT * lanes * clk_mhz * 1e6 / 1e12
-    achieved = samples_per_s * ops / 1e12
-    return {"bound": "alu", "pipe": pipe, "achieved": achieved, "peak": peak, "unit": f"T {pipe} op/s",
-            "frac": achieved / peak, "kernel": kernel, "ops_per_sample": {"fp32": fp32, "mufu": mufu},
-            "peak_basis": f"{SM_COUNT} SMs x {lanes} {pipe} lanes x {clk_mhz:.0f} MHz (median SM clock of "
-                          "the main timed region)"}
+    out = roofline_alu(samples_per_s * fp32, samples_per_s * mufu, 1.0, peaks, kernel)
+    out["ops_per_sample"] = {"fp32": fp32, "mufu": mufu}
+    return out
 
 
 def oracle_row(prob, n_pix_sample: int, free, note: str = "") -> dict:
@@ -214,9 +233,11 @@ def dist_env():
 # ---------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline): FD gradient on a pixel sample
 # ---------------------------------------------------------------------------
-def oracle_map_grad_rate(n_pix_sample: int, n_repeat: int = 1) -> tuple[float, float, int, str]:
+def oracle_map_grad_rate(n_pix_sample: int, n_repeat: int = 1, threads: int | None = None
+                         ) -> tuple[float, float, int, str]:
     """samples/s of map + gradient with the FP64 oracle: per map+grad, one
-    forward and 2 * 16 central-difference maps, on n_pix_sample pixels."""
+    forward and 2 * 16 central-difference maps, on n_pix_sample pixels, on
+    `threads` host threads (default: every core)."""
     import numpy as np
 
     import oracle
@@ -224,8 +245,8 @@ def oracle_map_grad_rate(n_pix_sample: int, n_repeat: int = 1) -> tuple[float, f
     oracle.build()
     prob, _, _ = inputs.config3()
     pix = inputs.sample_pixels(prob.npix, n_pix_sample, seed=41)
-    threads = oracle.default_threads()
     h = 1e-4 * inputs.jf12_scales(prob.theta)
+    threads = threads or oracle.default_threads()
     t0 = time.perf_counter()
     for _ in range(n_repeat):
         oracle.forward(prob, pix=pix, threads=threads)
@@ -239,6 +260,20 @@ def oracle_map_grad_rate(n_pix_sample: int, n_repeat: int = 1) -> tuple[float, f
     sample_desc = (f"{pix.size} of {prob.npix} pixels x {prob.n_steps} steps x 4 freq, "
                    f"map + 32-map central-difference gradient, {n_repeat} evaluation(s)")
     return samples / dt, dt, threads, sample_desc
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo), or the platform string."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -766,6 +801,7 @@ def run_synax(args):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
+    peaks = measure_peaks(sx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     barrier()
@@ -835,6 +871,22 @@ def run_synax(args):
     barrier()
     e2e_ms = [e_start.elapsed_time(e_end) / args.steps]
 
+    # the same call as a per-call latency: one stream, each step's copies,
+    # kernels and read-back in sequence (no overlap between steps)
+    b = bufs[0]
+    lat = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        b["flush"].fill_(float(k))
+        lat[k][0].record(stream)
+        b["d_target"].copy_(h_target, non_blocking=True)
+        g1, c1 = sx.adjoint(prob, target=b["d_target"], sigma=sigma, maps_out=b["maps"], workspace=b["ws"])
+        b["h_maps"].copy_(b["maps"], non_blocking=True)
+        b["h_grad"].copy_(g1, non_blocking=True)
+        b["h_chi2"].copy_(c1, non_blocking=True)
+        lat[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_lat_ms = float(np.median([a.elapsed_time(z) for a, z in lat]))
+
     ms = float(np.mean(step_ms))
     ms_e2e = float(np.mean(e2e_ms))
     ms_fwd = float(np.mean(fwd_ms))
@@ -843,28 +895,14 @@ def run_synax(args):
     value = whole_job_rate(world, samples, ms)
 
     # roofline of the dominant kernel (the adjoint march): algorithmic FP32 and
-    # MUFU work per launch over the launch's measured duration
-    clk_mhz = clk["sm_mhz"] or 2070.0
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12          # T op/s
-    mufu_peak = SM_COUNT * MUFU_LANES_PER_SM * clk_mhz * 1e6 / 1e12
+    # MUFU work per launch over the launch's measured duration, against the
+    # pipe peaks measured on this GPU inside the same clock-sampled region
     adj_fp32 = ADJ_FACTOR * FWD_FP32_OPS * samples
     adj_mufu = ADJ_FACTOR * FWD_MUFU_OPS * samples
-    t_s = ms * 1e-3
-    fp32_ach = adj_fp32 / t_s / 1e12
-    mufu_ach = adj_mufu / t_s / 1e12
-    bound_is_fp32 = adj_fp32 / fp32_peak >= adj_mufu / mufu_peak
-    roof = {
-        "bound": "alu",
-        "achieved": fp32_ach if bound_is_fp32 else mufu_ach,
-        "peak": fp32_peak if bound_is_fp32 else mufu_peak,
-        "unit": "T FP32 op/s" if bound_is_fp32 else "T MUFU op/s",
-        "frac": (fp32_ach / fp32_peak) if bound_is_fp32 else (mufu_ach / mufu_peak),
-        "traffic": ADJ_DRAM_BYTES,
-        "kernel": "k_adjoint (+ k_reduce_partials)",
-        "ops_per_sample": {"fp32": ADJ_FACTOR * FWD_FP32_OPS, "mufu": ADJ_FACTOR * FWD_MUFU_OPS},
-        "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x median SM clock "
-                      f"{clk_mhz:.0f} MHz (no measured FP32 peak in the peaks file)",
-    }
+    roof = roofline_alu(adj_fp32, adj_mufu, ms * 1e-3, peaks, "k_adjoint (+ k_reduce_partials)")
+    roof["traffic"] = ADJ_DRAM_BYTES
+    roof["ops_per_sample"] = {"fp32": ADJ_FACTOR * FWD_FP32_OPS, "mufu": ADJ_FACTOR * FWD_MUFU_OPS}
+    fwd_roof = roofline_alu(FWD_FP32_OPS * samples, FWD_MUFU_OPS * samples, ms_fwd * 1e-3, peaks, "k_forward")
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
@@ -877,13 +915,18 @@ def run_synax(args):
         "forward_samples_per_s": whole_job_rate(world, samples, ms_fwd),
         "forward_ms": ms_fwd,
         "roofline": roof,
+        "forward_roofline": fwd_roof,
+        "peaks_measured": dict(peaks, sm_mhz=clk["sm_mhz"]),
         "clocks": clk,
         "e2e": {"value": whole_job_rate(world, samples, ms_e2e), "unit": "samples/s",
                 "h2d_bytes_per_step": int(target.numel() * 4),
                 "d2h_bytes_per_step": int(maps.numel() * 4 + 16 * 8 + 8),
                 "ms_per_step": ms_e2e,
                 "schedule": "two streams alternating steps (copies of one step overlap the other's kernels); "
-                            "a 256 MiB L2 flush per step inside the timed region"},
+                            "a 256 MiB L2 flush per step inside the timed region",
+                "latency_ms_single_stream": e2e_lat_ms,
+                "latency_note": "median per-call time on one stream: H2D target, synax_adjoint, D2H maps, "
+                                "gradient and chi^2, no overlap between calls"},
         "gpu_launches": 2 * args.steps,
         "lanes_per_ray": {str(k): v for k, v in lanes_table.items()},
     }
@@ -903,23 +946,23 @@ def run_synax(args):
     # every row against its kernel's roofline (same clock as the main line)
     for key in ("batch", "batch_low_res"):
         if key in out:
-            out[key]["roofline"] = march_roofline("jf12", 4, out[key]["samples_per_s"], clk_mhz, True,
+            out[key]["roofline"] = march_roofline("jf12", 4, out[key]["samples_per_s"], peaks, True,
                                                   "k_batch (+ k_batch_reduce)")
     if "grid" in out:
         g = out["grid"]
-        g["roofline"] = march_roofline("grid", 1, g["samples_per_s"], clk_mhz, True,
+        g["roofline"] = march_roofline("grid", 1, g["samples_per_s"], peaks, True,
                                        "k_adjoint<GRID> (+ k_reduce_partials, k_grid_unpad)")
-        g["forward_roofline"] = march_roofline("grid", 1, g["forward_samples_per_s"], clk_mhz, False,
+        g["forward_roofline"] = march_roofline("grid", 1, g["forward_samples_per_s"], peaks, False,
                                                "k_forward<GRID>")
     if "wmap_stack" in out:
         w = out["wmap_stack"]
-        w["roofline"] = march_roofline("wmap_stack", 1, w["samples_per_s"], clk_mhz, True,
+        w["roofline"] = march_roofline("wmap_stack", 1, w["samples_per_s"], peaks, True,
                                        "k_adjoint<WMAP_STACK> (+ k_reduce_partials)")
-        w["forward_roofline"] = march_roofline("wmap_stack", 1, w["forward_samples_per_s"], clk_mhz, False,
+        w["forward_roofline"] = march_roofline("wmap_stack", 1, w["forward_samples_per_s"], peaks, False,
                                                "k_forward<WMAP_STACK>")
     if "hmc" in out:
         h = out["hmc"]
-        h["roofline"] = march_roofline("wmap", 1, h["gradient_evals_per_s"] * h["samples_per_map"], clk_mhz,
+        h["roofline"] = march_roofline("wmap", 1, h["gradient_evals_per_s"] * h["samples_per_map"], peaks,
                                        True, "k_batch<WMAP> per leapfrog step (momenta, leapfrog and "
                                              "Metropolis kernels included in the time)")
     if extras and not args.no_surrogate:
@@ -934,8 +977,11 @@ def run_synax(args):
     if extras and not args.no_cpu_baseline:
         try:
             rate, dt, threads, desc = oracle_map_grad_rate(16384)   # ~10 s on 16 cores
+            rate1, dt1, _, desc1 = oracle_map_grad_rate(1024, threads=1)   # ~10 s on one core
             out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads,
-                                   "kind": "oracle", "sample": desc, "seconds": dt}
+                                   "kind": "oracle", "sample": desc, "seconds": dt,
+                                   "value_1thread": rate1, "sample_1thread": desc1, "seconds_1thread": dt1,
+                                   "nproc": os.cpu_count(), "cpu_model": cpu_model()}
         except Exception as exc:  # the oracle is a baseline; report why it is absent
             out["cpu_baseline"] = {"value": None, "unit": "samples/s", "cores": os.cpu_count(),
                                    "kind": "oracle", "sample": f"failed: {exc}"}

@@ -48,6 +48,7 @@ extern "C" {
 #define SYNAX_ETIMEOUT    -5   /* a bounded device-side wait gave up */
 #define SYNAX_ENOTSUP     -6   /* combination not supported (e.g. model without adjoint) */
 #define SYNAX_ESPACE      -7   /* caller-provided workspace too small */
+#define SYNAX_EBOUNDS     -8   /* a device-side index check of SYNAX_CHECKED mode failed */
 
 /* ---- field models (layout of theta) ----
  * SYNAX_MODEL_TOY  (Sec. 2.4) theta = [Bx, By, Bz (uG), n_e (cm^-3), N0 (cm^-3), p, R0 (kpc)]:
@@ -84,6 +85,12 @@ extern "C" {
 /* ---- problem flags ---- */
 #define SYNAX_F64       (1u << 0)  /* march in FP64; maps (and gmaps/targets) are double */
 #define SYNAX_BOX_CLIP  (1u << 1)  /* ray ends at the box boundary (Sec. 2.3), else at r_max */
+#define SYNAX_CHECKED   (1u << 2)  /* bounds-checked kernels: every index a kernel is about to
+                                      use is tested against its buffer's extent; a failure
+                                      skips the access and records SYNAX_EBOUNDS in the
+                                      device status word (synax_last_status) instead of
+                                      faulting.  Results of a run without failures are
+                                      identical to an unchecked run. */
 
 /* One map to march: the paper's problem statement (Sec. 2.3). */
 typedef struct synax_problem {
@@ -187,6 +194,11 @@ int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_p
 int synax_batch_run(synax_batch_plan* plan, const double* thetas, const void* const* seeds_dev, int vjp,
                     double sigma_K, void* const* maps_dev, double* grads_dev, double* chi2_dev,
                     void* stream);
+/* The same call under the name of the batched entry point of the hot-path
+ * interface (synax_forward, synax_adjoint, synax_batch, synax_surrogate);
+ * arguments, results and errors are synax_batch_run's. */
+int synax_batch(synax_batch_plan* plan, const double* thetas, const void* const* seeds_dev, int vjp,
+                double sigma_K, void* const* maps_dev, double* grads_dev, double* chi2_dev, void* stream);
 
 /* Per-set completion time of the last run, ms after its first tile started
  * (device global timer); waits for the run.  ms_out: host [n_sets]. */
@@ -289,7 +301,9 @@ int synax_gemm_bf16(const void* a_dev, int lda, const void* b_dev, int ldb, int 
  * address (cudaGetSymbolAddress) with that device current; make it before
  * any stream capture.  Every call shares the array and it keeps the last
  * call's contents (nothing needs clearing: each call writes what it reads),
- * so calls that overlap on the GPU race and must be serialised by the caller. */
+ * so calls that overlap on the GPU race and must be serialised by the caller.
+ * The per-device address cache covers device indices 0..63; on a device
+ * with a higher index the call returns SYNAX_ENOTSUP. */
 int synax_adjoint_noalloc(const synax_problem* prob, const void* gmaps_dev, const void* target_dev,
                           double sigma_K, double* grad_dev, double* chi2_dev, void* maps_dev,
                           void* stream);
@@ -493,6 +507,58 @@ int synax_surrogate_load(synax_surrogate_t* s, const char* path);
  * the choice beyond rounding; the autotuner (paper_2410_01136_gb300/tune.py)
  * measures the candidates and installs the fastest.  Process-wide setting. */
 int synax_set_lanes_per_ray(int n_steps_min, int lanes);
+
+/* ---- device status word (no counterpart in the paper) ----
+ * Every device that loads the library holds one status word, which records
+ * the first device-side error since it was last read: SYNAX_EBOUNDS from a
+ * kernel launched with SYNAX_CHECKED (the site and index of the failed
+ * check are kept), or SYNAX_ETIMEOUT from a bounded wait of a tensor-core
+ * kernel that gave up.  Later errors leave it unchanged until it is read.
+ *
+ * synax_last_status: synchronises `stream`, then reads and clears the word
+ * of the current device.  Returns SYNAX_OK when no error was recorded, the
+ * recorded code otherwise, or SYNAX_ECUDA if the synchronisation or the
+ * read fails (a CUDA error in the stream's work surfaces here).
+ * synax_last_status_detail: the site (SYNAX_SITE_*) and the offending index
+ * of the error that this thread's last synax_last_status call returned
+ * (0, 0 after a call that returned SYNAX_OK).  Either pointer may be NULL.
+ * synax_checked_selftest: runs the bounds predicate of SYNAX_CHECKED mode
+ * on the host against indexes on either side of an extent; SYNAX_OK when
+ * each is classified correctly.  Needs no GPU. */
+#define SYNAX_SITE_MAP_STORE     1   /* a map element store (forward, adjoint, batch) */
+#define SYNAX_SITE_SEED_LOAD     2   /* a chi^2 target or VJP seed load */
+#define SYNAX_SITE_PARTIAL       3   /* a per-CTA (or per-tile) partial-gradient row */
+#define SYNAX_SITE_GRID_LOAD     4   /* the 8 nodes of a grid cell read by the march */
+#define SYNAX_SITE_GRID_SCATTER  5   /* the 8 nodes of a grid cell in the grid gradient */
+#define SYNAX_SITE_BATCH_SET     6   /* a parameter-set index of the persistent batch */
+#define SYNAX_SITE_GEMM_WAIT     7   /* a bounded mbarrier wait of a tensor-core kernel */
+int synax_last_status(void* stream);
+int synax_last_status_detail(int* site, long long* index);
+int synax_checked_selftest(void);
+
+#define SYNAX_PIPE_FFMA  0
+#define SYNAX_PIPE_FFMA2 1
+#define SYNAX_PIPE_EX2   2
+#define SYNAX_PIPE_LG2   3
+#define SYNAX_PIPE_SIN   4
+#define SYNAX_PIPE_COS   5
+#define SYNAX_PIPE_RCP   6
+#define SYNAX_PIPE_RSQRT 7
+/* ---- pipe-throughput microbenchmarks (no counterpart in the paper) ----
+ * The march is bound by the FP32 pipe and the SFU, not by memory, so its
+ * roofline needs their throughput on the GPU at hand.  synax_pipe_peak
+ * enqueues one kernel of `blocks` CTAs of 256 threads; every thread runs 8
+ * independent dependency chains of `iters` operations of one kind:
+ *   SYNAX_PIPE_FFMA  fmaf (one FP32 FMA per instruction)
+ *   SYNAX_PIPE_FFMA2 __ffma2_rn (two FP32 FMAs per paired instruction)
+ *   SYNAX_PIPE_EX2, _LG2, _SIN, _COS, _RCP, _RSQRT: the PTX
+ *       ex2/lg2/sin/cos/rcp/rsqrt.approx.ftz.f32 instructions (each chain
+ *       step may add one FP32 multiply or add to keep values bounded).
+ * *ops_out receives the element operations of the launch (an FFMA2 counts
+ * two); the caller times the launch on `stream` and divides.  sink_dev:
+ * device float[blocks * 256], overwritten (keeps the chains live).
+ * SYNAX_EINVAL for blocks < 1, iters < 1, a NULL pointer or an unknown pipe. */
+int synax_pipe_peak(int pipe, int blocks, int iters, float* sink_dev, long long* ops_out, void* stream);
 
 /* Last CUDA error code seen by this thread in a call that returned SYNAX_ECUDA. */
 int synax_last_cuda_error(void);

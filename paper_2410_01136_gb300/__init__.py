@@ -19,7 +19,7 @@ from . import _native
 from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
 
 __all__ = ["forward", "adjoint", "adjoint_grid", "adjoint_grid_workspace_bytes", "grid_sample", "adam_step", "GridFit", "HMC", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
-           "SynaxError"]
+           "SynaxError", "last_status", "pipe_peaks", "set_lanes_per_ray"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -318,11 +318,11 @@ class BatchPlan:
         map_arr = None
         if maps is not None:
             map_arr = (ctypes.c_void_p * self._n)(*[(t.data_ptr() if t is not None else None) for t in maps])
-        check(lib().synax_batch_run(self._h, th_ptr, seed_arr, 0 if targets is not None else 1,
-                                    ctypes.c_double(float(sigma)), map_arr,
-                                    ctypes.c_void_p(grads.data_ptr()),
-                                    ctypes.c_void_p(chi2.data_ptr() if chi2 is not None else 0),
-                                    _stream_handle(torch, stream)), "synax_batch_run")
+        check(lib().synax_batch(self._h, th_ptr, seed_arr, 0 if targets is not None else 1,
+                                ctypes.c_double(float(sigma)), map_arr,
+                                ctypes.c_void_p(grads.data_ptr()),
+                                ctypes.c_void_p(chi2.data_ptr() if chi2 is not None else 0),
+                                _stream_handle(torch, stream)), "synax_batch")
         return grads, chi2
 
     def bind(self, targets=None, seeds=None, sigma: float = 1.0, maps=None, grads=None, chi2=None):
@@ -386,6 +386,53 @@ def set_lanes_per_ray(lanes: int, n_steps_min: int = -1) -> None:
     """Launch tuning: 8, 16 or 32 lanes per ray (0 = built-in rule), for every
     map (n_steps_min < 0) or for the step-count bin containing n_steps_min."""
     check(lib().synax_set_lanes_per_ray(int(n_steps_min), int(lanes)), "synax_set_lanes_per_ray")
+
+
+def last_status(stream=None) -> tuple[int, int, int]:
+    """(code, site, index) of the first device-side error recorded since the
+    last read (synax_last_status, which synchronises the stream and clears
+    the word): code 0 when none, SYNAX_EBOUNDS from a SYNAX_CHECKED launch,
+    SYNAX_ETIMEOUT from a bounded wait that gave up."""
+    torch = _torch()
+    code = lib().synax_last_status(_stream_handle(torch, stream))
+    if code == _native.SYNAX_ECUDA:
+        check(code, "synax_last_status")
+    site, index = ctypes.c_int(0), ctypes.c_longlong(0)
+    lib().synax_last_status_detail(ctypes.byref(site), ctypes.byref(index))
+    return code, site.value, index.value
+
+
+def pipe_peaks(pipes=("ffma", "ffma2", "ex2", "lg2", "sin", "cos", "rcp", "rsqrt"), blocks_per_sm: int = 8,
+               iters: int = 4096, repeats: int = 5) -> dict:
+    """Measured throughput of the FP32 pipe and the SFU on the current device
+    (synax_pipe_peak): per pipe the best of `repeats` launches, in element
+    operations per second, from CUDA events on the launching stream.  A grid
+    of blocks_per_sm 256-thread CTAs per SM keeps every SM's pipes full."""
+    torch = _torch()
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = blocks_per_sm * sms
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = _stream_handle(torch, stream)
+    ops = ctypes.c_longlong(0)
+    out = {}
+    for name in pipes:
+        code = _native.PIPES[name]
+        check(lib().synax_pipe_peak(code, blocks, 64, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops), h),
+              "synax_pipe_peak")                                   # warm-up
+        best = 0.0
+        for _ in range(repeats):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            check(lib().synax_pipe_peak(code, blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops),
+                                        h), "synax_pipe_peak")
+            b.record(stream)
+            b.synchronize()
+            best = max(best, ops.value / (a.elapsed_time(b) * 1e-3))
+        out[name] = best
+    out["sms"] = sms
+    return out
 
 
 class SynaxMaps:

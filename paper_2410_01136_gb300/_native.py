@@ -22,9 +22,16 @@ SYNAX_ENOMEM = -4
 SYNAX_ETIMEOUT = -5
 SYNAX_ENOTSUP = -6
 SYNAX_ESPACE = -7
+SYNAX_EBOUNDS = -8
+
+SITE_MAP_STORE, SITE_SEED_LOAD, SITE_PARTIAL, SITE_GRID_LOAD, SITE_GRID_SCATTER, SITE_BATCH_SET, \
+    SITE_GEMM_WAIT = range(1, 8)
+
+PIPES = {"ffma": 0, "ffma2": 1, "ex2": 2, "lg2": 3, "sin": 4, "cos": 5, "rcp": 6, "rsqrt": 7}
 
 SYNAX_F64 = 1 << 0
 SYNAX_BOX_CLIP = 1 << 1
+SYNAX_CHECKED = 1 << 2
 
 MAX_FREQ = 16
 MAX_THETA = 32
@@ -158,6 +165,14 @@ SIGNATURES = {
     "synax_wait_selftest": (ctypes.c_int, [_VP, _VP, _VP]),
     "synax_surrogate_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "synax_surrogate_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "synax_pipe_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                       ctypes.POINTER(ctypes.c_longlong), _VP]),
+    "synax_last_status": (ctypes.c_int, [_VP]),
+    "synax_last_status_detail": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
+    "synax_checked_selftest": (ctypes.c_int, []),
+    "synax_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
     "synax_last_cuda_error": (ctypes.c_int, []),
     "synax_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "synax_version": (ctypes.c_int, []),
@@ -222,7 +237,8 @@ def problem_struct(prob) -> SynaxProblem:
     for k, x in enumerate(th):
         s.theta[k] = x
     s.flags = (SYNAX_F64 if getattr(prob, "f64", False) else 0) | (
-        SYNAX_BOX_CLIP if getattr(prob, "box_clip", False) else 0)
+        SYNAX_BOX_CLIP if getattr(prob, "box_clip", False) else 0) | (
+        SYNAX_CHECKED if getattr(prob, "checked", False) else 0)
     s.rm_rule = int(getattr(prob, "rm_rule", 0))
     s.pix_begin = int(getattr(prob, "pix_begin", 0))
     s.pix_count = int(getattr(prob, "pix_count", 0))

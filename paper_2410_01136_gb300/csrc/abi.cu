@@ -64,7 +64,7 @@ int validate_problem(const synax_problem* P, long long* n_pix) {
     if (!is_pow2(P->nside) || P->nside > 8192) return SYNAX_EINVAL;
     if (P->n_steps < 1 || P->n_steps > 65536) return SYNAX_EINVAL;
     if (P->n_freq < 1 || P->n_freq > SYNAX_MAX_FREQ) return SYNAX_EINVAL;
-    if (P->flags & ~(SYNAX_F64 | SYNAX_BOX_CLIP)) return SYNAX_EINVAL;
+    if (P->flags & ~(SYNAX_F64 | SYNAX_BOX_CLIP | SYNAX_CHECKED)) return SYNAX_EINVAL;
     if (P->rm_rule < 0 || P->rm_rule > 2) return SYNAX_EINVAL;
     const int nt = model_n_theta(P->model_id);
     if (nt < 0 || P->n_theta != nt) return SYNAX_EINVAL;
@@ -164,6 +164,8 @@ void fill_params(const synax_problem& P, long long n_pix, MapParams<R>& M) {
         }
         M.grid = (const R*)P.grid_dev;
     }
+    M.checked = (P.flags & SYNAX_CHECKED) ? 1 : 0;
+    M.status = device_status_word();
 }
 
 template <typename R>
@@ -195,10 +197,12 @@ int synax_forward(const synax_problem* prob, void* maps_dev, void* stream) {
     if (prob->flags & SYNAX_F64) {
         MapParams<double> M;
         fill_params<double>(*prob, n_pix, M);
+        if (M.checked && !M.status) return record_cuda_error((int)cudaErrorInvalidSymbol);
         return launch_forward_f64(M, maps_dev, stream);
     }
     MapParams<float> M;
     fill_params<float>(*prob, n_pix, M);
+    if (M.checked && !M.status) return record_cuda_error((int)cudaErrorInvalidSymbol);
     return launch_forward_f32(M, maps_dev, stream);
 }
 
@@ -240,6 +244,11 @@ static int adjoint_impl(const synax_problem* prob, const void* gmaps_dev, const 
     const size_t need = grid_grad_dev ? adjoint_grid_ws(prob, n_pix)
                                       : (n_pix > 0 ? adjoint_workspace_bytes(n_pix, prob->n_theta) : 0);
     if (workspace_bytes < need || (need > 0 && !workspace_dev)) return SYNAX_ESPACE;
+    // partial-gradient rows the workspace holds (the grid workspace keeps
+    // its node accumulator after the rows)
+    const size_t part_bytes = grid_grad_dev ? (n_pix > 0 ? adjoint_workspace_bytes(n_pix, prob->n_theta) : 0)
+                                            : workspace_bytes;
+    const long long part_rows = (long long)(part_bytes / (sizeof(double) * (size_t)(prob->n_theta + 1)));
     cudaStream_t st = (cudaStream_t)stream;
     const bool f64 = (prob->flags & SYNAX_F64) != 0;
     const size_t nodes = grid_grad_dev ? grid_nodes(prob) : 0;
@@ -269,6 +278,8 @@ static int adjoint_impl(const synax_problem* prob, const void* gmaps_dev, const 
         A.mode_chi2 = chi2_mode ? 1 : 0;
         A.inv_sigma2 = chi2_mode ? 1.0 / (sigma_K * sigma_K) : 0.0;
         A.grid_grad = (double*)grid_grad_dev;
+        A.n_part_rows = part_rows;
+        if (M.checked && !M.status) return record_cuda_error((int)cudaErrorInvalidSymbol);
         return launch_adjoint_f64(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
                                   maps_dev, workspace_dev, stream);
     }
@@ -279,6 +290,8 @@ static int adjoint_impl(const synax_problem* prob, const void* gmaps_dev, const 
     A.mode_chi2 = chi2_mode ? 1 : 0;
     A.inv_sigma2 = chi2_mode ? (float)(1.0 / (sigma_K * sigma_K)) : 0.0f;
     A.grid_acc = grid_acc;
+    A.n_part_rows = part_rows;
+    if (M.checked && !M.status) return record_cuda_error((int)cudaErrorInvalidSymbol);
     const int rc2 = launch_adjoint_f32(M, A, gmaps_dev, target_dev, grad_dev, chi2_mode ? chi2_dev : nullptr,
                                        maps_dev, workspace_dev, stream);
     if (rc2 != SYNAX_OK || !grid_acc) return rc2;
@@ -346,6 +359,7 @@ const char* synax_strerror(int status) {
     case SYNAX_ETIMEOUT: return "bounded device-side wait timed out";
     case SYNAX_ENOTSUP: return "operation not supported for this model";
     case SYNAX_ESPACE: return "workspace too small";
+    case SYNAX_EBOUNDS: return "device-side index check failed (SYNAX_CHECKED)";
     default: return "unknown status";
     }
 }

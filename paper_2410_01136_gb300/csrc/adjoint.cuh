@@ -158,6 +158,15 @@ struct GridAcc {
 
     __device__ __forceinline__ void flush(const MapParams<R>& P, typename GridGradPtr<R>::T* gg) {
         if (base < 0) return;
+        if (P.checked) {
+            // the cell's last node (i0 + 1, j0 + 1, k0 + 1) must be a node of the grid
+            const long long nodes = (long long)P.grid_n[0] * P.grid_n[1] * P.grid_n[2];
+            const long long last = (long long)base + 1 + P.grid_n[0] + (long long)P.grid_n[0] * P.grid_n[1];
+            if (!in_bounds(P, last, nodes, SYNAX_SITE_GRID_SCATTER) || !in_bounds(P, base, nodes, SYNAX_SITE_GRID_SCATTER)) {
+                base = -1;
+                return;
+            }
+        }
         if constexpr (sizeof(R) == 4) {
             const long long sy = P.grid_n[0], sz = sy * P.grid_n[1];
             float4* p = gg + base;
@@ -483,7 +492,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 }
                 const long long row = (long long)(3 * k) * P.n_pix + r_eff;
                 R gI, gQ, gU;
-                if (!live) {
+                if (!live || !in_bounds(P, row + 2 * P.n_pix, 3LL * P.n_freq * P.n_pix, SYNAX_SITE_SEED_LOAD)) {
                     gI = gQ = gU = R(0);
                 } else if (A.mode_chi2) {
                     const R dI = MI - target[row];
@@ -718,7 +727,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
         s_part[warp][NT] = (double)chi2_ray;
     }
     __syncthreads();
-    if (threadIdx.x <= NT) {
+    if (threadIdx.x <= NT && partial) {
         double acc = 0.0;
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) acc += s_part[w][threadIdx.x];
@@ -730,7 +739,9 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
             const int row = idx / RAYS;
             const int col = idx - row * RAYS;
             const long long r = ray0 + col;
-            if (r < P.n_pix) maps_out[(long long)row * P.n_pix + r] = s_stage[row][col];
+            const long long i = (long long)row * P.n_pix + r;
+            if (r < P.n_pix && in_bounds(P, i, 3LL * P.n_freq * P.n_pix, SYNAX_SITE_MAP_STORE))
+                maps_out[i] = s_stage[row][col];
         }
     }
     __syncthreads();
@@ -746,8 +757,10 @@ k_adjoint(const MapParams<R> P, const AdjParams<R> A, const R* __restrict__ gmap
           const R* __restrict__ target, R* __restrict__ maps_out, double* __restrict__ partial) {
     __shared__ AdjSmem<MODEL, NF, LPR, R> sm;
     constexpr int RAYS = kAdjThreads / LPR;
+    // (a CTA whose partial row lies beyond the workspace writes none)
+    const bool row_ok = in_bounds(P, (long long)blockIdx.x, A.n_part_rows, SYNAX_SITE_PARTIAL);
     adjoint_cta<MODEL, NF, LPR, R>(P, A, gmaps, target, maps_out,
-                                   partial + (long long)blockIdx.x * (Grad<MODEL>::NT + 1),
+                                   row_ok ? partial + (long long)blockIdx.x * (Grad<MODEL>::NT + 1) : nullptr,
                                    (long long)blockIdx.x * RAYS, sm);
 }
 

@@ -62,6 +62,8 @@ struct synax_batch_plan {
     cudaGraphExec_t exec_dev = nullptr;
     cudaEvent_t done = nullptr;
     bool pending = false;
+    int checked = 0;                  // SYNAX_CHECKED on any set: the kernel checks its set indexes
+    int* status = nullptr;            // the device status word
 };
 
 namespace {
@@ -124,7 +126,7 @@ int capture_graph_dev(synax_batch_plan* p, const double* theta) {
     int n_sets = p->n_sets;
     long long n_tiles = p->n_tiles;
     void* args[] = {&p->d_sets, &p->d_begin, &p->d_order, &n_sets, &n_tiles, &p->d_counter,
-                    &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0};
+                    &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0, &p->checked, &p->status};
     cudaLaunchKernel(p->kern.batch, dim3(p->grid), dim3(kAdjThreads), args, 0, p->cap);
     void* rargs[] = {&p->d_sets, &p->d_partial};
     cudaLaunchKernel(p->kern.reduce, dim3(p->n_sets), dim3(256), rargs, 0, p->cap);
@@ -146,7 +148,7 @@ int capture_graph(synax_batch_plan* p) {
     int n_sets = p->n_sets;
     long long n_tiles = p->n_tiles;
     void* args[] = {&p->d_sets, &p->d_begin, &p->d_order, &n_sets, &n_tiles, &p->d_counter,
-                    &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0};
+                    &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0, &p->checked, &p->status};
     cudaLaunchKernel(p->kern.batch, dim3(p->grid), dim3(kAdjThreads), args, 0, p->cap);
     void* rargs[] = {&p->d_sets, &p->d_partial};
     cudaLaunchKernel(p->kern.reduce, dim3(p->n_sets), dim3(256), rargs, 0, p->cap);
@@ -182,6 +184,10 @@ int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_p
     if (err != cudaSuccess) { plan_free(p); return record_cuda_error((int)err); }
     p->n_sets = n_sets;
     p->model = model;
+    for (int s = 0; s < n_sets; ++s)
+        if (sets[s].flags & SYNAX_CHECKED) p->checked = 1;
+    p->status = device_status_word();
+    if (p->checked && !p->status) { plan_free(p); return record_cuda_error((int)cudaErrorInvalidSymbol); }
     p->nf = nf_variant(sets[0].n_freq);
     p->probs.assign(sets, sets + n_sets);
     p->npix = npix;
@@ -300,6 +306,11 @@ int synax_batch_run(synax_batch_plan* p, const double* thetas, const void* const
     if (err != cudaSuccess) return record_cuda_error((int)err);
     p->pending = true;
     return SYNAX_OK;
+}
+
+int synax_batch(synax_batch_plan* p, const double* thetas, const void* const* seeds_dev, int vjp, double sigma_K,
+                void* const* maps_dev, double* grads_dev, double* chi2_dev, void* stream) {
+    return synax_batch_run(p, thetas, seeds_dev, vjp, sigma_K, maps_dev, grads_dev, chi2_dev, stream);
 }
 
 int synax_batch_latencies(synax_batch_plan* p, double* ms_out) {

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4)
 k_batch(const BatchSet* __restrict__ sets, const long long* __restrict__ order_begin,
         const int* __restrict__ order_set, int n_sets, long long n_tiles, unsigned long long* counter,
         double* __restrict__ partial, unsigned long long* set_done, unsigned long long* set_done_ns,
-        unsigned long long* t0) {
+        unsigned long long* t0, int checked, int* status) {
     constexpr int RAYS = kAdjThreads / LPR;
     constexpr int NT = Grad<MODEL>::NT;
     __shared__ AdjSmem<MODEL, NF, LPR, float> sm;
@@ -60,7 +60,13 @@ k_batch(const BatchSet* __restrict__ sets, const long long* __restrict__ order_b
                     if (order_begin[mid] <= t) lo = mid;
                     else hi = mid - 1;
                 }
-                s_set = order_set[lo];
+                int set = order_set[lo];
+                if (checked && !index_ok(set, n_sets)) {
+                    // a corrupt tile table: skip the tile (it contributes nothing)
+                    report_status(status, SYNAX_EBOUNDS, SYNAX_SITE_BATCH_SET, set);
+                    set = -1;
+                }
+                s_set = set;
                 s_ray0 = (t - order_begin[lo]) * RAYS;
                 if (t == 0) *t0 = global_ns();
             }
@@ -68,6 +74,10 @@ k_batch(const BatchSet* __restrict__ sets, const long long* __restrict__ order_b
         __syncthreads();
         const long long tile = s_tile;
         if (tile >= n_tiles) break;
+        if (s_set < 0) {
+            __syncthreads();
+            continue;
+        }
         const int* src = reinterpret_cast<const int*>(sets + s_set);
         int* dst = reinterpret_cast<int*>(s_raw);
         for (int i = threadIdx.x; i < (int)(sizeof(BatchSet) / 4); i += kAdjThreads) dst[i] = src[i];

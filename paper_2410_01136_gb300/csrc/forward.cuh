@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "march.cuh"
+#include "status.cuh"
 
 namespace synax {
 
@@ -112,7 +113,8 @@ k_forward(const MapParams<R> P, R* __restrict__ maps) {
         const int row = idx / RAYS;
         const int col = idx - row * RAYS;
         const long long r = ray0 + col;
-        if (r < P.n_pix) maps[(long long)row * P.n_pix + r] = s_stage[row][col];
+        const long long i = (long long)row * P.n_pix + r;
+        if (r < P.n_pix && in_bounds(P, i, 3LL * P.n_freq * P.n_pix, SYNAX_SITE_MAP_STORE)) maps[i] = s_stage[row][col];
     }
 }
 

@@ -40,6 +40,7 @@
 #include <mutex>
 
 #include "gemm.cuh"
+#include "status.cuh"
 #include "synax_internal.h"
 #include "tcgen05.cuh"
 
@@ -465,7 +466,10 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (threadIdx.x == 64 && stg > 0) tc::bulk_wait_all();   // every TMA store has completed
         if (lane == 0 && zblk > 0) tc::bulk_wait_all();            // this warp's pre-activation stores
     }
-    if (!ok) atomicExch(err, 1);
+    if (!ok) {
+        atomicExch(err, 1);
+        report_status(ep.status, SYNAX_ETIMEOUT, SYNAX_SITE_GEMM_WAIT, (long long)blockIdx.x);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if constexpr (EPI == EPI_MSE) {
@@ -487,7 +491,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 // mbar_wait_clock as the GEMM, on an mbarrier that nothing arrives at.  The
 // wait gives up after kWaitCycles; the CTA then sets *err, frees its TMEM and
 // returns.  *cycles receives the SM clocks the wait took.
-__global__ void __launch_bounds__(64, 1) k_wait_selftest(int* err, long long* cycles) {
+__global__ void __launch_bounds__(64, 1) k_wait_selftest(int* err, long long* cycles, int* status) {
     __shared__ alignas(8) uint64_t bar;
     __shared__ uint32_t tmem_slot;
     const int warp = threadIdx.x >> 5;
@@ -504,7 +508,10 @@ __global__ void __launch_bounds__(64, 1) k_wait_selftest(int* err, long long* cy
         const long long t0 = clock64();
         const bool ok = mbar_wait_clock(&bar, 0);
         *cycles = clock64() - t0;
-        if (!ok) atomicExch(err, 1);
+        if (!ok) {
+            atomicExch(err, 1);
+            report_status(status, SYNAX_ETIMEOUT, SYNAX_SITE_GEMM_WAIT, 0);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -604,6 +611,7 @@ int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, in
     const int tiles = ((N + BN - 1) / BN) * ((M + kGemmBM - 1) / kGemmBM);
     const int grid = tiles < sm_count() ? tiles : sm_count();
     GemmEpiParams ep = ep_in;
+    ep.status = device_status_word();
     CUtensorMap mc;
     std::memset(&mc, 0, sizeof mc);
     ep.tma_store = 0;
@@ -702,7 +710,7 @@ extern "C" int synax_gemm_bf16(const void* a_dev, int lda, const void* b_dev, in
 
 extern "C" int synax_wait_selftest(int* err_dev, long long* cycles_dev, void* stream) {
     if (!err_dev || !cycles_dev) return SYNAX_EINVAL;
-    k_wait_selftest<<<1, 64, 0, (cudaStream_t)stream>>>(err_dev, cycles_dev);
+    k_wait_selftest<<<1, 64, 0, (cudaStream_t)stream>>>(err_dev, cycles_dev, device_status_word());
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
 }

@@ -41,6 +41,7 @@ struct GemmEpiParams {
     const float* shift;          // EPI_AFFINE
     int accumulate;              // EPI_SCALE_ACC
     int tma_store;               // set by gemm_bf16: FP32 output written through TMA stores
+    int* status;                 // set by gemm_bf16: the device status word (a timed-out wait reports there)
 };
 
 // Set the kernels' shared-memory attributes (once per process; gemm_bf16

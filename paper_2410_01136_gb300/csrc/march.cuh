@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "ffmath.cuh"
+#include "status.cuh"
 #include "synax_internal.h"
 
 namespace synax {
@@ -1028,6 +1029,20 @@ __device__ __forceinline__ int grid_locate_ray(const MapParams<R>& P, const Grid
 
 template <typename R>
 __device__ __forceinline__ void grid_load(const MapParams<R>& P, int base, GridCell<R>& gc) {
+    if (P.checked) {
+        // the cell's first and last nodes must be nodes of the grid; otherwise
+        // the cell is cached as a zero field and nothing is read
+        const long long nodes = (long long)P.grid_n[0] * P.grid_n[1] * P.grid_n[2];
+        const long long last = (long long)base + 1 + P.grid_n[0] + (long long)P.grid_n[0] * P.grid_n[1];
+        if (!in_bounds(P, (long long)base, nodes, SYNAX_SITE_GRID_LOAD) ||
+            !in_bounds(P, last, nodes, SYNAX_SITE_GRID_LOAD)) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                gc.a[c] = gc.b[c] = gc.c[c] = gc.d[c] = gc.e[c] = gc.f[c] = gc.g[c] = gc.h[c] = R(0);
+            gc.base = base;
+            return;
+        }
+    }
     const long long sy = 3LL * P.grid_n[0], sz = sy * P.grid_n[1];
     const R* p = P.grid + 3LL * base;
 #pragma unroll

@@ -74,6 +74,8 @@ struct MapParams {
     R m[kModelConsts];
     const R* grid;            // grid model: B nodes [nz][ny][nx][3] (uG), else null
     int grid_n[3];            // (nx, ny, nz)
+    int checked;              // SYNAX_CHECKED: index checks report instead of faulting
+    int* status;              // the device status word (status.cu)
 };
 
 // Gradient-side constants (adjoint): d ln aI / dp and d ln aP / dp per
@@ -87,6 +89,7 @@ struct AdjParams {
     R inv_sigma2;
     R* grid_grad;             // grid model, FP64: gradient of every node value (zeroed by the host), or null
     float4* grid_acc;         // grid model, FP32: the same as [nodes] float4 (x, y, z, unused), zeroed
+    long long n_part_rows;    // partial-gradient rows the workspace holds (SYNAX_CHECKED)
 };
 
 // Host-side problem handling (abi.cu).
@@ -121,5 +124,9 @@ int launch_eval_fields_f64(const MapParams<double>& P, const double* pos, const 
 
 // Records a CUDA error for synax_last_cuda_error() and returns SYNAX_ECUDA.
 int record_cuda_error(int err);
+
+// Device address of the current device's status word (status.cu), or null
+// if it cannot be resolved.
+int* device_status_word();
 
 }  // namespace synax

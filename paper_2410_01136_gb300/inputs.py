@@ -104,7 +104,8 @@ class Problem:
     2 all of it (a plain cumulative sum).  grid: the grid model's B nodes,
     [nz][ny][nx][3] in uG, spanning box_kpc wall to wall (grid model only):
     a host array (kept as a read-only float64 copy) or a device tensor of the
-    march precision, used in place.
+    march precision, used in place.  checked: launch the bounds-checked
+    kernels (SYNAX_CHECKED; read the outcome with last_status()).
     """
 
     nside: int
@@ -121,6 +122,7 @@ class Problem:
     pix_count: int = 0
     rm_rule: int = 0
     grid: np.ndarray | None = None
+    checked: bool = False
 
     def __post_init__(self):
         self.theta = np.asarray(self.theta, dtype=np.float64).copy()

@@ -293,3 +293,26 @@ def test_every_entry_point_is_documented():
         if j < 0 or not lines[j].rstrip().endswith("*/"):
             undocumented.append(m.group(1))
     assert not undocumented, undocumented
+
+
+def test_checked_mode_host_side(L):
+    """SYNAX_CHECKED: the bounds predicate the kernels use classifies indexes
+    on both sides of an extent correctly (run on the host), and the flag
+    passes host validation while an unknown flag bit does not."""
+    assert L.synax_checked_selftest() == _native.SYNAX_OK
+    prob = inputs.config2().replace(nside=4, n_steps=16, checked=True)
+    s = _native.problem_struct(prob)
+    assert s.flags & _native.SYNAX_CHECKED
+    n = ctypes.c_size_t(0)
+    assert L.synax_adjoint_workspace_bytes(ctypes.byref(s), ctypes.byref(n)) == _native.SYNAX_OK
+    s.flags |= 1 << 3
+    assert L.synax_adjoint_workspace_bytes(ctypes.byref(s), ctypes.byref(n)) == _native.SYNAX_EINVAL
+    assert L.synax_strerror(_native.SYNAX_EBOUNDS).decode().startswith("device-side index check")
+
+
+def test_last_status_detail_without_a_read(L):
+    """Before any synax_last_status call on this thread the detail is zero."""
+    site, index = ctypes.c_int(-1), ctypes.c_longlong(-1)
+    assert L.synax_last_status_detail(ctypes.byref(site), ctypes.byref(index)) == _native.SYNAX_OK
+    assert (site.value, index.value) == (0, 0)
+    assert L.synax_last_status_detail(None, None) == _native.SYNAX_OK

@@ -1,9 +1,14 @@
-"""The persistent, graph-captured batch (synax_batch_*) against one-map
-synax_adjoint calls on the same sets, and chi^2 against the FP64 oracle.
+"""The persistent, graph-captured batch (synax_batch_*) against the FP64
+oracle and against one-map synax_adjoint calls on the same sets.
 
-The batch runs the same per-CTA adjoint code, inlined into another kernel and
-with one lanes-per-ray width for the whole ensemble, so per-ray FP32 rounding
-may differ from the one-map call: gradients are compared at FP32 precision
+Against the oracle: every set's chi^2 gradient (Eq. 15) and VJP gradient
+against Richardson-extrapolated central differences of the oracle (h and h/2,
+h_i = 1e-4 s_i), per component |g - g_FD| <= 1e-3 |g_FD| + 1e-4 max |g_FD|,
+the adjoint tests' tolerance; maps to the stated I and Q/U tolerances.
+
+Against the one-map call: the batch runs the same per-CTA adjoint code,
+inlined into another kernel and with its own lanes-per-ray width per set, so
+per-ray FP32 rounding may differ: gradients are compared at FP32 precision
 (1e-5 relative, 1e-6 of the largest component), bitwise only between replays."""
 import numpy as np
 import pytest
@@ -11,7 +16,7 @@ import pytest
 import oracle
 from paper_2410_01136_gb300 import BatchPlan, adjoint, forward, inputs
 
-from .parity import assert_parity
+from .parity import assert_parity, assert_parity_coarse
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +45,76 @@ def targets_for(torch, sets, seed=3):
         t = oracle.forward(p.with_theta(th)) + inputs.target_noise((p.n_freq, 3, p.npix), seed=seed + i)
         out.append(torch.tensor(t, dtype=torch.float32, device="cuda"))
     return out
+
+
+def fd_chi2_reference(prob, target, sigma):
+    """Richardson-extrapolated central differences of the oracle's chi^2."""
+    th = prob.theta
+    h = 1e-4 * inputs.jf12_scales(th)
+
+    def L(t):
+        return oracle.chi2(oracle.forward(prob.with_theta(t)), target, sigma)
+    g1 = oracle.fd_gradient(L, th, h)
+    g2 = oracle.fd_gradient(L, th, h / 2)
+    return (4 * g2 - g1) / 3
+
+
+def fd_vjp_reference(prob, seed):
+    th = prob.theta
+    h = 1e-4 * inputs.jf12_scales(th)
+
+    def L(t):
+        return float(np.sum(seed * oracle.forward(prob.with_theta(t))))
+    g1 = oracle.fd_gradient(L, th, h)
+    g2 = oracle.fd_gradient(L, th, h / 2)
+    return (4 * g2 - g1) / 3
+
+
+def assert_grad(g, ref, what, rel=1e-3, floor=1e-4):
+    g = np.asarray(g, dtype=np.float64)
+    tol = rel * np.abs(ref) + floor * np.max(np.abs(ref))
+    bad = np.where(np.abs(g - ref) > tol)[0]
+    assert bad.size == 0, (what, [(int(i), float(g[i]), float(ref[i])) for i in bad])
+
+
+def mixed_sets():
+    """Six sets of the ensemble draw at Nside 2-8 and 13-128 steps: the step
+    counts fall in different lanes-per-ray bins, 13 leaves lane chunks of one
+    or two samples, and two sets share a size but not their parameters."""
+    sets = inputs.config4(n_sets=6, seed=11)
+    shapes = [(2, 13), (4, 128), (8, 64), (2, 100), (8, 37), (4, 128)]
+    return [s.replace(nside=n, n_steps=k) for s, (n, k) in zip(sets, shapes)]
+
+
+def test_batch_gradient_against_oracle(torch):
+    sets = mixed_sets()
+    sigma = 0.5
+    tg_np = []
+    for i, p in enumerate(sets):
+        th = inputs.perturbed_theta(p.theta, seed=30 + i)
+        tg_np.append(oracle.forward(p.with_theta(th)) + inputs.target_noise((p.n_freq, 3, p.npix), seed=30 + i))
+    tg = [torch.tensor(t, dtype=torch.float32, device="cuda") for t in tg_np]
+    plan = BatchPlan(sets)
+    maps = [torch.empty_like(t) for t in tg]
+    grads, chi2 = plan.run(targets=tg, sigma=sigma, maps=maps)
+    g = grads.cpu().numpy()
+    c = chi2.cpu().numpy()
+    for i, p in enumerate(sets):
+        ora = oracle.forward(p)
+        if p.n_steps < 16:
+            assert_parity_coarse(maps[i].cpu().numpy(), ora, p.freq_hz, f"batch set {i} maps")
+        else:
+            assert_parity(maps[i].cpu().numpy(), ora, what=f"batch set {i} maps")
+        assert c[i] == pytest.approx(oracle.chi2(ora, tg_np[i], sigma), rel=1e-5)
+        assert_grad(g[i], fd_chi2_reference(p, tg_np[i], sigma), f"batch set {i} chi2 gradient")
+    # VJP mode of the same plan, two sets against the oracle
+    seeds_np = [inputs.normal(inputs.substream(80 + i, p.npix), p.n_freq * 3 * p.npix).reshape(p.n_freq, 3, p.npix)
+                for i, p in enumerate(sets)]
+    gv, _ = plan.run(seeds=[torch.tensor(s, dtype=torch.float32, device="cuda") for s in seeds_np])
+    gv = gv.cpu().numpy()
+    for i in (1, 4):
+        assert_grad(gv[i], fd_vjp_reference(sets[i], seeds_np[i]), f"batch set {i} VJP gradient")
+    plan.close()
 
 
 def test_batch_matches_single_adjoint(torch):

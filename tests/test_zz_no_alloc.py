@@ -84,6 +84,66 @@ def test_noalloc_matches_workspace_adjoint(torch):
         assert close(gv, gv_ref)
 
 
+def max_pixels_within_limit(L, prob):
+    """Largest pixel count whose adjoint workspace fits the library's fixed
+    scratch (bisection on synax_adjoint_workspace_bytes, a host-only call)."""
+    limit = 8 << 20
+    lo, hi = 1, prob.npix
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        s = _native.problem_struct(prob.replace(pix_begin=0, pix_count=mid))
+        n = ctypes.c_size_t(0)
+        assert L.synax_adjoint_workspace_bytes(ctypes.byref(s), ctypes.byref(n)) == 0
+        if n.value <= limit:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+def test_noalloc_at_the_size_limit(torch):
+    """The largest pixel range that fits, at 32 lanes per ray (the most CTAs,
+    so the last CTA's partial row sits at the end of the array), against the
+    workspace adjoint; one pixel more is rejected before anything runs."""
+    L = _native.lib()
+    base = inputs.config2().replace(nside=256, n_steps=16)
+    n_max = max_pixels_within_limit(L, base)
+    assert 200000 < n_max < base.npix
+    prob = base.replace(pix_begin=base.npix - n_max - 5, pix_count=n_max)
+    s = _native.problem_struct(prob)
+    gm = torch.tensor(inputs.normal(6, 4 * 3 * n_max).reshape(4, 3, n_max), dtype=torch.float32, device="cuda")
+    assert L.synax_set_lanes_per_ray(-1, 32) == 0
+    try:
+        g_ref, _, _ = call_reference(torch, L, s, gm, None, 1.0)
+        for _ in range(2):
+            g, _, _ = call_noalloc(torch, L, s, gm, None, 1.0)
+            assert close(g, g_ref)
+    finally:
+        assert L.synax_set_lanes_per_ray(-1, 0) == 0
+    over = _native.problem_struct(base.replace(pix_begin=0, pix_count=n_max + 1))
+    g = torch.full((16,), 7.0, dtype=torch.float64, device="cuda")
+    rc = L.synax_adjoint_noalloc(ctypes.byref(over), ptr(gm), None, 1.0, ptr(g), None, None,
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == _native.SYNAX_ESPACE
+    assert torch.all(g == 7.0)                  # nothing was enqueued
+
+
+def test_noalloc_fp64_wmap(torch):
+    """The FP64 march and the 8-parameter WMAP-type model through the scratch."""
+    L = _native.lib()
+    prob = inputs.config1().replace(nside=8, n_steps=64)
+    assert prob.f64
+    target = oracle.forward(prob) + inputs.target_noise((prob.n_freq, 3, prob.npix), seed=12, sigma=0.1)
+    tgt = torch.tensor(target, dtype=torch.float64, device="cuda")
+    s = _native.problem_struct(prob)
+    g_ref, c_ref, m_ref = call_reference(torch, L, s, None, tgt, 0.1)
+    for _ in range(2):
+        g, c, m = call_noalloc(torch, L, s, None, tgt, 0.1)
+        assert np.allclose(g, g_ref, rtol=1e-12, atol=1e-12 * np.abs(g_ref).max())
+        assert c[0] == pytest.approx(c_ref[0], rel=1e-12)
+        assert np.allclose(m, m_ref, rtol=1e-12, atol=0)
+
+
 def test_noalloc_rejects_oversize(torch):
     L = _native.lib()
     big = _native.problem_struct(inputs.config2().replace(nside=256, n_steps=16))
