@@ -49,6 +49,14 @@ ADJ_FACTOR = 3
 # blend and cell location in place of the field model; its adjoint adds 36
 # FP32 of node weights and sums per sample.  The pipe whose share of the
 # measured peaks (measure_peaks) is larger bounds each model.
+# The MUFU operations split into two classes because their measured rates
+# differ: 2^x (ex2) and the rest (lg2, sin, cos, rcp, rsqrt).  Of each
+# model's field MUFU count the exponentials are: JF12-type 9 (two logistic
+# transitions, halo and X-field profiles, the CR profile's two, n_e's two,
+# the emissivity power), WMAP-type 6, stacked 5, grid 5 (e^{-2|z|}, the CR
+# profile's two, n_e, the emissivity power).
+MODEL_EX2 = {"jf12": 9, "wmap": 6, "wmap_stack": 5, "grid": 5}
+FWD_EX2_OPS = 9
 MODEL_OPS = {"jf12": (168, 14), "wmap": (60, 14), "wmap_stack": (99, 25), "grid": (142, 9)}
 GRID_ADJ_EXTRA_FP32 = 36
 # DRAM bytes (read + write) of one k_adjoint launch of this workload, from the
@@ -139,28 +147,35 @@ class ClockSampler:
 def measure_peaks(sx) -> dict:
     """FP32 and SFU throughput measured on this GPU (synax_pipe_peak): the
     FP32 peak is the faster of scalar FFMA and paired FFMA2 (element
-    operations), the MUFU peak the fastest of the six SFU instructions the
-    march uses, so that neither flatters a kernel's fraction."""
+    operations); the SFU has two measured rates, ex2 and the slowest of the
+    other instructions the march uses (lg2, sin, cos, rcp, rsqrt)."""
     r = sx.pipe_peaks(iters=16384)
     mufu = {k: r[k] / 1e12 for k in ("ex2", "lg2", "sin", "cos", "rcp", "rsqrt")}
-    return {"fp32_top": max(r["ffma"], r["ffma2"]) / 1e12, "mufu_top": max(mufu.values()),
+    return {"fp32_top": max(r["ffma"], r["ffma2"]) / 1e12, "mufu_ex2": mufu["ex2"],
+            "mufu_other": min(v for k, v in mufu.items() if k != "ex2"),
             "unit": "T element op/s", "ffma": r["ffma"] / 1e12, "ffma2": r["ffma2"] / 1e12, "mufu": mufu,
             "sms": r["sms"]}
 
 
-def roofline_alu(fp32_ops: float, mufu_ops: float, t_s: float, peaks: dict, kernel: str) -> dict:
+def roofline_alu(fp32_ops: float, mufu_ops: float, t_s: float, peaks: dict, kernel: str,
+                 ex2_ops: float = 0.0) -> dict:
     """Roofline of a march kernel from its algorithmic FP32 and MUFU
-    operations over a measured duration t_s: the pipe whose share of its
-    measured peak is larger bounds it."""
-    fp32_ach = fp32_ops / t_s / 1e12
-    mufu_ach = mufu_ops / t_s / 1e12
-    on_fp32 = fp32_ach / peaks["fp32_top"] >= mufu_ach / peaks["mufu_top"]
-    pipe, ach, peak = ("FP32", fp32_ach, peaks["fp32_top"]) if on_fp32 else ("MUFU", mufu_ach, peaks["mufu_top"])
-    other = mufu_ach / peaks["mufu_top"] if on_fp32 else fp32_ach / peaks["fp32_top"]
+    operations (ex2_ops of the MUFU ones are exponentials) over a measured
+    duration t_s.  Each pipe's roofline time is its operations over its
+    measured rates; the pipe with the longer roofline time bounds the kernel
+    and frac = that time / t_s.  For MUFU, peak is the effective rate of the
+    kernel's mix (mufu_ops over its roofline time)."""
+    t_fp32 = fp32_ops / (peaks["fp32_top"] * 1e12)
+    t_mufu = ex2_ops / (peaks["mufu_ex2"] * 1e12) + (mufu_ops - ex2_ops) / (peaks["mufu_other"] * 1e12)
+    mufu_eff = mufu_ops / t_mufu / 1e12 if t_mufu > 0 else float("inf")
+    if t_fp32 >= t_mufu:
+        pipe, ach, peak, frac, other = "FP32", fp32_ops / t_s / 1e12, peaks["fp32_top"], t_fp32 / t_s, t_mufu / t_s
+    else:
+        pipe, ach, peak, frac, other = "MUFU", mufu_ops / t_s / 1e12, mufu_eff, t_mufu / t_s, t_fp32 / t_s
     return {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": f"T {pipe} op/s",
-            "frac": ach / peak, "frac_other_pipe": other, "kernel": kernel,
-            "peak_basis": f"measured {pipe} peak of this GPU (synax_pipe_peak, peaks_measured; "
-                          f"{'max of FFMA, FFMA2' if pipe == 'FP32' else 'fastest SFU instruction'})"}
+            "frac": frac, "frac_other_pipe": other, "kernel": kernel,
+            "peak_basis": f"measured peaks of this GPU (synax_pipe_peak, peaks_measured; "
+                          f"{'max of FFMA, FFMA2' if pipe == 'FP32' else 'ex2 and other-SFU rates weighted by the mix'})"}
 
 
 def march_roofline(model: str, n_freq: int, samples_per_s: float, peaks: dict, adjoint: bool,
@@ -168,13 +183,15 @@ def march_roofline(model: str, n_freq: int, samples_per_s: float, peaks: dict, a
     """Roofline of a march kernel from the per-sample operation counts of
     MODEL_OPS against the measured pipe peaks."""
     fp32, mufu = MODEL_OPS[model]
+    ex2 = MODEL_EX2[model]
     fp32 += 8 * n_freq
     mufu += 2 * n_freq
     if adjoint:
         fp32 = ADJ_FACTOR * fp32 + (GRID_ADJ_EXTRA_FP32 if model == "grid" else 0)
         mufu = ADJ_FACTOR * mufu
-    out = roofline_alu(samples_per_s * fp32, samples_per_s * mufu, 1.0, peaks, kernel)
-    out["ops_per_sample"] = {"fp32": fp32, "mufu": mufu}
+        ex2 = ADJ_FACTOR * ex2
+    out = roofline_alu(samples_per_s * fp32, samples_per_s * mufu, 1.0, peaks, kernel, samples_per_s * ex2)
+    out["ops_per_sample"] = {"fp32": fp32, "mufu": mufu, "mufu_ex2": ex2}
     return out
 
 
@@ -899,10 +916,13 @@ def run_synax(args):
     # pipe peaks measured on this GPU inside the same clock-sampled region
     adj_fp32 = ADJ_FACTOR * FWD_FP32_OPS * samples
     adj_mufu = ADJ_FACTOR * FWD_MUFU_OPS * samples
-    roof = roofline_alu(adj_fp32, adj_mufu, ms * 1e-3, peaks, "k_adjoint (+ k_reduce_partials)")
+    roof = roofline_alu(adj_fp32, adj_mufu, ms * 1e-3, peaks, "k_adjoint (+ k_reduce_partials)",
+                        ADJ_FACTOR * FWD_EX2_OPS * samples)
     roof["traffic"] = ADJ_DRAM_BYTES
-    roof["ops_per_sample"] = {"fp32": ADJ_FACTOR * FWD_FP32_OPS, "mufu": ADJ_FACTOR * FWD_MUFU_OPS}
-    fwd_roof = roofline_alu(FWD_FP32_OPS * samples, FWD_MUFU_OPS * samples, ms_fwd * 1e-3, peaks, "k_forward")
+    roof["ops_per_sample"] = {"fp32": ADJ_FACTOR * FWD_FP32_OPS, "mufu": ADJ_FACTOR * FWD_MUFU_OPS,
+                              "mufu_ex2": ADJ_FACTOR * FWD_EX2_OPS}
+    fwd_roof = roofline_alu(FWD_FP32_OPS * samples, FWD_MUFU_OPS * samples, ms_fwd * 1e-3, peaks, "k_forward",
+                            FWD_EX2_OPS * samples)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,

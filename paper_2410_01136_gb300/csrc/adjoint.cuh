@@ -579,7 +579,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                 }
                 R f = -ne * bn;
                 // as in the forward march (same operations, same rounding)
-                if constexpr (MODEL == SYNAX_MODEL_GRID && sizeof(R) == 4) f -= ne * bpar_lo(B, nd);
+                if constexpr (kPreciseLos<MODEL> && sizeof(R) == 4) f -= ne * bpar_lo(B, nd);
 
                 // Q <- Q - f (the RM before sample n) and s_n = that + w f,
                 // formed from the same Q as Q + (w - 1) f (exact factor)

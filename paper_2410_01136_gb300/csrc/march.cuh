@@ -756,7 +756,7 @@ template <> struct Model<SYNAX_MODEL_WMAP> {
         const R n0u = cr_density<R>(m[mc::W_N0U], rho, az);
         N0 = m[mc::W_N0OBS] * n0u;
         const R neu = F::exp(-F::mulc(rho, 0.05)) * sech2;
-        ne = m[mc::W_NE0] * neu;
+        ne = F::mul_hl(neu, m[mc::W_NE0], m[mc::W_NE0_LO]);
         loc.c = c; loc.s = s; loc.az = az; loc.rho = rho;
         loc.env = env; loc.cpsi = cp; loc.spsi = sp; loc.cchi = cc; loc.schi = sc;
         loc.lnr8 = lnr8; loc.thz = th; loc.in_range = in_range ? R(1) : R(0);
@@ -859,7 +859,6 @@ template <> struct Model<SYNAX_MODEL_JF12> {
 // permutations of Eq. 16 (stack_w, and the index maps in eval and in the
 // gradient rule).  B feeds the RM, so every transcendental here is the
 // accurate one (logf, sincosf, expf).
-__host__ __device__ constexpr double stack_w(int k) { return k == 0 ? 0.6 : (k == 2 ? 0.1 : 0.3); }
 
 template <> struct Model<SYNAX_MODEL_WMAP_STACK> {
     template <typename R>
@@ -880,6 +879,9 @@ template <> struct Model<SYNAX_MODEL_WMAP_STACK> {
         const R lnr8 = in_range ? F::log(rho * R(0.125)) : R(0);
         R th = (R(1) - e2) * inv1;                             // tanh |z|
         th = z < R(0) ? -th : th;
+        // unit vector of each component, scaled by its weight times b0 (a
+        // host product kept as hi + lo: the rounding of these magnitudes would
+        // be the same at every sample of every ray, a coherent RM bias)
         R comp[4][3];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -889,22 +891,20 @@ template <> struct Model<SYNAX_MODEL_WMAP_STACK> {
             R sp, cp, sc, cc;
             F::sincos(psi, &sp, &cp);
             F::sincos(chi, &sc, &cc);
-            const R br = q[0] * cp * cc, bp = q[0] * sp * cc;
-            comp[k][0] = br * c - bp * s;
-            comp[k][1] = br * s + bp * c;
-            comp[k][2] = q[0] * sc;
+            const R ur = cp * cc, up = sp * cc;
+            const R hi = m[mc::S_WB + k], lo = m[mc::S_WB_LO + k];
+            comp[k][0] = F::mul_hl(ur * c - up * s, hi, lo);
+            comp[k][1] = F::mul_hl(ur * s + up * c, hi, lo);
+            comp[k][2] = F::mul_hl(sc, hi, lo);
             loc.kcp[k] = cp; loc.ksp[k] = sp; loc.kcc[k] = cc; loc.ksc[k] = sc;
         }
-        B[0] = R(stack_w(0)) * comp[0][0] + R(stack_w(1)) * comp[1][0] + R(stack_w(2)) * comp[2][2] +
-               R(stack_w(3)) * comp[3][1];
-        B[1] = R(stack_w(0)) * comp[0][1] + R(stack_w(1)) * comp[1][2] + R(stack_w(2)) * comp[2][1] +
-               R(stack_w(3)) * comp[3][0];
-        B[2] = R(stack_w(0)) * comp[0][2] + R(stack_w(1)) * comp[1][1] + R(stack_w(2)) * comp[2][0] +
-               R(stack_w(3)) * comp[3][2];
+        B[0] = comp[0][0] + comp[1][0] + comp[2][2] + comp[3][1];
+        B[1] = comp[0][1] + comp[1][2] + comp[2][1] + comp[3][0];
+        B[2] = comp[0][2] + comp[1][1] + comp[2][0] + comp[3][2];
         const R n0u = cr_density<R>(m[mc::S_N0U], rho, az);
         N0 = m[mc::S_N0OBS] * n0u;
         const R neu = F::exp(-F::mulc(rho, 0.05)) * (R(4) * e2 * inv1 * inv1);
-        ne = m[mc::S_NE0] * neu;
+        ne = F::mul_hl(neu, m[mc::S_NE0], m[mc::S_NE0_LO]);
         loc.c = c; loc.s = s; loc.lnr8 = lnr8; loc.thz = th; loc.in_range = in_range ? R(1) : R(0);
         loc.n0_unit = n0u; loc.ne_unit = neu;
     }
@@ -1090,7 +1090,7 @@ __device__ __forceinline__ void grid_eval(const MapParams<R>& P, GridCell<R>& gc
     const R n0u = cr_density<R>(P.m[mc::G_N0U], rho, az);
     N0 = P.m[mc::G_N0OBS] * n0u;
     const R neu = F::exp(-F::mulc(rho, 0.05)) * (R(4) * e2 * inv1 * inv1);
-    ne = P.m[mc::G_NE0] * neu;
+    ne = F::mul_hl(neu, P.m[mc::G_NE0], P.m[mc::G_NE0_LO]);
     loc.n0_unit = n0u;
     loc.ne_unit = neu;
     loc.gbase = base;
@@ -1381,7 +1381,7 @@ __device__ __forceinline__ void wmap_eval(const float* m, float2 x, float2 y, fl
     const float2 n0u = mul2(dup2(m[mc::W_N0U]), mul2(eR, mul2(mul2(dup2(4.0f), ec), mul2(iv, iv))));
     N0 = mul2(dup2(m[mc::W_N0OBS]), n0u);
     const float2 neu = mul2(expf2(neg2(mulc(rho, 0.05))), sech2);
-    ne = mul2(dup2(m[mc::W_NE0]), neu);
+    ne = fma2(neu, dup2(m[mc::W_NE0]), mul2(neu, dup2(m[mc::W_NE0_LO])));      // ne0 as hi + lo
     if constexpr (LOC) {
         lc->c = c;
         lc->s = s;
@@ -1486,10 +1486,15 @@ __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const
 // and the FP32 rounding of the direction alone shifts the far end of a ray
 // by ~1e-6 kpc in one direction, a bias of the RM (Eq. 7) that is visible in
 // the Faraday rotation below 1 GHz.
+// The stacked WMAP model takes the same care: its field fills the box at
+// constant magnitude, so a ray's RM keeps growing out to the wall.
+template <int MODEL>
+constexpr bool kPreciseLos = MODEL == SYNAX_MODEL_GRID || MODEL == SYNAX_MODEL_WMAP_STACK;
+
 template <int MODEL, typename R>
 __device__ __forceinline__ void sample_pos(const MapParams<R>& P, const Los<R>& L, const ff* nd, R t, R& x, R& y,
                                            R& z) {
-    if constexpr (MODEL == SYNAX_MODEL_GRID && sizeof(R) == 4) {
+    if constexpr (kPreciseLos<MODEL> && sizeof(R) == 4) {
         x = fmaf(t, L.n[0], P.obs[0]) + fmaf(t, nd[0].lo, P.obs_lo[0]);
         y = fmaf(t, L.n[1], P.obs[1]) + fmaf(t, nd[1].lo, P.obs_lo[1]);
         z = fmaf(t, L.n[2], P.obs[2]) + fmaf(t, nd[2].lo, P.obs_lo[2]);
@@ -1565,7 +1570,7 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
             Model<MODEL>::eval(P.m, s_arms, t, x, y, z, ac, B, N0, ne, loc);
         }
         Emit<R> e = emit<R>(B, N0, ne, L, P.q);
-        if constexpr (MODEL == SYNAX_MODEL_GRID && sizeof(R) == 4) e.f -= ne * bpar_lo(B, nd);
+        if constexpr (kPreciseLos<MODEL> && sizeof(R) == 4) e.f -= ne * bpar_lo(B, nd);
         accI += e.jI;
         PT s_n;                                        // RM at the midpoint (Eq. 7)
         if constexpr (sizeof(R) == 4) {

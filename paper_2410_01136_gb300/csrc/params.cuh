@@ -80,6 +80,12 @@ SYNAX_HD inline FreqConsts freq_consts(double nu, double p) {
     return F;
 }
 
+// The low part of v in the march precision: v - (R)v (0 in FP64).
+template <typename R>
+SYNAX_HD inline R lo_part(double v) {
+    return R(v - (double)R(v));
+}
+
 // Writes every theta-dependent field of M and (when given) A, and nothing
 // else: q, aI, aP, the model constants m[] that depend on theta, dlnaI/dp and
 // dlnaP/dp.  n0_norm = 1 / (e^{-rho/5} sech^2 z) at the observer.
@@ -115,6 +121,7 @@ SYNAX_HD inline void fill_theta(int model, const double* th, const double* freq_
         M.m[mc::W_N0U] = R(n0_norm);
         M.m[mc::W_N0OBS] = R(th[5]);
         M.m[mc::W_NE0] = R(th[7]);
+        M.m[mc::W_NE0_LO] = lo_part<R>(th[7]);
         break;
     case SYNAX_MODEL_JF12:
         for (int k = 0; k < 8; ++k) M.m[mc::J_B + k] = R(th[k]);
@@ -146,11 +153,18 @@ SYNAX_HD inline void fill_theta(int model, const double* th, const double* freq_
         M.m[mc::S_N0U] = R(n0_norm);
         M.m[mc::S_N0OBS] = R(th[16]);
         M.m[mc::S_NE0] = R(th[18]);
+        M.m[mc::S_NE0_LO] = lo_part<R>(th[18]);
+        for (int k = 0; k < 4; ++k) {
+            const double wb = stack_w(k) * th[4 * k];
+            M.m[mc::S_WB + k] = R(wb);
+            M.m[mc::S_WB_LO + k] = lo_part<R>(wb);
+        }
         break;
     case SYNAX_MODEL_GRID:
         M.m[mc::G_N0U] = R(n0_norm);
         M.m[mc::G_N0OBS] = R(th[0]);
         M.m[mc::G_NE0] = R(th[2]);
+        M.m[mc::G_NE0_LO] = lo_part<R>(th[2]);
         break;
     default: break;
     }

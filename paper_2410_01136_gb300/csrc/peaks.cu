@@ -35,11 +35,13 @@ __device__ __forceinline__ float mufu_step(float x) {
         asm volatile("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     } else if constexpr (PIPE == SYNAX_PIPE_RCP) {
+        // x -> 1/x + 1 (fixed point at the golden ratio); a bare 1/x chain
+        // would be an involution that the compiler may fold away
         asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-        return y;
+        return y + 1.0f;
     } else {
         asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-        return y;
+        return y + 0.5f;                        // x -> x^-1/2 + 1/2 stays near 1.2
     }
 }
 

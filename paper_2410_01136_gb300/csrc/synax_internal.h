@@ -32,7 +32,8 @@ namespace mc {
 // toy
 constexpr int TOY_B = 0, TOY_NE = 3, TOY_N0 = 4, TOY_R0 = 5;
 // WMAP-type
-constexpr int W_B0 = 0, W_PSI0 = 1, W_PSI1 = 2, W_CHI0 = 3, W_BUX = 4, W_N0U = 5, W_NE0 = 6, W_N0OBS = 7;
+constexpr int W_B0 = 0, W_PSI0 = 1, W_PSI1 = 2, W_CHI0 = 3, W_BUX = 4, W_N0U = 5, W_NE0 = 6, W_N0OBS = 7,
+              W_NE0_LO = 8;   // ne0 - (R)ne0: n_e multiplies the RM integrand, so its scale is kept as hi + lo
 // JF12-type
 constexpr int J_B = 0;              // b_1..b_8 at 0..7
 constexpr int J_BH = 8, J_IZH = 9, J_BX = 10, J_COSX = 11, J_SINX = 12, J_COTX = 13,
@@ -41,11 +42,15 @@ constexpr int J_BH = 8, J_IZH = 9, J_BX = 10, J_COSX = 11, J_SINX = 12, J_COTX =
               J_BH_IZH2 = 27, J_IH1_SQ = 28, J_IH2_SQ = 29;   // B_h / z_h^2, 1 / h1^2, 1 / h2^2 (gradients)
 // grid model: N0 normalisation, N0_obs, ne0; per axis (n - 1) / l (as hi + lo),
 // (n - 1) / 2 and n - 1
-constexpr int G_N0U = 0, G_N0OBS = 1, G_NE0 = 2, G_S = 3, G_O = 6, G_UMAX = 9, G_SLO = 12;
+constexpr int G_N0U = 0, G_N0OBS = 1, G_NE0 = 2, G_S = 3, G_O = 6, G_UMAX = 9, G_SLO = 12, G_NE0_LO = 15;
 // stacked WMAP model: component k's b0, psi0, psi1, chi0B at 4k .. 4k + 3, then
-// the N0 normalisation, N0_obs and ne0
-constexpr int S_COMP = 0, S_N0U = 16, S_N0OBS = 17, S_NE0 = 18;
+// the N0 normalisation, N0_obs and ne0; ne0's low part; the stacking weight
+// times b0 of component k as hi (S_WB + k) and lo (S_WB_LO + k) parts
+constexpr int S_COMP = 0, S_N0U = 16, S_N0OBS = 17, S_NE0 = 18, S_NE0_LO = 19, S_WB = 20, S_WB_LO = 24;
 }  // namespace mc
+
+// Weight of component k of the stacked WMAP model (Eq. 16).
+__host__ __device__ constexpr double stack_w(int k) { return k == 0 ? 0.6 : (k == 2 ? 0.1 : 0.3); }
 
 template <typename R>
 struct MapParams {

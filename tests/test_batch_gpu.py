@@ -70,6 +70,23 @@ def fd_vjp_reference(prob, seed):
     return (4 * g2 - g1) / 3
 
 
+def chi2_tolerance(ora, target, sigma, freqs, n_steps):
+    """Bound on |chi^2 - chi^2_oracle| implied by maps at the stated
+    tolerances: every entry may differ from the oracle by b_e (1e-5 |I|;
+    1e-4 max(|P|, 1e-2 median |P|) for Q and U, 2e-4 below 1 GHz for
+    marches of fewer than 16 steps), so chi^2 moves by at most
+    sum (2 |M - T| b_e + b_e^2) / sigma^2."""
+    b = np.empty_like(ora)
+    for f, nu in enumerate(freqs):
+        b[f, 0] = 1e-5 * np.abs(ora[f, 0])
+        P = np.hypot(ora[f, 1], ora[f, 2])
+        tol = 2e-4 if (n_steps < 16 and nu < 1e9) else 1e-4
+        bp = tol * np.maximum(P, 1e-2 * np.median(P))
+        b[f, 1] = bp
+        b[f, 2] = bp
+    return float(np.sum(2 * np.abs(ora - target) * b + b * b)) / sigma ** 2
+
+
 def assert_grad(g, ref, what, rel=1e-3, floor=1e-4):
     g = np.asarray(g, dtype=np.float64)
     tol = rel * np.abs(ref) + floor * np.max(np.abs(ref))
@@ -105,7 +122,8 @@ def test_batch_gradient_against_oracle(torch):
             assert_parity_coarse(maps[i].cpu().numpy(), ora, p.freq_hz, f"batch set {i} maps")
         else:
             assert_parity(maps[i].cpu().numpy(), ora, what=f"batch set {i} maps")
-        assert c[i] == pytest.approx(oracle.chi2(ora, tg_np[i], sigma), rel=1e-5)
+        c_ora = oracle.chi2(ora, tg_np[i], sigma)
+        assert abs(c[i] - c_ora) <= chi2_tolerance(ora, tg_np[i], sigma, p.freq_hz, p.n_steps), (i, c[i], c_ora)
         assert_grad(g[i], fd_chi2_reference(p, tg_np[i], sigma), f"batch set {i} chi2 gradient")
     # VJP mode of the same plan, two sets against the oracle
     seeds_np = [inputs.normal(inputs.substream(80 + i, p.npix), p.n_freq * 3 * p.npix).reshape(p.n_freq, 3, p.npix)

@@ -79,25 +79,30 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
 def test_roofline_accounting():
     """The per-sample operation counts behind every row's roofline and the
     choice of bounding pipe against given peaks: the JF12-type adjoint is
-    3 x (200 FP32 + 22 MUFU) at four frequencies; the grid adjoint adds 36
-    FP32 of node weights; with FP32 at 8 times the SFU rate the JF12-type
-    rows are FP32-bound and the WMAP-type and stacked rows MUFU-bound."""
+    3 x (200 FP32 + 22 MUFU, 9 of them ex2) at four frequencies; the grid
+    adjoint adds 36 FP32 of node weights.  Each pipe's roofline time is its
+    operations over its rates (ex2 and the other SFU instructions apart),
+    the longer one bounds, frac = that time over the measured time."""
     sys.path.insert(0, ROOT)
     import bench
-    peaks = {"fp32_top": 40.0, "mufu_top": 5.0}
+    peaks = {"fp32_top": 40.0, "mufu_ex2": 10.0, "mufu_other": 5.0}
     r = bench.march_roofline("jf12", 4, 4.0e10, peaks, True, "k")
-    assert r["ops_per_sample"] == {"fp32": 600, "mufu": 66} and r["pipe"] == "FP32"
+    assert r["ops_per_sample"] == {"fp32": 600, "mufu": 66, "mufu_ex2": 27} and r["pipe"] == "FP32"
     assert r["peak"] == pytest.approx(40.0)
     assert r["frac"] == pytest.approx(4.0e10 * 600 / 40.0e12)
-    assert r["frac_other_pipe"] == pytest.approx(4.0e10 * 66 / 5.0e12)
+    assert r["frac_other_pipe"] == pytest.approx(4.0e10 * (27 / 10.0e12 + 39 / 5.0e12))
     f = bench.march_roofline("jf12", 4, 1.0e11, peaks, False, "k")
-    assert f["ops_per_sample"] == {"fp32": 200, "mufu": 22}
+    assert f["ops_per_sample"] == {"fp32": 200, "mufu": 22, "mufu_ex2": 9}
     g = bench.march_roofline("grid", 1, 1.0, peaks, True, "k")
-    assert g["ops_per_sample"] == {"fp32": 486, "mufu": 33} and g["pipe"] == "FP32"
-    for model, fwd in (("wmap", {"fp32": 68, "mufu": 16}), ("wmap_stack", {"fp32": 107, "mufu": 27})):
+    assert g["ops_per_sample"] == {"fp32": 486, "mufu": 33, "mufu_ex2": 15} and g["pipe"] == "FP32"
+    for model, fwd in (("wmap", {"fp32": 68, "mufu": 16, "mufu_ex2": 6}),
+                       ("wmap_stack", {"fp32": 107, "mufu": 27, "mufu_ex2": 5})):
         w = bench.march_roofline(model, 1, 1.0e10, peaks, False, "k")
         assert w["ops_per_sample"] == fwd and w["pipe"] == "MUFU"
-        assert w["peak"] == pytest.approx(5.0)
-    # a faster SFU (12 T/s) moves the stacked model's bound to the FP32 pipe
-    w = bench.march_roofline("wmap_stack", 1, 1.0e10, {"fp32_top": 40.0, "mufu_top": 12.0}, False, "k")
+        t_mufu = fwd["mufu_ex2"] / 10.0e12 + (fwd["mufu"] - fwd["mufu_ex2"]) / 5.0e12
+        assert w["frac"] == pytest.approx(1.0e10 * t_mufu)
+        assert w["peak"] == pytest.approx(fwd["mufu"] / t_mufu / 1e12)
+    # a faster SFU moves the stacked model's bound to the FP32 pipe
+    w = bench.march_roofline("wmap_stack", 1, 1.0e10, {"fp32_top": 40.0, "mufu_ex2": 20.0, "mufu_other": 12.0},
+                             False, "k")
     assert w["pipe"] == "FP32" and w["frac"] == pytest.approx(1.0e10 * 107 / 40.0e12)

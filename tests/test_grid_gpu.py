@@ -5,14 +5,10 @@ Maps: element-wise parity (I to 1e-5, P = Q + iU to 1e-4 relative) on seeded
 smooth grids, at small sizes with ragged pixel ranges and step counts, and on
 sampled pixels of the full Nside-64, 512-step, 128 x 128 x 32 workload.
 
-Below 1 GHz, FP32 holds P to 5e-4 on these grids: their field is strong out
-to the walls of the box, the Faraday phase reaches ~1.6e3 rad at 408 MHz and
-the most rotated pixels keep only ~0.3 % of their unrotated polarised
-intensity P0.  An FP32 march is accurate to ~1e-6 P0 there (phase errors of
-~1e-6 rad from the per-sample rounding of n_e B_par, coherent over a ray),
-which is ~3e-4 of such a pixel's |P|.  FP64 is held to 1e-9 at every
-frequency, and FP32 to 1e-4 at and above 1 GHz (the grid workload of Sec. 3.3
-is at 2.4 GHz).
+FP32 is held to these tolerances at every frequency, 408 MHz included
+(where the Faraday phase reaches ~1.6e3 rad on these grids); FP64 to 1e-9.
+An FP32 march reads its grid as float32, the library's input format, so the
+oracle of an FP32 case is given the same float32 node values (fp32_grid).
 theta gradient: Richardson-extrapolated central differences of the oracle.
 Grid gradient (synax_adjoint_grid): directional derivatives <G, V> along
 seeded random directions V and single-node derivatives, both against
@@ -26,7 +22,7 @@ import pytest
 import oracle
 from paper_2410_01136_gb300 import adjoint, adjoint_grid, eval_fields, forward, inputs
 
-from .parity import assert_parity, assert_parity_by_frequency
+from .parity import assert_parity, assert_parity_by_frequency, fp32_grid
 
 pytestmark = pytest.mark.gpu
 
@@ -42,11 +38,11 @@ def torch():
 
 
 def small(nside=8, n_steps=100, n=(12, 10, 6), seed=21, freqs=(408e6, 2.4e9), **kw):
-    return inputs.grid_problem(nside=nside, n_steps=n_steps, freq_hz=freqs, n=n, seed=seed, **kw)
+    return fp32_grid(inputs.grid_problem(nside=nside, n_steps=n_steps, freq_hz=freqs, n=n, seed=seed, **kw))
 
 
 def check_maps(m, ref, prob, what):
-    """Parity per frequency (tests/parity.py: FP32 P to 5e-4 below 1 GHz)."""
+    """Parity per frequency (tests/parity.py)."""
     assert_parity_by_frequency(m, ref, prob.freq_hz, prob.f64, what)
 
 
@@ -84,10 +80,19 @@ def test_low_frequency(torch, f64, n):
 
 
 def test_forward_full_size_sampled(torch):
-    prob = inputs.grid_problem()                     # Nside 64, 512 steps, 128 x 128 x 32, 2.4 GHz
+    prob = fp32_grid(inputs.grid_problem())          # Nside 64, 512 steps, 128 x 128 x 32, 2.4 GHz
     m = forward(prob).cpu().numpy()
     pix = inputs.sample_pixels(prob.npix, 96, seed=12)
     assert_parity(m[:, :, pix], oracle.forward(prob, pix=pix), what="grid full size")
+
+
+def test_forward_full_size_sampled_408mhz(torch):
+    """The full workload's geometry and grid at 408 MHz, where the Faraday
+    phase is largest, at the stated tolerances."""
+    prob = fp32_grid(inputs.grid_problem(freq_hz=(408e6,)))
+    m = forward(prob).cpu().numpy()
+    pix = inputs.sample_pixels(prob.npix, 96, seed=15)
+    assert_parity(m[:, :, pix], oracle.forward(prob, pix=pix), what="grid full size 408 MHz")
 
 
 def test_uniform_grid_equals_wmap_model(torch):

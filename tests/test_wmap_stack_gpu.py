@@ -1,7 +1,7 @@
 """The stacked WMAP model of Sec. 4.3 (Eq. 16) on the GPU against the FP64
-oracle, through the C ABI: maps (FP32 and FP64; at and above 1 GHz to the
-stated tolerance, at 408 MHz to the FP32 bound of a box-filling field,
-tests/parity.py), the full Nside-64 workload at sampled pixels, fields at
+oracle, through the C ABI: maps (FP32 and FP64, 408 MHz to 2.4 GHz, to the
+stated tolerances, tests/parity.py), the full Nside-64 workload at sampled
+pixels, fields at
 points, and the 19-component gradient (16 field parameters of the paper's
 table + N0_obs, p, n_e0) against Richardson-extrapolated central
 differences of the oracle, as in tests/test_adjoint_gpu.py."""
@@ -45,6 +45,13 @@ def test_forward_full_size_sampled(torch):
     m = forward(prob).cpu().numpy()
     pix = inputs.sample_pixels(prob.npix, 96, seed=14)
     assert_parity(m[:, :, pix], oracle.forward(prob, pix=pix), what="stacked WMAP full size")
+
+
+def test_forward_full_size_sampled_408mhz(torch):
+    prob = inputs.wmap_stack_problem(freq_hz=(408e6,))
+    m = forward(prob).cpu().numpy()
+    pix = inputs.sample_pixels(prob.npix, 96, seed=16)
+    assert_parity(m[:, :, pix], oracle.forward(prob, pix=pix), what="stacked WMAP full size 408 MHz")
 
 
 @pytest.mark.parametrize("f64", [False, True])
