@@ -204,7 +204,9 @@ int synax_batch(synax_batch_plan* plan, const double* thetas, const void* const*
  * (device global timer); waits for the run.  ms_out: host [n_sets]. */
 int synax_batch_latencies(synax_batch_plan* plan, double* ms_out);
 
-/* Tile count, lanes per ray and persistent grid size chosen by the plan. */
+/* Tile count, lanes per ray (of the largest share of the samples: each
+ * work item takes the tuned width of its step count and map size) and
+ * persistent grid size chosen by the plan. */
 int synax_batch_plan_info(const synax_batch_plan* plan, long long* n_tiles, int* lanes_per_ray,
                           int* grid);
 
@@ -215,6 +217,18 @@ void synax_batch_plan_destroy(synax_batch_plan* plan);
 /* Parameter sets and parameter count of a plan. */
 int synax_batch_plan_n_sets(const synax_batch_plan* plan);
 int synax_batch_plan_n_theta(const synax_batch_plan* plan);
+
+/* Two-set work items of a plan: sets that share their whole ray geometry
+ * (Nside, step count, pixel range, ray extent or box, observer, frequencies,
+ * RM rule and flags) are marched two at a time, computing the part of the
+ * field that depends on position only once (the batched evaluation of
+ * Sec. 1).  Each set's results equal its one-set results to FP32 rounding.
+ * synax_batch_plan_n_pairs: the number of such items in a plan.
+ * synax_set_batch_pairing: whether plans created afterwards in this process
+ * form them (1, the default) or march every set alone (0); SYNAX_EINVAL
+ * otherwise.  A tuning and comparison switch, like synax_set_lanes_per_ray. */
+int synax_batch_plan_n_pairs(const synax_batch_plan* plan);
+int synax_set_batch_pairing(int on);
 
 /* Device-resident parameters, for samplers that keep theta on the GPU.
  * synax_batch_bind fixes the seeds (targets in chi^2 mode), sigma and the

@@ -103,6 +103,8 @@ SIGNATURES = {
                                      ctypes.c_void_p]),
     "synax_batch_plan_n_sets": (ctypes.c_int, [ctypes.c_void_p]),
     "synax_batch_plan_n_theta": (ctypes.c_int, [ctypes.c_void_p]),
+    "synax_batch_plan_n_pairs": (ctypes.c_int, [ctypes.c_void_p]),
+    "synax_set_batch_pairing": (ctypes.c_int, [ctypes.c_int]),
     "synax_batch_bind": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                         ctypes.c_void_p]),

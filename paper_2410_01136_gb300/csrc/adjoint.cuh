@@ -231,6 +231,8 @@ __device__ __forceinline__ void reverse_lane_pair(const MapParams<float>& P, con
     const float q = P.q, w_own = P.w_own;
     const float half_p1 = 2.0f * q + 2.0f;
     const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
+    FlatZ fz{false, 0.0f, 0.0f};
+    if constexpr (MODEL == SYNAX_MODEL_WMAP) fz = flat_z_of(P, nd);
     float s8 = 0.f, s9 = 0.f, s10 = 0.f, s11a = 0.f, s11b = 0.f, s12 = 0.f, s13 = 0.f, s14 = 0.f, s15 = 0.f;
     float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f, w6 = 0.f, w7 = 0.f;   // WMAP-type
     float2 nh = make_float2(float(n1 - 1) + 0.5f, float(n1 - 2) + 0.5f);     // n + 1/2, exact
@@ -249,7 +251,7 @@ __device__ __forceinline__ void reverse_lane_pair(const MapParams<float>& P, con
             trk.step_pair(-1, ab);
             pair2::jf12_eval<true>(m, s_arms, x, y, z, aa, ab, B, N0, ne, &lc);
         } else {
-            pair2::wmap_eval<true>(m, x, y, z, B, N0, ne, &lw);
+            pair2::wmap_eval<true>(m, x, y, z, B, N0, ne, fz, &lw);
         }
 
         // emission (Eq. 2, 5, 8) and RM integrand (Eq. 7), as the forward pair march
@@ -538,6 +540,8 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
             if constexpr (MODEL == SYNAX_MODEL_GRID) grid_ray_init<R>(P, L, nd, n0, dr, dr_lo, gr);
             auto* const gg = live ? GridGradPtr<R>::get(A) : nullptr;   // idle segments scatter nothing
             const R q = P.q;
+            FlatZ fzr{false, 0.0f, 0.0f};
+            if constexpr (sizeof(R) == 4) fzr = flat_z_of(P, nd);
             R nh = R(n1 - 1) + R(0.5);                  // n + 1/2, exact
             for (int n = n1 - 1; n >= n0; --n, nh -= R(1)) {
                 const R t = fma(nh, dr, nh * dr_lo);
@@ -550,6 +554,7 @@ __device__ __forceinline__ void adjoint_cta(const MapParams<R>& P, const AdjPara
                     else ac = trk.coord(x, y, F::sqrt(x * x + y * y));
                 }
                 FieldLocal<R> loc;
+                set_flat_z<R>(loc, fzr);
                 if constexpr (MODEL == SYNAX_MODEL_GRID) {
                     R fx, fy, fz;
                     const int base = grid_locate_ray<R>(P, gr, n, fx, fy, fz);

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -19,8 +20,8 @@
 #include "params.cuh"
 
 namespace synax {
-int batch_kernels_jf12(int nf, int lpr, BatchKernels* out);
-int batch_kernels_wmap(int nf, int lpr, BatchKernels* out);
+int batch_kernels_jf12(int nf, BatchKernels* out);
+int batch_kernels_wmap(int nf, BatchKernels* out);
 }  // namespace synax
 
 using namespace synax;
@@ -30,20 +31,22 @@ struct synax_batch_plan {
     int n_sets = 0;
     int model = 0;
     int nf = 0;        // frequency-count variant of the kernels
-    int lpr = 32;
-    int rays = 8;
+    int lpr = 32;      // lanes per ray of the largest share of the samples (plan info)
     int grid = 0;
+    int n_items = 0;
+    int n_pairs = 0;
     int n_theta = 0;
     long long n_tiles = 0;
     BatchKernels kern{};
     std::vector<synax_problem> probs;
     std::vector<long long> npix;
-    std::vector<int> order;          // processing position -> set
-    std::vector<long long> begin;    // processing position -> first tile
-    std::vector<long long> pos_of;   // set -> processing position
+    std::vector<BatchItem> items;    // processing order
+    std::vector<long long> begin;    // item -> first tile (n_items + 1 entries)
+    std::vector<long long> row_of;   // set -> its first partial-gradient row
+    std::vector<long long> tiles_of; // set -> its tiles (= rows)
     BatchSet* d_sets = nullptr;
     long long* d_begin = nullptr;
-    int* d_order = nullptr;
+    BatchItem* d_items = nullptr;
     unsigned long long* d_counter = nullptr;
     unsigned long long* d_done = nullptr;
     unsigned long long* d_done_ns = nullptr;
@@ -68,6 +71,9 @@ struct synax_batch_plan {
 
 namespace {
 
+// Process-wide: whether new plans pair sets of one geometry (synax_set_batch_pairing).
+std::atomic<int> g_batch_pairing{1};
+
 void plan_free(synax_batch_plan* p) {
     if (!p) return;
     if (p->pending && p->done) cudaEventSynchronize(p->done);
@@ -82,7 +88,7 @@ void plan_free(synax_batch_plan* p) {
     if (p->cap) cudaStreamDestroy(p->cap);
     cudaFree(p->d_sets);
     cudaFree(p->d_begin);
-    cudaFree(p->d_order);
+    cudaFree(p->d_items);
     cudaFree(p->d_counter);
     cudaFree(p->d_done);
     cudaFree(p->d_done_ns);
@@ -125,7 +131,8 @@ int capture_graph_dev(synax_batch_plan* p, const double* theta) {
     cudaMemsetAsync(p->d_done, 0, sizeof(unsigned long long) * (size_t)p->n_sets, p->cap);
     int n_sets = p->n_sets;
     long long n_tiles = p->n_tiles;
-    void* args[] = {&p->d_sets, &p->d_begin, &p->d_order, &n_sets, &n_tiles, &p->d_counter,
+    int n_items = p->n_items;
+    void* args[] = {&p->d_sets, &p->d_begin, &p->d_items, &n_items, &n_sets, &n_tiles, &p->d_counter,
                     &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0, &p->checked, &p->status};
     cudaLaunchKernel(p->kern.batch, dim3(p->grid), dim3(kAdjThreads), args, 0, p->cap);
     void* rargs[] = {&p->d_sets, &p->d_partial};
@@ -147,7 +154,8 @@ int capture_graph(synax_batch_plan* p) {
     cudaMemsetAsync(p->d_done, 0, sizeof(unsigned long long) * (size_t)p->n_sets, p->cap);
     int n_sets = p->n_sets;
     long long n_tiles = p->n_tiles;
-    void* args[] = {&p->d_sets, &p->d_begin, &p->d_order, &n_sets, &n_tiles, &p->d_counter,
+    int n_items = p->n_items;
+    void* args[] = {&p->d_sets, &p->d_begin, &p->d_items, &n_items, &n_sets, &n_tiles, &p->d_counter,
                     &p->d_partial, &p->d_done, &p->d_done_ns, &p->d_t0, &p->checked, &p->status};
     cudaLaunchKernel(p->kern.batch, dim3(p->grid), dim3(kAdjThreads), args, 0, p->cap);
     void* rargs[] = {&p->d_sets, &p->d_partial};
@@ -192,38 +200,77 @@ int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_p
     p->probs.assign(sets, sets + n_sets);
     p->npix = npix;
 
-    // lanes per ray from the tuning table at the ensemble's sample-weighted step count
-    long long tot_rays = 0;
-    double wsteps = 0.0, wsum = 0.0;
-    for (int s = 0; s < n_sets; ++s) {
-        tot_rays += npix[s];
-        wsteps += (double)npix[s] * sets[s].n_steps * sets[s].n_steps;
-        wsum += (double)npix[s] * sets[s].n_steps;
-    }
-    p->lpr = lanes_per_ray((int)std::lround(wsteps / wsum), tot_rays);
-    p->rays = kAdjThreads / p->lpr;
-    int rc = model == SYNAX_MODEL_JF12 ? batch_kernels_jf12(p->nf, p->lpr, &p->kern)
-                                       : batch_kernels_wmap(p->nf, p->lpr, &p->kern);
+    int rc = model == SYNAX_MODEL_JF12 ? batch_kernels_jf12(p->nf, &p->kern) : batch_kernels_wmap(p->nf, &p->kern);
     if (rc != SYNAX_OK) { plan_free(p); return rc; }
     p->n_theta = p->kern.n_theta;
 
-    // tile order: most steps per ray first (longest-processing-time order)
-    p->order.resize(n_sets);
-    std::iota(p->order.begin(), p->order.end(), 0);
-    std::stable_sort(p->order.begin(), p->order.end(), [&](int a, int b) {
-        if (sets[a].n_steps != sets[b].n_steps) return sets[a].n_steps > sets[b].n_steps;
-        return npix[a] > npix[b];
-    });
-    p->begin.resize(n_sets + 1);
-    p->pos_of.resize(n_sets);
-    long long t = 0;
-    for (int k = 0; k < n_sets; ++k) {
-        p->begin[k] = t;
-        p->pos_of[p->order[k]] = k;
-        t += (npix[p->order[k]] + p->rays - 1) / p->rays;
+    // work items: sets of one ray geometry are paired (two-set items), the
+    // rest run alone; each item takes the tuned lane width of its step count
+    // and map size
+    std::vector<int> lpr_of(n_sets);
+    for (int s = 0; s < n_sets; ++s) lpr_of[s] = lanes_per_ray(sets[s].n_steps, npix[s]);
+    std::vector<int> idx(n_sets);
+    std::iota(idx.begin(), idx.end(), 0);
+    auto geo_less = [&](int a, int b) {
+        const synax_problem &A = sets[a], &B = sets[b];
+        if (A.nside != B.nside) return A.nside < B.nside;
+        if (A.n_steps != B.n_steps) return A.n_steps < B.n_steps;
+        if (A.pix_begin != B.pix_begin) return A.pix_begin < B.pix_begin;
+        if (npix[a] != npix[b]) return npix[a] < npix[b];
+        return std::memcmp(&A.r_max_kpc, &B.r_max_kpc, sizeof(double) * 7) < 0;
+    };
+    auto same_geo = [&](int a, int b) {
+        const synax_problem &A = sets[a], &B = sets[b];
+        return A.nside == B.nside && A.n_steps == B.n_steps && A.pix_begin == B.pix_begin && npix[a] == npix[b] &&
+               A.r_max_kpc == B.r_max_kpc && A.flags == B.flags && A.rm_rule == B.rm_rule &&
+               std::memcmp(A.box_kpc, B.box_kpc, sizeof(A.box_kpc)) == 0 &&
+               std::memcmp(A.obs_kpc, B.obs_kpc, sizeof(A.obs_kpc)) == 0 &&
+               std::memcmp(A.freq_hz, B.freq_hz, sizeof(double) * (size_t)A.n_freq) == 0 && lpr_of[a] == lpr_of[b];
+    };
+    std::stable_sort(idx.begin(), idx.end(), geo_less);
+    std::vector<BatchItem> items;
+    for (size_t k = 0; k < idx.size();) {
+        if (g_batch_pairing.load() && k + 1 < idx.size() && same_geo(idx[k], idx[k + 1])) {
+            items.push_back(BatchItem{idx[k], idx[k + 1], lpr_of[idx[k]], 0});
+            k += 2;
+        } else {
+            items.push_back(BatchItem{idx[k], -1, lpr_of[idx[k]], 0});
+            k += 1;
+        }
     }
-    p->begin[n_sets] = t;
+    // processing order: most steps per ray first (longest-processing-time
+    // order), then the larger maps
+    std::stable_sort(items.begin(), items.end(), [&](const BatchItem& a, const BatchItem& b) {
+        if (sets[a.a].n_steps != sets[b.a].n_steps) return sets[a.a].n_steps > sets[b.a].n_steps;
+        return npix[a.a] > npix[b.a];
+    });
+    p->items = items;
+    p->n_items = (int)items.size();
+    p->begin.assign(items.size() + 1, 0);
+    p->row_of.assign(n_sets, 0);
+    p->tiles_of.assign(n_sets, 0);
+    long long t = 0, rows = 0;
+    std::vector<double> samples_at(33, 0.0);
+    for (size_t k = 0; k < items.size(); ++k) {
+        const BatchItem& it = items[k];
+        const long long rays = kAdjThreads / it.lpr;
+        const long long nt = (npix[it.a] + rays - 1) / rays;
+        p->begin[k] = t;
+        t += nt;
+        for (int s : {it.a, it.b}) {
+            if (s < 0) continue;
+            p->row_of[s] = rows;
+            p->tiles_of[s] = nt;
+            rows += nt;
+            samples_at[it.lpr] += (double)npix[s] * sets[s].n_steps;
+        }
+        if (it.b >= 0) ++p->n_pairs;
+    }
+    p->begin[items.size()] = t;
     p->n_tiles = t;
+    p->lpr = 8;
+    for (int l : {16, 32})
+        if (samples_at[l] > samples_at[p->lpr]) p->lpr = l;
 
     int per_sm = 0, sms = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->kern.batch, kAdjThreads, 0);
@@ -231,10 +278,10 @@ int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_p
     if (err != cudaSuccess || per_sm < 1) { plan_free(p); return record_cuda_error((int)(err ? err : cudaErrorInvalidValue)); }
     p->grid = (int)std::min<long long>((long long)per_sm * sms, p->n_tiles);
 
-    const size_t part_bytes = sizeof(double) * (size_t)p->n_tiles * (size_t)(p->n_theta + 1);
+    const size_t part_bytes = sizeof(double) * (size_t)rows * (size_t)(p->n_theta + 1);
     bool ok = cudaMalloc(&p->d_sets, sizeof(BatchSet) * n_sets) == cudaSuccess &&
-              cudaMalloc(&p->d_begin, sizeof(long long) * (n_sets + 1)) == cudaSuccess &&
-              cudaMalloc(&p->d_order, sizeof(int) * n_sets) == cudaSuccess &&
+              cudaMalloc(&p->d_begin, sizeof(long long) * (p->n_items + 1)) == cudaSuccess &&
+              cudaMalloc(&p->d_items, sizeof(BatchItem) * p->n_items) == cudaSuccess &&
               cudaMalloc(&p->d_counter, sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&p->d_done, sizeof(unsigned long long) * n_sets) == cudaSuccess &&
               cudaMalloc(&p->d_done_ns, sizeof(unsigned long long) * n_sets) == cudaSuccess &&
@@ -243,8 +290,8 @@ int synax_batch_plan_create(const synax_problem* sets, int n_sets, synax_batch_p
               cudaMallocHost(&p->h_sets, sizeof(BatchSet) * n_sets) == cudaSuccess;
     if (!ok) { cudaGetLastError(); plan_free(p); return SYNAX_ENOMEM; }
     std::memset(p->h_sets, 0, sizeof(BatchSet) * n_sets);
-    ok = cudaMemcpy(p->d_begin, p->begin.data(), sizeof(long long) * (n_sets + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(p->d_order, p->order.data(), sizeof(int) * n_sets, cudaMemcpyHostToDevice) == cudaSuccess &&
+    ok = cudaMemcpy(p->d_begin, p->begin.data(), sizeof(long long) * (p->n_items + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->d_items, p->items.data(), sizeof(BatchItem) * p->n_items, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemset(p->d_done_ns, 0, sizeof(unsigned long long) * n_sets) == cudaSuccess &&
          cudaMemset(p->d_t0, 0, sizeof(unsigned long long)) == cudaSuccess &&
          cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) == cudaSuccess &&
@@ -292,9 +339,8 @@ int synax_batch_run(synax_batch_plan* p, const double* thetas, const void* const
         d.maps = maps_dev ? (float*)maps_dev[s] : nullptr;
         d.grad = grads_dev + (size_t)s * p->n_theta;
         d.chi2 = chi2_dev ? chi2_dev + s : nullptr;
-        const long long k = p->pos_of[s];
-        d.tile_begin = p->begin[k];
-        d.n_tiles = p->begin[k + 1] - p->begin[k];
+        d.tile_begin = p->row_of[s];
+        d.n_tiles = p->tiles_of[s];
     }
     if (!p->exec) {
         const int rc = capture_graph(p);
@@ -377,9 +423,8 @@ int synax_batch_bind(synax_batch_plan* p, const void* const* seeds_dev, int vjp,
         d.maps = maps_dev ? (float*)maps_dev[s] : nullptr;
         d.grad = grads_dev + (size_t)s * p->n_theta;
         d.chi2 = chi2_dev ? chi2_dev + s : nullptr;
-        const long long k = p->pos_of[s];
-        d.tile_begin = p->begin[k];
-        d.n_tiles = p->begin[k + 1] - p->begin[k];
+        d.tile_begin = p->row_of[s];
+        d.n_tiles = p->tiles_of[s];
         for (int f = 0; f < p->probs[s].n_freq; ++f) freq[(size_t)s * SYNAX_MAX_FREQ + f] = p->probs[s].freq_hz[f];
         n0n[s] = observer_n0_norm(p->probs[s]);
     }
@@ -410,6 +455,13 @@ int synax_batch_run_device(synax_batch_plan* p, const double* theta_dev, void* s
 }
 
 int synax_batch_plan_n_theta(const synax_batch_plan* p) { return p ? p->n_theta : 0; }
+int synax_batch_plan_n_pairs(const synax_batch_plan* p) { return p ? p->n_pairs : 0; }
+
+int synax_set_batch_pairing(int on) {
+    if (on != 0 && on != 1) return SYNAX_EINVAL;
+    g_batch_pairing.store(on);
+    return SYNAX_OK;
+}
 int synax_batch_plan_n_sets(const synax_batch_plan* p) { return p ? p->n_sets : 0; }
 
 void synax_batch_plan_destroy(synax_batch_plan* p) { plan_free(p); }

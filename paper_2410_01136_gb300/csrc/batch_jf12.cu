@@ -2,7 +2,7 @@
 #include "batch.cuh"
 
 namespace synax {
-int batch_kernels_jf12(int nf, int lpr, BatchKernels* out) {
-    return batch_kernels_for<SYNAX_MODEL_JF12>(nf, lpr, out);
+int batch_kernels_jf12(int nf, BatchKernels* out) {
+    return batch_kernels_for<SYNAX_MODEL_JF12>(nf, out);
 }
 }  // namespace synax

@@ -2,7 +2,7 @@
 #include "batch.cuh"
 
 namespace synax {
-int batch_kernels_wmap(int nf, int lpr, BatchKernels* out) {
-    return batch_kernels_for<SYNAX_MODEL_WMAP>(nf, lpr, out);
+int batch_kernels_wmap(int nf, BatchKernels* out) {
+    return batch_kernels_for<SYNAX_MODEL_WMAP>(nf, out);
 }
 }  // namespace synax

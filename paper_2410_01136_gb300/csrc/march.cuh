@@ -700,7 +700,41 @@ struct FieldLocal {
     R gfx, gfy, gfz;     // fractional position in the cell
     // stacked WMAP: cos/sin of each component's psi and chi
     R kcp[4], ksp[4], kcc[4], ksc[4];
+    // input set by the FP32 marches before eval: on a ray of constant z (the
+    // HEALPix equator ring, n_z = 0) the vertical n_e profile sech^2 z is the
+    // same at every sample, so its FP32 rounding would be a coherent relative
+    // bias of the RM (Eq. 7) over the whole ray; there it is taken from a
+    // per-ray FP64 evaluation kept as hi + lo (flat_z_of)
+    bool flat_z = false;
+    R zc_hi = R(0), zc_lo = R(0);
 };
+
+// sech^2 of the observer's z in FP64, as hi + lo, for a ray of constant z
+// (direction with zero z component in double-float); flat = false otherwise.
+struct FlatZ {
+    bool flat;
+    float hi, lo;
+};
+__device__ __forceinline__ FlatZ flat_z_of(const MapParams<float>& P, const ff* nd) {
+    FlatZ r{false, 0.0f, 0.0f};
+    if (nd[2].hi == 0.0f && nd[2].lo == 0.0f) {
+        const double z = (double)P.obs[2] + (double)P.obs_lo[2];
+        const double c = ::cosh(z);
+        const double Z = 1.0 / (c * c);
+        r.flat = true;
+        r.hi = (float)Z;
+        r.lo = (float)(Z - (double)r.hi);
+    }
+    return r;
+}
+template <typename R>
+__device__ __forceinline__ void set_flat_z(FieldLocal<R>& loc, const FlatZ& fz) {
+    if constexpr (sizeof(R) == 4) {
+        loc.flat_z = fz.flat;
+        loc.zc_hi = fz.hi;
+        loc.zc_lo = fz.lo;
+    }
+}
 
 template <int MODEL> struct Model;
 
@@ -755,7 +789,8 @@ template <> struct Model<SYNAX_MODEL_WMAP> {
         B[2] = amp * sc;
         const R n0u = cr_density<R>(m[mc::W_N0U], rho, az);
         N0 = m[mc::W_N0OBS] * n0u;
-        const R neu = F::exp(-F::mulc(rho, 0.05)) * sech2;
+        const R er = F::exp(-F::mulc(rho, 0.05));
+        const R neu = loc.flat_z ? F::mul_hl(er, loc.zc_hi, loc.zc_lo) : er * sech2;
         ne = F::mul_hl(neu, m[mc::W_NE0], m[mc::W_NE0_LO]);
         loc.c = c; loc.s = s; loc.az = az; loc.rho = rho;
         loc.env = env; loc.cpsi = cp; loc.spsi = sp; loc.cchi = cc; loc.schi = sc;
@@ -903,7 +938,8 @@ template <> struct Model<SYNAX_MODEL_WMAP_STACK> {
         B[2] = comp[0][2] + comp[1][1] + comp[2][0] + comp[3][2];
         const R n0u = cr_density<R>(m[mc::S_N0U], rho, az);
         N0 = m[mc::S_N0OBS] * n0u;
-        const R neu = F::exp(-F::mulc(rho, 0.05)) * (R(4) * e2 * inv1 * inv1);
+        const R er = F::exp(-F::mulc(rho, 0.05));
+        const R neu = loc.flat_z ? F::mul_hl(er, loc.zc_hi, loc.zc_lo) : er * (R(4) * e2 * inv1 * inv1);
         ne = F::mul_hl(neu, m[mc::S_NE0], m[mc::S_NE0_LO]);
         loc.c = c; loc.s = s; loc.lnr8 = lnr8; loc.thz = th; loc.in_range = in_range ? R(1) : R(0);
         loc.n0_unit = n0u; loc.ne_unit = neu;
@@ -1089,7 +1125,8 @@ __device__ __forceinline__ void grid_eval(const MapParams<R>& P, GridCell<R>& gc
     const R inv1 = F::rcp_nr(R(1) + e2);
     const R n0u = cr_density<R>(P.m[mc::G_N0U], rho, az);
     N0 = P.m[mc::G_N0OBS] * n0u;
-    const R neu = F::exp(-F::mulc(rho, 0.05)) * (R(4) * e2 * inv1 * inv1);
+    const R er = F::exp(-F::mulc(rho, 0.05));
+    const R neu = loc.flat_z ? F::mul_hl(er, loc.zc_hi, loc.zc_lo) : er * (R(4) * e2 * inv1 * inv1);
     ne = F::mul_hl(neu, P.m[mc::G_NE0], P.m[mc::G_NE0_LO]);
     loc.n0_unit = n0u;
     loc.ne_unit = neu;
@@ -1339,7 +1376,7 @@ struct WmapLoc2 {
 // instead of a branch; with LOC also the gradient's intermediates.
 template <bool LOC = false>
 __device__ __forceinline__ void wmap_eval(const float* m, float2 x, float2 y, float2 z, float2 B[3], float2& N0,
-                                          float2& ne, WmapLoc2* lc = nullptr) {
+                                          float2& ne, const FlatZ& fz, WmapLoc2* lc = nullptr) {
     const float2 rho2 = fma2(x, x, mul2(y, y));
     const float2 rho = f2(__fsqrt_rn(rho2.x), __fsqrt_rn(rho2.y));
     const float2 rr = rcp_nr(rho);
@@ -1380,7 +1417,9 @@ __device__ __forceinline__ void wmap_eval(const float* m, float2 x, float2 y, fl
     const float2 eR = f2(ex2_approx(er.x), ex2_approx(er.y));
     const float2 n0u = mul2(dup2(m[mc::W_N0U]), mul2(eR, mul2(mul2(dup2(4.0f), ec), mul2(iv, iv))));
     N0 = mul2(dup2(m[mc::W_N0OBS]), n0u);
-    const float2 neu = mul2(expf2(neg2(mulc(rho, 0.05))), sech2);
+    const float2 ne_r = expf2(neg2(mulc(rho, 0.05)));
+    // (a ray of constant z: sech^2 z from the per-ray FP64 value, see FieldLocal)
+    const float2 neu = fz.flat ? fma2(ne_r, dup2(fz.hi), mul2(ne_r, dup2(fz.lo))) : mul2(ne_r, sech2);
     ne = fma2(neu, dup2(m[mc::W_NE0]), mul2(neu, dup2(m[mc::W_NE0_LO])));      // ne0 as hi + lo
     if constexpr (LOC) {
         lc->c = c;
@@ -1418,6 +1457,8 @@ __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const
     }
     float2 nh = make_float2(float(n0) + 0.5f, float(n0) + 1.5f);     // n + 1/2, exact
     const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
+    FlatZ fz{false, 0.0f, 0.0f};
+    if constexpr (MODEL == SYNAX_MODEL_WMAP) fz = flat_z_of(P, nd);
     for (int n = n0; n < n1; n += 2, nh = add2(nh, dup2(2.0f))) {
         // the second sample of an odd tail is a placeholder whose terms are zeroed
         const float live_b = n + 1 < n1 ? 1.0f : 0.0f;
@@ -1432,7 +1473,7 @@ __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const
             trk.step_pair(+1, ab);
             pair2::jf12_eval(P.m, s_arms, x, y, z, aa, ab, B, N0, ne);
         } else {
-            pair2::wmap_eval(P.m, x, y, z, B, N0, ne);
+            pair2::wmap_eval(P.m, x, y, z, B, N0, ne, fz);
         }
         // emission (Eq. 2, 5, 8) and RM integrand (Eq. 7), element-wise as emit()
         float2 v = mul2(B[0], dup2(L.n[0]));
@@ -1549,6 +1590,8 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
         if (n0 < n1) grid_ray_init<R>(P, L, nd, n0, dr, dr_lo, gr);
     }
     R nh = R(n0) + R(0.5);                              // n + 1/2, exact
+    FlatZ fzr{false, 0.0f, 0.0f};
+    if constexpr (sizeof(R) == 4) fzr = flat_z_of(P, nd);
 #pragma unroll 2
     for (int n = n0; n < n1; ++n, nh += R(1)) {
         const R t = fma(nh, dr, nh * dr_lo);            // (n + 1/2) dr, dr as hi + lo
@@ -1562,6 +1605,7 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
             else ac = trk.coord(x, y, M<R>::sqrt(x * x + y * y));
         }
         FieldLocal<R> loc;
+        set_flat_z<R>(loc, fzr);
         if constexpr (MODEL == SYNAX_MODEL_GRID) {
             R fx, fy, fz;
             const int base = grid_locate_ray<R>(P, gr, n, fx, fy, fz);
