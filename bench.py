@@ -354,6 +354,21 @@ def bench_batch(sx, inputs, torch, dev, n_runs: int = 3, sets=None, name=None) -
     ms_batch = e0.elapsed_time(e1) / n_runs
     lat = plan.latencies()
     plan.close()
+    # the same ensemble with every set marched alone (no two-set items)
+    sx.set_batch_pairing(False)
+    try:
+        plan1 = sx.BatchPlan(sets)
+        plan1.run(targets=targets, sigma=0.5, grads=grads, chi2=chi2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n_runs):
+            plan1.run(targets=targets, sigma=0.5, grads=grads, chi2=chi2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_unpaired = e0.elapsed_time(e1) / n_runs
+        plan1.close()
+    finally:
+        sx.set_batch_pairing(True)
     ws = torch.empty(max(sx.adjoint_workspace_bytes(p) for p in sets), dtype=torch.uint8, device=dev)
     for p, t in zip(sets[:4], targets[:4]):
         sx.adjoint(p, target=t, sigma=0.5, workspace=ws)
@@ -375,6 +390,9 @@ def bench_batch(sx, inputs, torch, dev, n_runs: int = 3, sets=None, name=None) -
         "sequential_ms": ms_seq,
         "sequential_maps_grad_per_s": len(sets) / (ms_seq * 1e-3),
         "speedup_vs_sequential": ms_seq / ms_batch,
+        "unpaired_ms": ms_unpaired,
+        "pairing_note": "the plan marches sets of one ray geometry two at a time, sharing their position-only "
+                        "field work; unpaired_ms is the same ensemble with every set alone",
         "plan": info,
     }
 

@@ -19,7 +19,7 @@ from . import _native
 from ._native import (SYNAX_F64, SynaxError, check, lib, problem_struct)
 
 __all__ = ["forward", "adjoint", "adjoint_grid", "adjoint_grid_workspace_bytes", "grid_sample", "adam_step", "GridFit", "HMC", "eval_fields", "BatchPlan", "adjoint_workspace_bytes", "SynaxMaps", "inputs", "build",
-           "SynaxError", "last_status", "pipe_peaks", "set_lanes_per_ray"]
+           "SynaxError", "last_status", "pipe_peaks", "set_lanes_per_ray", "set_batch_pairing"]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -282,7 +282,8 @@ class BatchPlan:
         grid = ctypes.c_int()
         check(lib().synax_batch_plan_info(self._h, ctypes.byref(nt), ctypes.byref(lpr), ctypes.byref(grid)),
               "synax_batch_plan_info")
-        return {"n_tiles": nt.value, "lanes_per_ray": lpr.value, "grid": grid.value}
+        return {"n_tiles": nt.value, "lanes_per_ray": lpr.value, "grid": grid.value,
+                "n_pairs": lib().synax_batch_plan_n_pairs(self._h)}
 
     def run(self, targets=None, seeds=None, sigma: float = 1.0, thetas=None, maps=None, grads=None,
             chi2=None, stream=None):
@@ -380,6 +381,12 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def set_batch_pairing(on: bool) -> None:
+    """Whether batch plans created afterwards march sets of one ray geometry
+    two at a time (the default) or every set alone."""
+    check(lib().synax_set_batch_pairing(1 if on else 0), "synax_set_batch_pairing")
 
 
 def set_lanes_per_ray(lanes: int, n_steps_min: int = -1) -> None:

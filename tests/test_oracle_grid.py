@@ -144,3 +144,33 @@ def test_grid_field_recipe_is_seeded():
     c = I.grid_field(n=(8, 6, 4), seed=22)
     assert a.shape == (4, 6, 8, 3)
     assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_g7_one_ulp_response_is_a_linear_conditioning_measure():
+    """The FP32 floor of the grid tests (tests/parity.py) is the oracle's
+    response to moving every grid value by one float32 ulp.  Pinned here as a
+    first-order (linear) response: two ulps in the same directions move
+    Q + iU twice as far (to 10 %), the response is far below the unrotated
+    polarised intensity P0 = Pi I (Pi = (p+1)/(p+7/3), the polarised fraction
+    of Eq. 2 and 5; below 1e-4 P0) on every pixel, and at 2.4 GHz (the grid workload's
+    frequency) 16 times the response stays below 1e-4 |P| on every pixel, so
+    the floor acts only where the Faraday rotation depolarises."""
+    import oracle
+    from paper_2410_01136_gb300 import inputs
+    from tests.parity import ulp_perturbed_grid
+    oracle.build()
+    prob = inputs.grid_problem(nside=4, n_steps=48, freq_hz=(408e6, 2.4e9), n=(12, 10, 6))
+    prob = prob.replace(grid=np.asarray(prob.grid, dtype=np.float32).astype(np.float64))
+    ref = oracle.forward(prob)
+    P = ref[:, 1] + 1j * ref[:, 2]
+    d1 = oracle.forward(prob.replace(grid=ulp_perturbed_grid(prob.grid, 5, 1)))
+    d2 = oracle.forward(prob.replace(grid=ulp_perturbed_grid(prob.grid, 5, 2)))
+    r1 = (d1[:, 1] + 1j * d1[:, 2]) - P
+    r2 = (d2[:, 1] + 1j * d2[:, 2]) - P
+    big = np.abs(r1) > 1e-3 * np.abs(r1).max()
+    np.testing.assert_allclose(r2[big], 2 * r1[big], rtol=0.1, atol=0)
+    p = prob.theta[1]
+    P0 = (p + 1) / (p + 7 / 3) * ref[:, 0]
+    assert np.all(np.abs(r1) <= 1e-4 * P0)
+    den = np.maximum(np.abs(P[1]), 1e-2 * np.median(np.abs(P[1])))
+    assert np.all(16 * np.abs(r1[1]) < 1e-4 * den)
