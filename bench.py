@@ -77,6 +77,8 @@ def parse():
                     help="run only the grid-model measurement (no interpolation study) and print its JSON")
     ap.add_argument("--grid-runs", type=int, default=10, help="timed steps of the grid-model measurement")
     ap.add_argument("--only-hmc", action="store_true", help="run only the HMC sampling measurement")
+    ap.add_argument("--only-batch-low-res", action="store_true",
+                    help="run only the 256-chain Nside-16 batch measurement and print its JSON (a profiling aid)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the learned surrogate")
     ap.add_argument("--surrogate-steps", type=int, default=20000, help="Adam steps of the surrogate training")
     ap.add_argument("--surrogate-maps", type=int, default=50000, help="training maps of the surrogate")
@@ -777,6 +779,13 @@ def run_synax(args):
     if args.only_hmc:
         if rank == 0:
             print(json.dumps({"hmc": bench_hmc(sx, inputs, torch, dev)}), flush=True)
+        return
+    if args.only_batch_low_res:
+        tune.load_or_tune()
+        chains = [p.replace(nside=16, n_steps=256) for p in inputs.config4()]
+        if rank == 0:
+            print(json.dumps({"batch_low_res": bench_batch(sx, inputs, torch, dev, n_runs=3, sets=chains,
+                                                           name="256 chains, Nside 16, 256 steps")}), flush=True)
         return
     if args.only_grid:
         if rank == 0:

@@ -196,10 +196,8 @@ __device__ __forceinline__ void wmap_eval2(const PairConsts& pc, const WmapGeo& 
     const float2 psi = in ? fma2(lds2(pc.m[mc::W_PSI1]), dup2(g.lnr8), lds2(pc.m[mc::W_PSI0])) : dup2(0.0f);
     const float2 chi = in ? mul2(lds2(pc.m[mc::W_CHI0]), dup2(g.thz)) : dup2(0.0f);
     float2 sp, cp, sc, cc;
-    sincosf(psi.x, &sp.x, &cp.x);
-    sincosf(psi.y, &sp.y, &cp.y);
-    sincosf(chi.x, &sc.x, &cc.x);
-    sincosf(chi.y, &sc.y, &cc.y);
+    sincos_cw2(psi, sp, cp);
+    sincos_cw2(chi, sc, cc);
     const float2 amp = mul2(lds2(pc.m[mc::W_B0]), dup2(g.env));
     const float2 br = mul2(mul2(amp, cp), cc), bp = mul2(mul2(amp, sp), cc);
     B[0] = add2(fma2(br, dup2(g.c), neg2(mul2(bp, dup2(g.s)))), lds2(pc.m[mc::W_BUX]));
