@@ -29,18 +29,31 @@
 
 namespace synax {
 
-// 128 threads with at most 85 registers each, so that 6 CTAs (24 warps)
-// share an SM (measured: 0.283 ms against 0.304 ms for 256 threads at the
-// natural 96 registers, for the Nside-64, 512-step, 4-frequency map).
-constexpr int kThreads = 128;
-constexpr int kFwdMinBlocks = 6;
+// 128-thread CTAs.  The JF12-type march runs 5 per SM (at most 102
+// registers): measured for the Nside-64, 512-step, 4-frequency map (8 lanes
+// per ray, 3072 CTAs), 5 CTAs per SM (95 registers, 4.04 waves) 0.247 ms;
+// 6 (79 registers, 3.37 waves) 0.250 ms; 7 and 8 (spills) 0.255 and
+// 0.260 ms; 64-thread CTAs at 12 or 14 per SM 0.250 and 0.255 ms.  The other
+// models keep 6 per SM (at most 85 registers), where they were measured.
+// SYNAX_FWD_MIN_BLOCKS / SYNAX_FWD_THREADS override both at build time.
+#ifndef SYNAX_FWD_THREADS
+#define SYNAX_FWD_THREADS 128
+#endif
+constexpr int kThreads = SYNAX_FWD_THREADS;
+template <int MODEL> constexpr int fwd_min_blocks() {
+#ifdef SYNAX_FWD_MIN_BLOCKS
+    return SYNAX_FWD_MIN_BLOCKS;
+#else
+    return MODEL == SYNAX_MODEL_JF12 ? 5 : 6;
+#endif
+}
 
 // LPR lanes march one ray (32, 16 or 8): a CTA of 128 threads handles
 // 128 / LPR rays.  Fewer lanes per ray amortise the per-ray set-up (LOS
 // geometry, arm-tracker anchor, scan, rotation, reductions) over more samples
 // per lane; more lanes give more parallelism for few rays.
 template <int MODEL, int NF, int LPR, typename R>
-__global__ void __launch_bounds__(kThreads, kFwdMinBlocks)
+__global__ void __launch_bounds__(kThreads, fwd_min_blocks<MODEL>())
 k_forward(const MapParams<R> P, R* __restrict__ maps) {
     using Ph = PhaseOps<R>;
     using PT = typename Ph::T;
