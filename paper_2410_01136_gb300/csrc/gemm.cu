@@ -64,14 +64,21 @@ constexpr int gemm_threads() {
 }
 constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
 
-template <int BN>
+template <int BN, int EPI = EPI_F32>
 struct GemmCfg {
-    static constexpr int ST = BN == 256 ? 4 : 6;                       // pipeline stages
+    // The BF16 activations of the GELU and GELU' epilogues leave through TMA
+    // stores from per-warp 32 x 32 staging blocks (8 epilogue warps x 2 KB,
+    // BN = 128); one pipeline stage fewer makes room for them.
+    static constexpr bool BF16_STAGE = BN == 128 && (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_BWD);
+    static constexpr int ST = BN == 256 ? 4 : (BF16_STAGE ? 5 : 6);   // pipeline stages
     static constexpr uint32_t A_BYTES = kGemmBM * kGemmBK * 2;
     static constexpr uint32_t B_BYTES = BN * kGemmBK * 2;
     static constexpr uint32_t TMEM_COLS = 2 * BN;                      // two accumulators
     static constexpr uint32_t STG_BYTES = kGemmBM * 32 * 4;                 // one 128 x 32 FP32 chunk
-    static constexpr size_t SMEM = 1024 + (size_t)ST * (A_BYTES + B_BYTES) + 2 * STG_BYTES + 256;
+    static constexpr uint32_t BF16_BLOCK = 32 * 32 * 2;                     // one warp's 32 x 32 BF16 block
+    static constexpr uint32_t BF16_STG_BYTES = BF16_STAGE ? 8 * BF16_BLOCK : 0;
+    static constexpr size_t SMEM =
+        1024 + (size_t)ST * (A_BYTES + B_BYTES) + 2 * STG_BYTES + BF16_STG_BYTES + 256;
 };
 
 __device__ __forceinline__ bool mbar_wait_clock(uint64_t* bar, uint32_t parity) {
@@ -86,9 +93,38 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// Standard normal CDF Phi(z) = erfc(-z / sqrt 2) / 2 with erfc(x), x >= 0,
+// from Abramowitz & Stegun 7.1.26 (Hastings' rational form; the error of
+// erf is at most 1.5e-7): erfc(x) ~ t P(t) exp(-x^2), t = 1 / (1 + p x).
+// Also returns g = exp(-z^2 / 2), the Gaussian that GELU' needs: one
+// reciprocal and one exponential on the SFU for both.  Phi is off by at most
+// ~1e-7 absolute, far below the BF16 rounding (2^-9 relative) of the
+// activations these feed.
+struct NormalCdf {
+    float Phi, g;
+};
+__device__ __forceinline__ NormalCdf normal_cdf(float z) {
+    const float x = fabsf(z) * 0.70710678118654752f;
+    float t, g;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, x, 1.0f)));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(z * z * -0.72134752044448170f));   // -log2(e) / 2
+    const float P =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                 0.254829592f);
+    const float q = 0.5f * P * g;       // Phi(-|z|)
+    return {z >= 0.0f ? 1.0f - q : q, g};
+}
+__device__ __forceinline__ float gelu_f(float z) { return z * normal_cdf(z).Phi; }
 __device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+    const NormalCdf n = normal_cdf(z);
+    return fmaf(z * 0.39894228040143268f, n.g, n.Phi);   // Phi(z) + z phi(z)
+}
+
+// Two FP32 values rounded to BF16 and packed: lo in bits 0-15, hi in 16-31.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t w;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+    return w;
 }
 
 // 16 per-column values p[col0 .. col0 + 15] (the last valid column repeated
@@ -111,11 +147,15 @@ __device__ __forceinline__ void load16(const float* __restrict__ p, int col0, in
 }
 
 // Epilogue of 16 consecutive columns col0.. of one row (nv of them valid).
-// With zkeep (EPI_BIAS_GELU whose pre-activation goes through the TMA-store
-// staging), the 16 pre-activations are copied there instead of stored.
+// With keep_z (EPI_BIAS_GELU whose pre-activation goes through the TMA-store
+// staging) the 16 pre-activations are copied to zkeep instead of stored; with
+// keep_h the 16 BF16 results go to hkeep (8 packed words) the same way.  The
+// flags are separate from the arrays so that no address is selected at run
+// time and the arrays stay in registers.
 template <int EPI>
 __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float* v, int row, int col0, int nv,
-                                           long long trow, float& sq, float* zkeep = nullptr) {
+                                           long long trow, float& sq, bool keep_z = false, float* zkeep = nullptr,
+                                           bool keep_h = false, uint32_t* hkeep = nullptr) {
     if constexpr (EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC) {
         float* o = ep.out_f32 + (long long)row * ep.ld_f32 + col0;
         float r[16], b[16], sc[16], sh[16];
@@ -167,7 +207,7 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
             r[i] = x;
         }
         if constexpr (EPI == EPI_BIAS_GELU) {
-            if (zkeep) {
+            if (keep_z) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) zkeep[i] = z16[i];
             } else if (ep.out_z) {
@@ -182,26 +222,32 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
                 }
             }
         }
-        // BF16 rounding once; pairs packed into 32-bit words with bit operations
+        // BF16 rounding once, two values per conversion into 32-bit words
         // (no array whose address is taken, so nothing goes to local memory)
-        uint32_t h[16];
+        uint32_t w[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = __bfloat16_as_ushort(__float2bfloat16_rn(r[i]));
+        for (int i = 0; i < 8; ++i) w[i] = pack_bf16x2(r[2 * i], r[2 * i + 1]);
+        if (keep_h) {
+            // the caller stages the 16 values for a TMA store
+#pragma unroll
+            for (int i = 0; i < 8; ++i) hkeep[i] = w[i];
+            return;
+        }
         __nv_bfloat16* o = ep.out_bf16 + (long long)row * ep.ld_bf16 + col0;
         if (nv == 16 && (((uintptr_t)o) & 15) == 0) {
-            reinterpret_cast<uint4*>(o)[0] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16),
-                                                        h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-            reinterpret_cast<uint4*>(o)[1] = make_uint4(h[8] | (h[9] << 16), h[10] | (h[11] << 16),
-                                                        h[12] | (h[13] << 16), h[14] | (h[15] << 16));
+            reinterpret_cast<uint4*>(o)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            reinterpret_cast<uint4*>(o)[1] = make_uint4(w[4], w[5], w[6], w[7]);
         } else {
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-                if (i < nv) o[i] = __ushort_as_bfloat16((unsigned short)h[i]);
+                if (i < nv) o[i] = __ushort_as_bfloat16((unsigned short)(w[i >> 1] >> (16 * (i & 1))));
         }
         if (ep.out_bf16_t) {
 #pragma unroll
             for (int i = 0; i < 16; ++i)
-                if (i < nv) ep.out_bf16_t[(long long)(col0 + i) * ep.ld_t + row] = __ushort_as_bfloat16((unsigned short)h[i]);
+                if (i < nv)
+                    ep.out_bf16_t[(long long)(col0 + i) * ep.ld_t + row] =
+                        __ushort_as_bfloat16((unsigned short)(w[i >> 1] >> (16 * (i & 1))));
         }
     }
 }
@@ -209,15 +255,17 @@ __device__ __forceinline__ void epilogue16(const GemmEpiParams& ep, const float*
 template <int BN, int EPI>
 __global__ void __launch_bounds__(gemm_threads<EPI>(), 1)
 k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            const __grid_constant__ CUtensorMap tmC, int M, int N, int K, GemmEpiParams ep, int* err) {
-    using C = GemmCfg<BN>;
+            const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmD, int M, int N, int K,
+            GemmEpiParams ep, int* err) {
+    using C = GemmCfg<BN, EPI>;
     constexpr int ST = C::ST;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sB = smem + ST * C::A_BYTES;
     uint8_t* sC = sB + ST * C::B_BYTES;          // two FP32 staging chunks (1024-byte aligned)
-    uint64_t* full = (uint64_t*)(sC + 2 * C::STG_BYTES);
+    uint8_t* sD = sC + 2 * C::STG_BYTES;         // BF16 staging blocks (C::BF16_STAGE)
+    uint64_t* full = (uint64_t*)(sD + C::BF16_STG_BYTES);
     uint64_t* empty = full + ST;
     uint64_t* acc_full = empty + ST;      // [2]
     uint64_t* acc_empty = acc_full + 2;   // [2]
@@ -321,7 +369,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int c_lo = ((warp - 2) >> 2) * COLS;
         int j = 0;
         int stg = 0;       // staging chunks used (TMA-store path)
-        int zblk = 0;      // pre-activation blocks stored by this warp (GELU)
+        int zblk = 0;      // staged GELU / GELU' blocks stored by this warp
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             const int buf = j & 1;
             // all EW epilogue warps agree (they share named barriers below):
@@ -401,13 +449,22 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 // The GELU pre-activation (ep.tma_store) goes through this
                 // warp's 4 KB slot of the staging area: 32 rows x 32 columns in
                 // the 128-byte swizzle, one TMA store per block.
+                // The BF16 activations (ep.tma_store_bf16, C::BF16_STAGE) go
+                // through the warp's 2 KB slot of sD: 32 rows x 64 bytes in the
+                // 64-byte swizzle, stored with the pre-activation block.
                 constexpr bool kZStage = EPI == EPI_BIAS_GELU;
+                constexpr bool kBStage = C::BF16_STAGE;
                 const bool zst = kZStage && ep.tma_store;
+                const bool bst = kBStage && ep.tma_store_bf16;
                 uint8_t* zslot = sC + (warp - 2) * 4096;
+                uint8_t* bslot = sD + (warp - 2) * C::BF16_BLOCK;
                 uint32_t ra[16], rb[16];
                 float za[16], zb[16];
+                uint32_t ha[8], hb[8];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) za[i] = zb[i] = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) ha[i] = hb[i] = 0u;
                 tc::tmem_ld16_async(base + (uint32_t)c_lo, ra);
                 tc::tmem_wait_ld();
                 for (int c = c_lo; c < c_lo + COLS; c += 32) {
@@ -417,7 +474,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
                         const int nv = N - (n0 + c) < 16 ? N - (n0 + c) : 16;
-                        epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq, zst ? za : nullptr);
+                        epilogue16<EPI>(ep, v, row, n0 + c, nv, trow, sq, zst, za, bst, ha);
                     }
                     tc::tmem_wait_ld();
                     if (c + 32 < c_lo + COLS) tc::tmem_ld16_async(base + (uint32_t)(c + 32), ra);
@@ -426,26 +483,39 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                         for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(rb[i]);
                         const int nv = N - (n0 + c + 16) < 16 ? N - (n0 + c + 16) : 16;
-                        epilogue16<EPI>(ep, v, row, n0 + c + 16, nv, trow, sq, zst ? zb : nullptr);
+                        epilogue16<EPI>(ep, v, row, n0 + c + 16, nv, trow, sq, zst, zb, bst, hb);
                     }
-                    if constexpr (kZStage) {
-                        if (zst && n0 + c < N) {          // the same for every lane of the warp
-                            // the slot's previous block has been read by its store
+                    if constexpr (kZStage || kBStage) {
+                        if ((zst || bst) && n0 + c < N) {     // the same for every lane of the warp
+                            // the slots' previous blocks have been read by their stores
                             if (lane == 0 && zblk > 0) tc::bulk_wait_read<0>();
                             __syncwarp();
-                            // rows past M hold stale values: the store clips them
+                            // rows past M and columns past N hold stale values: the stores clip them
+                            if (zst) {
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                *reinterpret_cast<float4*>(zslot + lane * 128 + ((j ^ (lane & 7)) << 4)) =
-                                    make_float4(za[4 * j], za[4 * j + 1], za[4 * j + 2], za[4 * j + 3]);
+                                for (int j = 0; j < 4; ++j)
+                                    *reinterpret_cast<float4*>(zslot + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                                        make_float4(za[4 * j], za[4 * j + 1], za[4 * j + 2], za[4 * j + 3]);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                *reinterpret_cast<float4*>(zslot + lane * 128 + (((j + 4) ^ (lane & 7)) << 4)) =
-                                    make_float4(zb[4 * j], zb[4 * j + 1], zb[4 * j + 2], zb[4 * j + 3]);
+                                for (int j = 0; j < 4; ++j)
+                                    *reinterpret_cast<float4*>(zslot + lane * 128 + (((j + 4) ^ (lane & 7)) << 4)) =
+                                        make_float4(zb[4 * j], zb[4 * j + 1], zb[4 * j + 2], zb[4 * j + 3]);
+                            }
+                            if (bst) {
+                                // 64-byte swizzle: 16-byte unit j of row r sits at unit j ^ ((r / 2) % 4)
+                                uint8_t* rp = bslot + lane * 64;
+                                const int sw = (lane >> 1) & 3;
+                                *reinterpret_cast<uint4*>(rp + ((0 ^ sw) << 4)) = make_uint4(ha[0], ha[1], ha[2], ha[3]);
+                                *reinterpret_cast<uint4*>(rp + ((1 ^ sw) << 4)) = make_uint4(ha[4], ha[5], ha[6], ha[7]);
+                                *reinterpret_cast<uint4*>(rp + ((2 ^ sw) << 4)) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
+                                *reinterpret_cast<uint4*>(rp + ((3 ^ sw) << 4)) = make_uint4(hb[4], hb[5], hb[6], hb[7]);
+                            }
                             tc::fence_proxy_async_smem();
                             __syncwarp();
                             if (lane == 0) {
-                                tc::tma_store_2d(&tmC, zslot, n0 + c, m0 + q * 32);
+                                // n0 + c is a multiple of 32: 128 bytes (FP32) and 64 bytes (BF16)
+                                if (zst) tc::tma_store_2d(&tmC, zslot, n0 + c, m0 + q * 32);
+                                if (bst) tc::tma_store_2d(&tmD, bslot, n0 + c, m0 + q * 32);
                                 tc::bulk_commit();
                             }
                             ++zblk;
@@ -464,7 +534,7 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (lane == 0) red[warp - 2] = sq;
         }
         if (threadIdx.x == 64 && stg > 0) tc::bulk_wait_all();   // every TMA store has completed
-        if (lane == 0 && zblk > 0) tc::bulk_wait_all();            // this warp's pre-activation stores
+        if (lane == 0 && zblk > 0) tc::bulk_wait_all();            // this warp's staged GELU stores
     }
     if (!ok) {
         atomicExch(err, 1);
@@ -580,7 +650,7 @@ int sm_count() {
 template <int BN, int EPI>
 cudaError_t set_smem_attr() {
     return cudaFuncSetAttribute(k_gemm_bf16<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)GemmCfg<BN>::SMEM);
+                                (int)GemmCfg<BN, EPI>::SMEM);
 }
 
 template <int EPI>
@@ -605,6 +675,20 @@ int make_out_map(CUtensorMap* map, const void* base, int rows, int cols, int ld,
     return r == CUDA_SUCCESS ? SYNAX_OK : SYNAX_EINVAL;
 }
 
+// 2-D BF16 tensor map of an output [rows][ld], box 32 x 32, 64-byte swizzle.
+int make_bf16_out_map(CUtensorMap* map, const void* base, int rows, int cols, int ld) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return SYNAX_ECUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {32u, 32u};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SYNAX_OK : SYNAX_EINVAL;
+}
+
 template <int BN, int EPI>
 int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K, const GemmEpiParams& ep_in,
                   int* err, cudaStream_t st) {
@@ -624,7 +708,16 @@ int launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, in
     if (EPI == EPI_BIAS_GELU && ep.out_z && ((uintptr_t)ep.out_z & 15) == 0 && (ep.ld_z & 3) == 0 &&
         make_out_map(&mc, ep.out_z, M, N, ep.ld_z, 32) == SYNAX_OK)
         ep.tma_store = 1;
-    k_gemm_bf16<BN, EPI><<<grid, gemm_threads<EPI>(), GemmCfg<BN>::SMEM, st>>>(ma, mb, mc, M, N, K, ep, err);
+    // GELU / GELU': the BF16 activations through per-warp 32 x 32 staging blocks
+    // (not with a transposed copy, which the epilogue writes element by element)
+    CUtensorMap md;
+    std::memset(&md, 0, sizeof md);
+    ep.tma_store_bf16 = 0;
+    if (GemmCfg<BN, EPI>::BF16_STAGE && ep.out_bf16 && !ep.out_bf16_t && ((uintptr_t)ep.out_bf16 & 15) == 0 &&
+        (ep.ld_bf16 & 7) == 0 && make_bf16_out_map(&md, ep.out_bf16, M, N, ep.ld_bf16) == SYNAX_OK)
+        ep.tma_store_bf16 = 1;
+    k_gemm_bf16<BN, EPI><<<grid, gemm_threads<EPI>(), GemmCfg<BN, EPI>::SMEM, st>>>(ma, mb, mc, md, M, N, K, ep,
+                                                                                       err);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
 }

@@ -41,6 +41,7 @@ struct GemmEpiParams {
     const float* shift;          // EPI_AFFINE
     int accumulate;              // EPI_SCALE_ACC
     int tma_store;               // set by gemm_bf16: FP32 output written through TMA stores
+    int tma_store_bf16;          // set by gemm_bf16: GELU / GELU' BF16 output written through TMA stores
     int* status;                 // set by gemm_bf16: the device status word (a timed-out wait reports there)
 };
 

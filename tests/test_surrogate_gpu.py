@@ -157,8 +157,12 @@ def test_adam_update_matches_oracle(torch):
     sur.close()
 
 
-def test_eval_and_vjp_match_oracle(torch):
-    sur, params, lo, hi, _, _ = small(torch, max_eval=50)      # 3 chunks for n = 130
+@pytest.mark.parametrize("width", [128, 320])
+def test_eval_and_vjp_match_oracle(torch, width):
+    """Width 320 takes the 128-column GEMM tiles whose GELU and GELU' epilogues
+    stage their BF16 outputs for TMA stores (three column tiles, the last one
+    half full; 50-row chunks leave the row tile ragged)."""
+    sur, params, lo, hi, _, _ = small(torch, width=width, max_eval=50)      # 3 chunks for n = 130
     mean = np.linspace(2, -2, sur.n_out).astype(np.float32)
     scale = 1.7
     sur.set_normalization(mean, scale)
