@@ -120,12 +120,6 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
     return fmaf(z * 0.39894228040143268f, n.g, n.Phi);   // Phi(z) + z phi(z)
 }
 
-// Two FP32 values rounded to BF16 and packed: lo in bits 0-15, hi in 16-31.
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-    uint32_t w;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
-    return w;
-}
 
 // 16 per-column values p[col0 .. col0 + 15] (the last valid column repeated
 // past nv): four 16-byte loads when the run is whole and aligned.
@@ -757,6 +751,8 @@ int gemm_init() {
     });
     return err == cudaSuccess ? SYNAX_OK : record_cuda_error((int)err);
 }
+
+int device_sm_count() { return sm_count(); }
 
 int gemm_tiles(int M, int N, int K) {
     const int bn = gemm_bn_for(N, K);

@@ -3,10 +3,20 @@
 // fused epilogue.
 #pragma once
 
+#include <cstdint>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace synax {
+
+// Two FP32 values rounded to BF16 (nearest even) and packed into one word:
+// lo in bits 0-15, hi in bits 16-31.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t w;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+    return w;
+}
 
 enum GemmEpi : int {
     EPI_F32 = 0,        // out_f32 = acc
@@ -44,6 +54,9 @@ struct GemmEpiParams {
     int tma_store_bf16;          // set by gemm_bf16: GELU / GELU' BF16 output written through TMA stores
     int* status;                 // set by gemm_bf16: the device status word (a timed-out wait reports there)
 };
+
+// Streaming multiprocessors of the current device (cached per process).
+int device_sm_count();
 
 // Set the kernels' shared-memory attributes (once per process; gemm_bf16
 // calls it too).  Call before capturing a stream that will launch GEMMs.

@@ -208,6 +208,39 @@ __global__ void k_seed_out(const float* __restrict__ g, long long n, float scale
         d[i] = __float2bfloat16_rn(g[i] * scale);
 }
 
+// The same, eight values per item (g and d 16-byte aligned, n8 = n / 8):
+// two 16-byte loads, four paired BF16 roundings, one 16-byte store.  Each
+// thread keeps kSeedUnroll items' loads in flight, so that a small grid (two
+// CTAs per SM) streams at HBM speed: 126 us for the 16384 x 9216 seed.
+constexpr int kSeedUnroll = 4;
+__global__ void __launch_bounds__(256) k_seed_out8(const float4* __restrict__ g, long long n8, float scale,
+                                                   uint4* __restrict__ d) {
+    const long long step = (long long)gridDim.x * blockDim.x * kSeedUnroll;
+    for (long long base = (long long)blockIdx.x * blockDim.x * kSeedUnroll + threadIdx.x; base < n8; base += step) {
+        float4 a[kSeedUnroll], b[kSeedUnroll];
+#pragma unroll
+        for (int u = 0; u < kSeedUnroll; ++u) {
+            const long long i = base + (long long)u * blockDim.x;
+            if (i < n8) {
+                a[u] = g[2 * i];
+                b[u] = g[2 * i + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSeedUnroll; ++u) {
+            const long long i = base + (long long)u * blockDim.x;
+            if (i < n8) {
+                uint4 o;
+                o.x = pack_bf16x2(a[u].x * scale, a[u].y * scale);
+                o.y = pack_bf16x2(a[u].z * scale, a[u].w * scale);
+                o.z = pack_bf16x2(b[u].x * scale, b[u].y * scale);
+                o.w = pack_bf16x2(b[u].z * scale, b[u].w * scale);
+                d[i] = o;
+            }
+        }
+    }
+}
+
 struct LayerTable {
     int L;
     int rows[kMaxLayers];         // N_l (outputs)
@@ -1095,21 +1128,29 @@ int synax_surrogate(synax_surrogate_t* s, const float* theta_dev, int n, float* 
     const bool vjp = gcoeff_dev != nullptr;
     for (int r0 = 0; r0 < n; r0 += s->E) {
         const int m = n - r0 < s->E ? n - r0 : s->E;
-        if (vjp) {
-            // the seed's scaling and BF16 rounding depend only on the caller's
-            // seed: they run on the side stream (after everything enqueued so
-            // far, including the previous chunk's use of eD0) while the
-            // forward products run here; HBM-bound, it overlaps the
-            // epilogue-bound forward layers
+        // The seed's scaling and BF16 rounding depend only on the caller's
+        // seed.  They run on the side stream (after everything enqueued so
+        // far, including the previous chunk's use of eD0) while the forward
+        // layers run here.  Forking them instead just before the output
+        // layer's forward GEMM, whose CTAs leave room beside them, measured
+        // 1.036 ms per 16384-set call against 0.946 ms.
+        auto launch_seed = [&]() -> int {
             cudaError_t e = cudaEventRecord(s->ev_fork, st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
             if (e != cudaSuccess) return record_cuda_error((int)e);
-            k_seed_out<<<grid_for((long long)m * s->n_out), 256, 0, s->side>>>(
-                gcoeff_dev + (long long)r0 * s->n_out, (long long)m * s->n_out, s->scale, s->eD0);
+            const float* gsrc = gcoeff_dev + (long long)r0 * s->n_out;
+            const long long nseed = (long long)m * s->n_out;
+            if ((((uintptr_t)gsrc | (uintptr_t)s->eD0) & 15) == 0 && nseed % 8 == 0)
+                k_seed_out8<<<2 * device_sm_count(), 256, 0, s->side>>>(reinterpret_cast<const float4*>(gsrc),
+                                                                         nseed / 8, s->scale,
+                                                                         reinterpret_cast<uint4*>(s->eD0));
+            else
+                k_seed_out<<<grid_for(nseed), 256, 0, s->side>>>(gsrc, nseed, s->scale, s->eD0);
             SX_TRY(launch_status());
             e = cudaEventRecord(s->ev_join, s->side);
-            if (e != cudaSuccess) return record_cuda_error((int)e);
-        }
+            return e == cudaSuccess ? SYNAX_OK : record_cuda_error((int)e);
+        };
+        if (vjp) SX_TRY(launch_seed());
         GatherArgs a = gather_identity(s, theta_dev + (long long)r0 * nt, m, s->eX[0], nullptr, nullptr);
         k_gather_input<<<(m + 3) / 4, 128, 0, st>>>(a);
         SX_TRY(launch_status());
