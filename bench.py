@@ -77,6 +77,9 @@ def parse():
                     help="run only the grid-model measurement (no interpolation study) and print its JSON")
     ap.add_argument("--grid-runs", type=int, default=10, help="timed steps of the grid-model measurement")
     ap.add_argument("--only-hmc", action="store_true", help="run only the HMC sampling measurement")
+    ap.add_argument("--only-wmap-stack", action="store_true",
+                    help="run only the stacked-WMAP (Eq. 16) measurement, --wmap-stack-runs timed steps")
+    ap.add_argument("--wmap-stack-runs", type=int, default=10, help="timed steps of the stacked-WMAP measurement")
     ap.add_argument("--only-batch-low-res", action="store_true",
                     help="run only the 256-chain Nside-16 batch measurement and print its JSON (a profiling aid)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the learned surrogate")
@@ -787,6 +790,11 @@ def run_synax(args):
             print(json.dumps({"batch_low_res": bench_batch(sx, inputs, torch, dev, n_runs=3, sets=chains,
                                                            name="256 chains, Nside 16, 256 steps")}), flush=True)
         return
+    if args.only_wmap_stack:
+        if rank == 0:
+            print(json.dumps({"wmap_stack": bench_wmap_stack(sx, inputs, torch, dev, max(args.wmap_stack_runs, 1))}),
+                  flush=True)
+        return
     if args.only_grid:
         if rank == 0:
             print(json.dumps({"grid": bench_grid(sx, inputs, torch, dev, max(args.grid_runs, 1),
@@ -988,7 +996,7 @@ def run_synax(args):
     if extras and not args.no_grid:
         out["grid"] = bench_grid(sx, inputs, torch, dev)
         out["interp_study"] = interp_study(sx, inputs, torch)
-        out["wmap_stack"] = bench_wmap_stack(sx, inputs, torch, dev)
+        out["wmap_stack"] = bench_wmap_stack(sx, inputs, torch, dev, max(args.wmap_stack_runs, 1))
         out["hmc"] = bench_hmc(sx, inputs, torch, dev)
     # every row against its kernel's roofline (same clock as the main line)
     for key in ("batch", "batch_low_res"):
