@@ -65,12 +65,19 @@ __device__ __forceinline__ float cos_approx(float x) {
 // cos (degree 10) on |r| <= pi/4 by Horner's rule, and the quadrant k mod 4.
 // Measured against FP64: at most 1.4 ulp, no mean bias, the class of
 // sincosf at about half its arithmetic.
+// k comes from one FMA against the magic constant 1.5 * 2^23: x 2/pi + M,
+// rounded once to FP32 (unit spacing there), is M + k with k the nearest
+// integer, so k = that - M exactly and k mod 4 is the low two bits of its
+// encoding (|k| < 2^22): no rounding or float-to-integer conversion on the
+// SFU.
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
 __device__ __forceinline__ void sincos_cw(float x, float* s, float* c) {
     if (!(fabsf(x) < 3200.0f)) {
         sincosf(x, s, c);
         return;
     }
-    const float k = rintf(x * 0.63661977236758134f);
+    const float t = fmaf(x, 0.63661977236758134f, kRoundMagic);
+    const float k = t - kRoundMagic;
     float r = fmaf(-k, 1.5703125f, x);
     r = fmaf(-k, 4.837512969970703e-4f, r);
     r = fmaf(-k, 7.549790126404332e-8f, r);
@@ -84,7 +91,7 @@ __device__ __forceinline__ void sincos_cw(float x, float* s, float* c) {
     pc = fmaf(r2, pc, 4.1666667e-2f);                         // 1/4!
     pc = fmaf(r2, pc, -0.5f);
     const float cs = fmaf(r2, pc, 1.0f);
-    const int q = (int)k & 3;
+    const int q = __float_as_int(t) & 3;
     const float ss = (q & 1) ? cs : sn, cc = (q & 1) ? sn : cs;
     *s = (q & 2) ? -ss : ss;
     *c = ((q + 1) & 2) ? -cc : cc;
@@ -267,7 +274,9 @@ __device__ __forceinline__ void sincos_cw2(float2 x, float2& s, float2& c) {
         sincos_cw(x.y, &s.y, &c.y);
         return;
     }
-    const float2 k = make_float2(rintf(x.x * 0.63661977236758134f), rintf(x.y * 0.63661977236758134f));
+    // k = nearest integer to x 2/pi by the magic-constant FMA (sincos_cw)
+    const float2 t = fma2(x, dup2(0.63661977236758134f), dup2(kRoundMagic));
+    const float2 k = add2(t, dup2(-kRoundMagic));
     float2 r = fma2(neg2(k), dup2(1.5703125f), x);
     r = fma2(neg2(k), dup2(4.837512969970703e-4f), r);
     r = fma2(neg2(k), dup2(7.549790126404332e-8f), r);
@@ -281,7 +290,7 @@ __device__ __forceinline__ void sincos_cw2(float2 x, float2& s, float2& c) {
     pc = fma2(r2, pc, dup2(4.1666667e-2f));
     pc = fma2(r2, pc, dup2(-0.5f));
     const float2 cs = fma2(r2, pc, dup2(1.0f));
-    const int qa = (int)k.x & 3, qb = (int)k.y & 3;
+    const int qa = __float_as_int(t.x) & 3, qb = __float_as_int(t.y) & 3;
     const float sa = (qa & 1) ? cs.x : sn.x, ca = (qa & 1) ? sn.x : cs.x;
     const float sb = (qb & 1) ? cs.y : sn.y, cb = (qb & 1) ? sn.y : cs.y;
     s = make_float2((qa & 2) ? -sa : sa, (qb & 2) ? -sb : sb);
