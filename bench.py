@@ -159,7 +159,7 @@ def measure_peaks(sx) -> dict:
     return {"fp32_top": max(r["ffma"], r["ffma2"]) / 1e12, "mufu_ex2": mufu["ex2"],
             "mufu_other": min(v for k, v in mufu.items() if k != "ex2"),
             "unit": "T element op/s", "ffma": r["ffma"] / 1e12, "ffma2": r["ffma2"] / 1e12, "mufu": mufu,
-            "sms": r["sms"]}
+            "sfu_conversions": {"frnd": r["frnd"] / 1e12, "f2i": r["f2i"] / 1e12}, "sms": r["sms"]}
 
 
 def roofline_alu(fp32_ops: float, mufu_ops: float, t_s: float, peaks: dict, kernel: str,

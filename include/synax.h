@@ -558,6 +558,8 @@ int synax_checked_selftest(void);
 #define SYNAX_PIPE_COS   5
 #define SYNAX_PIPE_RCP   6
 #define SYNAX_PIPE_RSQRT 7
+#define SYNAX_PIPE_FRND  8
+#define SYNAX_PIPE_F2I   9
 /* ---- pipe-throughput microbenchmarks (no counterpart in the paper) ----
  * The march is bound by the FP32 pipe and the SFU, not by memory, so its
  * roofline needs their throughput on the GPU at hand.  synax_pipe_peak
@@ -568,6 +570,10 @@ int synax_checked_selftest(void);
  *   SYNAX_PIPE_EX2, _LG2, _SIN, _COS, _RCP, _RSQRT: the PTX
  *       ex2/lg2/sin/cos/rcp/rsqrt.approx.ftz.f32 instructions (each chain
  *       step may add one FP32 multiply or add to keep values bounded).
+ *   SYNAX_PIPE_FRND  cvt.rni.f32.f32 (rintf), SYNAX_PIPE_F2I cvt.rni.s32.f32:
+ *       the rounding and float-to-integer conversions, which share the SFU
+ *       (each step adds one FP32 add, or one integer OR, to keep the chain
+ *       moving).
  * *ops_out receives the element operations of the launch (an FFMA2 counts
  * two); the caller times the launch on `stream` and divides.  sink_dev:
  * device float[blocks * 256], overwritten (keeps the chains live).

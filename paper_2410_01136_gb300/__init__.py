@@ -409,7 +409,7 @@ def last_status(stream=None) -> tuple[int, int, int]:
     return code, site.value, index.value
 
 
-def pipe_peaks(pipes=("ffma", "ffma2", "ex2", "lg2", "sin", "cos", "rcp", "rsqrt"), blocks_per_sm: int = 8,
+def pipe_peaks(pipes=("ffma", "ffma2", "ex2", "lg2", "sin", "cos", "rcp", "rsqrt", "frnd", "f2i"), blocks_per_sm: int = 8,
                iters: int = 4096, repeats: int = 5) -> dict:
     """Measured throughput of the FP32 pipe and the SFU on the current device
     (synax_pipe_peak): per pipe the best of `repeats` launches, in element

@@ -27,7 +27,7 @@ SYNAX_EBOUNDS = -8
 SITE_MAP_STORE, SITE_SEED_LOAD, SITE_PARTIAL, SITE_GRID_LOAD, SITE_GRID_SCATTER, SITE_BATCH_SET, \
     SITE_GEMM_WAIT = range(1, 8)
 
-PIPES = {"ffma": 0, "ffma2": 1, "ex2": 2, "lg2": 3, "sin": 4, "cos": 5, "rcp": 6, "rsqrt": 7}
+PIPES = {"ffma": 0, "ffma2": 1, "ex2": 2, "lg2": 3, "sin": 4, "cos": 5, "rcp": 6, "rsqrt": 7, "frnd": 8, "f2i": 9}
 
 SYNAX_F64 = 1 << 0
 SYNAX_BOX_CLIP = 1 << 1

@@ -1,6 +1,7 @@
 // peaks.cu -- pipe-throughput microbenchmarks that give the march's roofline
 // denominators: the FP32 FMA pipe (scalar FFMA and paired FFMA2) and the SFU
-// (MUFU ex2, lg2, sin, cos, rcp, rsqrt as the PTX .approx.ftz.f32 forms).
+// (MUFU ex2, lg2, sin, cos, rcp, rsqrt as the PTX .approx.ftz.f32 forms, and
+// the rounding and float-to-integer conversions that share it).
 //
 // Each thread runs kChains independent dependency chains for `iters`
 // iterations, so that the pipe, not the latency of one chain, is the limit;
@@ -45,6 +46,21 @@ __device__ __forceinline__ float mufu_step(float x) {
     }
 }
 
+// Conversions on the SFU: round to integer (kept as a float) and float to
+// integer (its bits put back into a float in [1, 2) by one OR).
+template <int PIPE>
+__device__ __forceinline__ float cvt_step(float x) {
+    if constexpr (PIPE == SYNAX_PIPE_FRND) {
+        float y;
+        asm volatile("cvt.rni.f32.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y + 0.3f;                        // x -> rint(x) + 0.3: a fixed point, never folded
+    } else {
+        int y;
+        asm volatile("cvt.rni.s32.f32 %0, %1;" : "=r"(y) : "f"(x));
+        return __int_as_float(y | 0x3f800000);  // stays in [1, 2)
+    }
+}
+
 template <int PIPE>
 __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, float seed, float* __restrict__ sink) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,6 +87,16 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, float seed, fl
         }
 #pragma unroll
         for (int c = 0; c < kChains; ++c) r += a[c].x + a[c].y;
+    } else if constexpr (PIPE == SYNAX_PIPE_FRND || PIPE == SYNAX_PIPE_F2I) {
+        float a[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) a[c] = 0.25f + 0.37f * (float)c + seed;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) a[c] = cvt_step<PIPE>(a[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) r += a[c];
     } else {
         float a[kChains];
 #pragma unroll
@@ -104,6 +130,8 @@ extern "C" int synax_pipe_peak(int pipe, int blocks, int iters, float* sink_dev,
     case SYNAX_PIPE_COS: k_peak<SYNAX_PIPE_COS><<<blocks, kPeakThreads, 0, st>>>(iters, 0.0f, sink_dev); break;
     case SYNAX_PIPE_RCP: k_peak<SYNAX_PIPE_RCP><<<blocks, kPeakThreads, 0, st>>>(iters, 0.0f, sink_dev); break;
     case SYNAX_PIPE_RSQRT: k_peak<SYNAX_PIPE_RSQRT><<<blocks, kPeakThreads, 0, st>>>(iters, 0.0f, sink_dev); break;
+    case SYNAX_PIPE_FRND: k_peak<SYNAX_PIPE_FRND><<<blocks, kPeakThreads, 0, st>>>(iters, 0.0f, sink_dev); break;
+    case SYNAX_PIPE_F2I: k_peak<SYNAX_PIPE_F2I><<<blocks, kPeakThreads, 0, st>>>(iters, 0.0f, sink_dev); break;
     default: return SYNAX_EINVAL;
     }
     const cudaError_t err = cudaGetLastError();
