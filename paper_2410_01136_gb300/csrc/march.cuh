@@ -1509,10 +1509,72 @@ __device__ __forceinline__ void wmap_eval(const float* m, float2 x, float2 y, fl
     }
 }
 
+// B, N0 and n_e of the stacked WMAP model (Eq. 16) at two points, element
+// by element as Model<WMAP_STACK>::eval (the same operations and summation
+// order; the range test a select).
+__device__ __forceinline__ void stack_eval(const float* m, float2 x, float2 y, float2 z, float2 B[3], float2& N0,
+                                           float2& ne, const FlatZ& fz) {
+    const float2 rho2 = fma2(x, x, mul2(y, y));
+    const float2 rho = f2(__fsqrt_rn(rho2.x), __fsqrt_rn(rho2.y));
+    const float2 rr = rcp_nr(rho);
+    const float2 ri = f2(rho2.x > 0.0f ? rr.x : 0.0f, rho2.y > 0.0f ? rr.y : 0.0f);
+    const float2 cq = mul2(x, ri), sq = mul2(y, ri);
+    const float2 c = f2(rho2.x > 0.0f ? cq.x : 1.0f, rho2.y > 0.0f ? cq.y : 1.0f);
+    const float2 s = f2(rho2.x > 0.0f ? sq.x : 0.0f, rho2.y > 0.0f ? sq.y : 0.0f);
+    const float2 az = f2(fabsf(z.x), fabsf(z.y));
+    const float2 e2 = expf2(mul2(dup2(-2.0f), az));                  // e^{-2|z|}
+    const float2 inv1 = rcp_nr(add2(dup2(1.0f), e2));
+    const bool in_a = rho.x >= 3.0f && rho.x <= 20.0f, in_b = rho.y >= 3.0f && rho.y <= 20.0f;
+    const float2 r8 = mul2(rho, dup2(0.125f));
+    const float2 lnr8 = f2(in_a ? logf(r8.x) : 0.0f, in_b ? logf(r8.y) : 0.0f);
+    float2 th = mul2(add2(dup2(1.0f), neg2(e2)), inv1);                 // tanh |z|
+    th = f2(z.x < 0.0f ? -th.x : th.x, z.y < 0.0f ? -th.y : th.y);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float* q = m + mc::S_COMP + 4 * k;
+        const float2 psi = f2(in_a ? fmaf(q[2], lnr8.x, q[1]) : 0.0f, in_b ? fmaf(q[2], lnr8.y, q[1]) : 0.0f);
+        const float2 chi = f2(in_a ? q[3] * th.x : 0.0f, in_b ? q[3] * th.y : 0.0f);
+        float2 sp, cp, sc, cc;
+        sincos_cw2(psi, sp, cp);
+        sincos_cw2(chi, sc, cc);
+        const float2 ur = mul2(cp, cc), up = mul2(sp, cc);
+        const float2 hi = dup2(m[mc::S_WB + k]), lo = dup2(m[mc::S_WB_LO + k]);
+        const float2 u0 = fma2(ur, c, neg2(mul2(up, s)));
+        const float2 u1 = fma2(ur, s, mul2(up, c));
+        const float2 c0 = fma2(u0, hi, mul2(u0, lo));                    // mul_hl
+        const float2 c1 = fma2(u1, hi, mul2(u1, lo));
+        const float2 c2 = fma2(sc, hi, mul2(sc, lo));
+        // the component permutations of Eq. 16, summed in component order
+        if (k == 0) { B[0] = c0; B[1] = c1; B[2] = c2; }
+        if (k == 1) { B[0] = add2(B[0], c0); B[1] = add2(B[1], c2); B[2] = add2(B[2], c1); }
+        if (k == 2) { B[0] = add2(B[0], c2); B[1] = add2(B[1], c1); B[2] = add2(B[2], c0); }
+        if (k == 3) { B[0] = add2(B[0], c1); B[1] = add2(B[1], c0); B[2] = add2(B[2], c2); }
+    }
+    // CR density (fast primitives: magnitudes only), as cr_density
+    const float2 e2c = mul2(dup2((float)(-2.0 * kLog2e)), az);
+    const float2 ec = f2(ex2_approx(e2c.x), ex2_approx(e2c.y));
+    const float2 onep = add2(dup2(1.0f), ec);
+    const float2 iv = f2(rcp_approx(onep.x), rcp_approx(onep.y));
+    const float2 er = mul2(dup2((float)(-0.2 * kLog2e)), rho);
+    const float2 eR = f2(ex2_approx(er.x), ex2_approx(er.y));
+    const float2 n0u = mul2(dup2(m[mc::S_N0U]), mul2(eR, mul2(mul2(dup2(4.0f), ec), mul2(iv, iv))));
+    N0 = mul2(dup2(m[mc::S_N0OBS]), n0u);
+    const float2 ne_r = expf2(neg2(mulc(rho, 0.05)));
+    const float2 sech2 = mul2(mul2(mul2(dup2(4.0f), e2), inv1), inv1);
+    const float2 neu = fz.flat ? fma2(ne_r, dup2(fz.hi), mul2(ne_r, dup2(fz.lo))) : mul2(ne_r, sech2);
+    ne = fma2(neu, dup2(m[mc::S_NE0]), mul2(neu, dup2(m[mc::S_NE0_LO])));      // ne0 as hi + lo
+}
+
 }  // namespace pair2
 
-// The FP32 JF12-type and WMAP-type lane march, two samples per iteration
-// (see pair2).  Same contract as march_lane.
+// The stacked WMAP model fills the box at constant magnitude, so its
+// positions and RM integrand carry the low parts of the direction as the
+// one-sample march does for it (kPreciseLos, sample_pos, bpar_lo).
+template <int MODEL>
+constexpr bool kPreciseLosPair = MODEL == SYNAX_MODEL_WMAP_STACK;
+
+// The FP32 JF12-type, WMAP-type and stacked-WMAP lane march, two samples per
+// iteration (see pair2).  Same contract as march_lane.
 template <int MODEL, int NF>
 __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const float* s_arms,
                                                 const Los<float>& L, const ff* nd, int n0, int n1, float dr,
@@ -1530,20 +1592,28 @@ __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const
     float2 nh = make_float2(float(n0) + 0.5f, float(n0) + 1.5f);     // n + 1/2, exact
     const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
     FlatZ fz{false, 0.0f, 0.0f};
-    if constexpr (MODEL == SYNAX_MODEL_WMAP) fz = flat_z_of(P, nd);
+    if constexpr (MODEL == SYNAX_MODEL_WMAP || MODEL == SYNAX_MODEL_WMAP_STACK) fz = flat_z_of(P, nd);
     for (int n = n0; n < n1; n += 2, nh = add2(nh, dup2(2.0f))) {
         // the second sample of an odd tail is a placeholder whose terms are zeroed
         const float live_b = n + 1 < n1 ? 1.0f : 0.0f;
         const float2 t = fma2(nh, dup2(dr), mul2(nh, dup2(dr_lo)));
-        const float2 x = fma2(t, dup2(L.n[0]), obs_x);
-        const float2 y = fma2(t, dup2(L.n[1]), obs_y);
-        const float2 z = fma2(t, dup2(L.n[2]), obs_z);
+        float2 x = fma2(t, dup2(L.n[0]), obs_x);
+        float2 y = fma2(t, dup2(L.n[1]), obs_y);
+        float2 z = fma2(t, dup2(L.n[2]), obs_z);
+        if constexpr (kPreciseLosPair<MODEL>) {
+            // the low parts of the direction and observer (sample_pos)
+            x = add2(x, fma2(t, dup2(nd[0].lo), dup2(P.obs_lo[0])));
+            y = add2(y, fma2(t, dup2(nd[1].lo), dup2(P.obs_lo[1])));
+            z = add2(z, fma2(t, dup2(nd[2].lo), dup2(P.obs_lo[2])));
+        }
         float2 B[3], N0, ne;
         if constexpr (MODEL == SYNAX_MODEL_JF12) {
             const ArmCoord<float> aa = trk.coord(0.f, 0.f, 0.f);
             ArmCoord<float> ab;
             trk.step_pair(+1, ab);
             pair2::jf12_eval(P.m, s_arms, x, y, z, aa, ab, B, N0, ne);
+        } else if constexpr (MODEL == SYNAX_MODEL_WMAP_STACK) {
+            pair2::stack_eval(P.m, x, y, z, B, N0, ne, fz);
         } else {
             pair2::wmap_eval(P.m, x, y, z, B, N0, ne, fz);
         }
@@ -1563,7 +1633,13 @@ __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const
         accI2 = fma2(nw, bp2, accI2);
         const float2 pc = mul2(nw, fma2(bl, bl, neg2(mul2(bb, bb))));
         const float2 ps = mul2(nw, mul2(dup2(2.0f), mul2(bl, bb)));
-        const float2 f = mul2(neg2(mul2(ne, bn)), make_float2(1.0f, live_b));
+        float2 fr = neg2(mul2(ne, bn));
+        if constexpr (kPreciseLosPair<MODEL>) {
+            // B . n_lo, the part of B_LOS that the FP32 direction drops (bpar_lo)
+            const float2 blo = fma2(B[0], dup2(nd[0].lo), fma2(B[1], dup2(nd[1].lo), mul2(B[2], dup2(nd[2].lo))));
+            fr = fma2(neg2(ne), blo, fr);
+        }
+        const float2 f = mul2(fr, make_float2(1.0f, live_b));
         // RM at the two midpoints: s_a = S + w f_a, S1 = S + f_a; s_b = S1 + w f_b, S2 = S1 + f_b
         ff s_a, S1, s_b;
         ff_add_f_pair(S, make_float2(P.w_own * f.x, f.x), s_a, S1);
@@ -1640,7 +1716,8 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
                                            typename PhaseOps<R>::T& S) {
     using Ph = PhaseOps<R>;
     using PT = typename Ph::T;
-    if constexpr (sizeof(R) == 4 && (MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP)) {
+    if constexpr (sizeof(R) == 4 &&
+                  (MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP || MODEL == SYNAX_MODEL_WMAP_STACK)) {
         march_lane_pair<MODEL, NF>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
         return;
     }
