@@ -720,7 +720,17 @@ template <int EPI>
 int launch_gemm_bn(const CUtensorMap& ma, const void* B, int N, int K, int ldb, int M, const GemmEpiParams& ep,
                    int* err, cudaStream_t st) {
     CUtensorMap mb;
-    const int bn = gemm_bn_for(N, K);
+    int bn = gemm_bn_for(N, K);
+    // FP32 outputs (their 128-row staging chunks keep the epilogue light): a
+    // 128 x 256 tile fetches 768 KB of operands per 2 x 128 x 256 x K flop
+    // against 512 KB per half the work at 128 columns, and the SMs' operand
+    // bandwidth is what a 128-column tile runs out of at K ~ 1024
+    // (16384 x 1024 x 1024: 40.3 against 48.1 us).  Only with two waves of
+    // tiles or more, so that smaller products keep enough CTAs.
+    constexpr bool kF32Out = EPI == EPI_F32 || EPI == EPI_BIAS_F32 || EPI == EPI_AFFINE || EPI == EPI_SCALE_ACC;
+    if (kF32Out && bn == 128 && N >= 1024 &&
+        (long long)((M + kGemmBM - 1) / kGemmBM) * ((N + 255) / 256) >= 2LL * sm_count())
+        bn = 256;
     if (bn == 256) {
         if (make_map(&mb, B, N, K, ldb, 256) != SYNAX_OK) return SYNAX_EINVAL;
         return launch_gemm_t<256, EPI>(ma, mb, M, N, K, ep, err, st);

@@ -36,7 +36,8 @@ def run_gemm(torch, A, B, ldc=None):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 64, 64), (256, 1024, 1024), (200, 9216, 1024),
-                                   (1024, 64, 512), (512, 300, 128), (77, 256, 192), (1, 1024, 64)])
+                                   (1024, 64, 512), (512, 300, 128), (77, 256, 192), (1, 1024, 64),
+                                   (12345, 1100, 64)])          # two waves of 256-column tiles, ragged edges
 def test_gemm_matches_fp32_matmul(torch, M, N, K):
     g = torch.Generator(device="cuda").manual_seed(M * 7919 + N * 31 + K)
     A = torch.randn((M, K), generator=g, device="cuda").to(torch.bfloat16)
