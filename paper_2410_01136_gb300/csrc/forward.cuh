@@ -33,8 +33,10 @@ namespace synax {
 // registers): measured for the Nside-64, 512-step, 4-frequency map (8 lanes
 // per ray, 3072 CTAs), 5 CTAs per SM (95 registers, 4.04 waves) 0.247 ms;
 // 6 (79 registers, 3.37 waves) 0.250 ms; 7 and 8 (spills) 0.255 and
-// 0.260 ms; 64-thread CTAs at 12 or 14 per SM 0.250 and 0.255 ms.  The other
-// models keep 6 per SM (at most 85 registers), where they were measured.
+// 0.260 ms; 64-thread CTAs at 12 or 14 per SM 0.250 and 0.255 ms.  The grid
+// model's two-sample march also runs 5 (6 spill 64 bytes at 80 registers:
+// 0.260 against 0.251 ms for the Sec. 3.3 map at 16 lanes per ray).  The
+// other models keep 6 per SM (at most 85 registers), where they were measured.
 // SYNAX_FWD_MIN_BLOCKS / SYNAX_FWD_THREADS override both at build time.
 #ifndef SYNAX_FWD_THREADS
 #define SYNAX_FWD_THREADS 128
@@ -44,7 +46,7 @@ template <int MODEL> constexpr int fwd_min_blocks() {
 #ifdef SYNAX_FWD_MIN_BLOCKS
     return SYNAX_FWD_MIN_BLOCKS;
 #else
-    return MODEL == SYNAX_MODEL_JF12 ? 5 : 6;
+    return MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_GRID ? 5 : 6;
 #endif
 }
 

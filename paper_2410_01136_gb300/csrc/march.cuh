@@ -1565,16 +1565,76 @@ __device__ __forceinline__ void stack_eval(const float* m, float2 x, float2 y, f
     ne = fma2(neu, dup2(m[mc::S_NE0]), mul2(neu, dup2(m[mc::S_NE0_LO])));      // ne0 as hi + lo
 }
 
+// Grid model at samples n and n + 1 of a ray (grid_locate_ray, grid_blend
+// and grid_eval element by element).  When both samples fall in one cell the
+// trilinear blend runs as element pairs from the cached cell; otherwise the
+// two are blended one after the other, the second reloading the cache.
+__device__ __forceinline__ void grid_blend2(const GridCell<float>& gc, float2 fx, float2 fy, float2 fz, float2 B[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 t3 = fma2(fy, fma2(fz, dup2(gc.h[c]), dup2(gc.e[c])), fma2(fz, dup2(gc.f[c]), dup2(gc.b[c])));
+        const float2 t6 = fma2(fy, fma2(fz, dup2(gc.g[c]), dup2(gc.c[c])), fma2(fz, dup2(gc.d[c]), dup2(gc.a[c])));
+        B[c] = fma2(fx, t3, t6);
+    }
+}
+__device__ __forceinline__ void grid_pair(const MapParams<float>& P, GridCell<float>& gc, const GridRay<float>& g,
+                                          int n, float2 x, float2 y, float2 z, const FlatZ& fz, float2 B[3],
+                                          float2& N0, float2& ne) {
+    const float2 kf = make_float2((float)(n - g.na), (float)(n + 1 - g.na));
+    float2 fr[3];
+    int ca[3], cb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float2 v = fma2(kf, dup2(g.du[k]), fma2(kf, dup2(g.dulo[k]), dup2(g.a[k])));
+        const float2 fl = f2(floorf(v.x), floorf(v.y));
+        float fa, fb;
+        ca[k] = grid_axis_split<float>(g.ia[k] + fl.x, v.x - fl.x, P.m[mc::G_UMAX + k], fa);
+        cb[k] = grid_axis_split<float>(g.ia[k] + fl.y, v.y - fl.y, P.m[mc::G_UMAX + k], fb);
+        fr[k] = f2(fa, fb);
+    }
+    const int base_a = (ca[2] * P.grid_n[1] + ca[1]) * P.grid_n[0] + ca[0];
+    const int base_b = (cb[2] * P.grid_n[1] + cb[1]) * P.grid_n[0] + cb[0];
+    if (base_a != gc.base) grid_load<float>(P, base_a, gc);
+    if (base_b == base_a) {
+        grid_blend2(gc, fr[0], fr[1], fr[2], B);
+    } else {
+        float Ba[3], Bb[3];
+        grid_blend<float>(gc, fr[0].x, fr[1].x, fr[2].x, Ba);
+        grid_load<float>(P, base_b, gc);
+        grid_blend<float>(gc, fr[0].y, fr[1].y, fr[2].y, Bb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) B[c] = f2(Ba[c], Bb[c]);
+    }
+    // N0 and n_e: the WMAP-type profiles (grid_eval)
+    const float2 rho2 = fma2(x, x, mul2(y, y));
+    const float2 rho = f2(__fsqrt_rn(rho2.x), __fsqrt_rn(rho2.y));
+    const float2 az = f2(fabsf(z.x), fabsf(z.y));
+    const float2 e2 = expf2(mul2(dup2(-2.0f), az));                  // e^{-2|z|}
+    const float2 inv1 = rcp_nr(add2(dup2(1.0f), e2));
+    const float2 e2c = mul2(dup2((float)(-2.0 * kLog2e)), az);
+    const float2 ec = f2(ex2_approx(e2c.x), ex2_approx(e2c.y));
+    const float2 onep = add2(dup2(1.0f), ec);
+    const float2 iv = f2(rcp_approx(onep.x), rcp_approx(onep.y));
+    const float2 er = mul2(dup2((float)(-0.2 * kLog2e)), rho);
+    const float2 eR = f2(ex2_approx(er.x), ex2_approx(er.y));
+    const float2 n0u = mul2(dup2(P.m[mc::G_N0U]), mul2(eR, mul2(mul2(dup2(4.0f), ec), mul2(iv, iv))));
+    N0 = mul2(dup2(P.m[mc::G_N0OBS]), n0u);
+    const float2 ne_r = expf2(neg2(mulc(rho, 0.05)));
+    const float2 sech2 = mul2(mul2(mul2(dup2(4.0f), e2), inv1), inv1);
+    const float2 neu = fz.flat ? fma2(ne_r, dup2(fz.hi), mul2(ne_r, dup2(fz.lo))) : mul2(ne_r, sech2);
+    ne = fma2(neu, dup2(P.m[mc::G_NE0]), mul2(neu, dup2(P.m[mc::G_NE0_LO])));      // ne0 as hi + lo
+}
+
 }  // namespace pair2
 
-// The stacked WMAP model fills the box at constant magnitude, so its
-// positions and RM integrand carry the low parts of the direction as the
-// one-sample march does for it (kPreciseLos, sample_pos, bpar_lo).
+// The stacked WMAP and grid models fill the box, so their positions and RM
+// integrand carry the low parts of the direction as the one-sample march
+// does for them (kPreciseLos, sample_pos, bpar_lo).
 template <int MODEL>
-constexpr bool kPreciseLosPair = MODEL == SYNAX_MODEL_WMAP_STACK;
+constexpr bool kPreciseLosPair = MODEL == SYNAX_MODEL_WMAP_STACK || MODEL == SYNAX_MODEL_GRID;
 
-// The FP32 JF12-type, WMAP-type and stacked-WMAP lane march, two samples per
-// iteration (see pair2).  Same contract as march_lane.
+// The FP32 lane march of the JF12-type, WMAP-type, stacked-WMAP and grid
+// models, two samples per iteration (see pair2).  Same contract as march_lane.
 template <int MODEL, int NF>
 __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const float* s_arms,
                                                 const Los<float>& L, const ff* nd, int n0, int n1, float dr,
@@ -1589,10 +1649,16 @@ __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const
     if constexpr (MODEL == SYNAX_MODEL_JF12) {
         if (n0 < n1) trk.init(P, nd, n0, dr, dr_lo);
     }
+    GridCell<float> gc;
+    GridRay<float> gr;
+    gc.base = -1;
+    if constexpr (MODEL == SYNAX_MODEL_GRID) {
+        if (n0 < n1) grid_ray_init<float>(P, L, nd, n0, dr, dr_lo, gr);
+    }
     float2 nh = make_float2(float(n0) + 0.5f, float(n0) + 1.5f);     // n + 1/2, exact
     const float2 obs_x = dup2(P.obs[0]), obs_y = dup2(P.obs[1]), obs_z = dup2(P.obs[2]);
     FlatZ fz{false, 0.0f, 0.0f};
-    if constexpr (MODEL == SYNAX_MODEL_WMAP || MODEL == SYNAX_MODEL_WMAP_STACK) fz = flat_z_of(P, nd);
+    if constexpr (MODEL != SYNAX_MODEL_JF12) fz = flat_z_of(P, nd);
     for (int n = n0; n < n1; n += 2, nh = add2(nh, dup2(2.0f))) {
         // the second sample of an odd tail is a placeholder whose terms are zeroed
         const float live_b = n + 1 < n1 ? 1.0f : 0.0f;
@@ -1614,6 +1680,8 @@ __device__ __forceinline__ void march_lane_pair(const MapParams<float>& P, const
             pair2::jf12_eval(P.m, s_arms, x, y, z, aa, ab, B, N0, ne);
         } else if constexpr (MODEL == SYNAX_MODEL_WMAP_STACK) {
             pair2::stack_eval(P.m, x, y, z, B, N0, ne, fz);
+        } else if constexpr (MODEL == SYNAX_MODEL_GRID) {
+            pair2::grid_pair(P, gc, gr, n, x, y, z, fz, B, N0, ne);
         } else {
             pair2::wmap_eval(P.m, x, y, z, B, N0, ne, fz);
         }
@@ -1716,8 +1784,8 @@ __device__ __forceinline__ void march_lane(const MapParams<R>& P, const R* s_arm
                                            typename PhaseOps<R>::T& S) {
     using Ph = PhaseOps<R>;
     using PT = typename Ph::T;
-    if constexpr (sizeof(R) == 4 &&
-                  (MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP || MODEL == SYNAX_MODEL_WMAP_STACK)) {
+    if constexpr (sizeof(R) == 4 && (MODEL == SYNAX_MODEL_JF12 || MODEL == SYNAX_MODEL_WMAP ||
+                                     MODEL == SYNAX_MODEL_WMAP_STACK || MODEL == SYNAX_MODEL_GRID)) {
         march_lane_pair<MODEL, NF>(P, s_arms, L, nd, n0, n1, dr, dr_lo, cd, accI, zr, zi, S);
         return;
     }
